@@ -1,0 +1,389 @@
+"""Benchmark of the pipe-flow time step on GB300 (one JSON line on stdout).
+
+Workload: the medium single-run configuration -- N=48 radial points, |k|<32,
+m<24, m_p=2, Re=2400, alpha=1.25, dt=0.005, seeded puff-like perturbation of
+amplitude 0.1 -- one "step" = one full predictor-corrector time step
+(2 nonlinear evaluations + 2 banded-solve passes) of that grid.  The state
+fits in L2, so L2 is flushed (256 MB write) between timed steps and each
+step is timed alone with CUDA events on the launching stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision 0|1] [--impl reference]
+
+N > 1 (torchrun, one rank per GPU): independent replicas, no collective on
+the data path; time = max over ranks; value = all ranks' steps / that time.
+--impl reference times the CPU oracle (the plain FP64 restatement of the
+method) on the host cores for the same workload and metric.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "timesteps/s & GDOF-steps/s per grid, mixed vs FP64 on 1 GB300; % HBM roofline"
+WORKLOAD = "medium"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_params():
+    from paper_1705_03838_gb300 import inputs
+
+    w = inputs.WORKLOADS[WORKLOAD]
+    return w
+
+
+def dof(w):
+    return 3 * w["N"] * (2 * w["K"] - 1) * (2 * w["M"] - 1)
+
+
+def config_dict(w, precision):
+    return {
+        "workload": (f"pipe medium: N={w['N']} |k|<{w['K']} m<{w['M']} m_p={w['m_p']} "
+                     f"Re={w['Re']:g} alpha={w['alpha']} dt={w['dt']} amp={w['amplitude']}"),
+        "grid": f"{3 * w['K']}x{3 * w['M']} (z x theta) per radial point",
+        "dof": dof(w),
+        "precision": "fp64" if precision == 0 else "mixed (fp32 transforms, fp64 solves)",
+        "l2": "flushed (256 MB write) before every timed step",
+        "parallelism": "replicas (one trajectory per GPU)",
+    }
+
+
+# ------------------------------------------------------------------ algorithmic costs
+def kernel_costs(w):
+    """Algorithmic flops (FP64 path) and bytes per launch, per kernel.
+
+    FFT flops use 2.5 n log2 n per real 2-D transform of n = 9KM points,
+    split between z (log2 3K) and theta (log2 3M) parts; bytes are the
+    spectral/intermediate arrays each launch must read and write once."""
+    N, K, M = w["N"], w["K"], w["M"]
+    nz, nth, nk = 3 * K, 3 * M, 2 * K - 1
+    n = nz * nth
+    F = N * nk * M  # complex per spectral field
+    P = N * nz * M  # complex per half-physical field
+    lz, lt = math.log2(nz), math.log2(nth)
+    # banded solve per real RHS: forward nl_i, backward nu_i + 1 (multiply by 1/U_ii)
+    lo = [min(max(i - 4, 0), N - 9) for i in range(N)]
+    fwd = sum(2 * (i - lo[i]) for i in range(N))
+    bwd = sum(2 * (min(i + 4, N - 1) - i) + 1 for i in range(N))
+    solve_flops_per_rhs = fwd + bwd
+    modes = nk * M
+    solve = modes * (2 * (solve_flops_per_rhs + 2 * 9 * N + 10 * N)  # pressure: div N + solve
+                     + 6 * (solve_flops_per_rhs + 2 * 9 * N + 6 * N))  # velocity: grad p + rhs + solve
+    return {
+        "curl": {"flops": F * (2 * 9 * 4 + 30), "bytes": 16 * (3 * F + 6 * F)},
+        "zsynth": {"flops": 6 * N * 2.5 * n * lz, "bytes": 16 * (6 * F + 6 * P)},
+        "product": {"flops": 9 * N * 2.5 * n * lt + 9 * N * n, "bytes": 16 * (6 * P + 3 * P)},
+        "zanalysis": {"flops": 3 * N * 2.5 * n * lz, "bytes": 16 * (3 * P + 3 * F)},
+        "solve": {"flops": solve, "bytes": 16 * (3 * F * 3 + 3 * F)},
+    }
+
+
+def step_algorithmic_bytes(w, precision):
+    """Minimum HBM bytes per step: spectral fields only (528 F FP64, 432 F mixed)."""
+    F = w["N"] * (2 * w["K"] - 1) * w["M"]
+    return (528 if precision == 0 else 432) * F
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 peak from unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = max(smax, float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def oracle_timing(seconds_budget=20.0, max_steps=None):
+    """Time the CPU oracle (single thread) on the same workload in a fresh
+    process; returns (steps/s, steps timed, setup seconds)."""
+    budget = seconds_budget
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+from oracle.opf_oracle import Oracle, Params
+from paper_1705_03838_gb300 import inputs
+w = inputs.WORKLOADS[{WORKLOAD!r}]
+o = Oracle(Params(w['N'], w['K'], w['M'], w['m_p'], w['alpha'], w['Re'], w['dt']))
+U = inputs.workload_state({WORKLOAD!r})
+t0 = time.time(); U = o.step(U, 1); setup = time.time() - t0
+n = 0; t0 = time.time()
+while True:
+    U = o.step(U, 1); n += 1
+    el = time.time() - t0
+    if el > {budget} or ({max_steps!r} is not None and n >= {max_steps!r}):
+        break
+print(json.dumps({{"steps": n, "seconds": el, "setup": setup}}))
+"""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    return res["steps"] / res["seconds"], res["steps"], res["setup"], res["seconds"]
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = None
+    # bounded sample: as many full oracle steps as fit in ~2 minutes, at most K
+    sps, n, setup, secs = oracle_timing(seconds_budget=min(120.0, 1.0 + 0.7 * args.steps),
+                                        max_steps=args.steps)
+    gd = dof(w)
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": sps,
+        "unit": "timesteps/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1000.0 / sps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": config_dict(w, 0),
+        "gdof_steps_per_s": sps * gd / 1e9,
+        "cpu_baseline": {"value": sps, "unit": "timesteps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n} full oracle steps of the medium workload after 1 setup step "
+                                   f"({setup:.1f} s, LU factorisation), {secs:.1f} s"},
+        "e2e": {"value": sps, "unit": "timesteps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, w):
+    import numpy as np
+    import torch
+
+    from paper_1705_03838_gb300 import build as _build, inputs, opf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not _build.up_to_date():
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    h = opf.opf_create(w["N"], w["K"], w["M"], w["m_p"], w["alpha"], w["Re"], w["dt"])
+    opf.opf_set_stream(h, stream.cuda_stream)
+    if args.precision:
+        opf.opf_set_option(h, "precision", args.precision)
+    # each replica runs its own seeded trajectory
+    U0 = inputs.seeded_state(w["N"], w["K"], w["M"], w["m_p"], w["alpha"], w["amplitude"],
+                             w["seed"] + rank, w["envelope"])
+    opf.opf_set_state(h, U0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # warm-up (builds the CUDA graph)
+    for _ in range(args.warmup):
+        flush.zero_()
+        opf.opf_step(h, 1)
+    opf.opf_set_option(h, "timing", 1)
+    opf.opf_step(h, 1)  # capture the timed graph outside the timed region
+    opf.opf_kernel_times(h, reset=True)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.time()
+    for i in range(args.steps):
+        flush.zero_()
+        ev0[i].record(stream)
+        opf.opf_step(h, 1)
+        ev1[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.time() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_ms = sum(step_ms)
+    ktimes = opf.opf_kernel_times(h, reset=True)
+    opf.opf_set_option(h, "timing", 0)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # end-to-end through the public API with host buffers: per step, copy the
+    # state in from pinned memory, advance one step, read E, I, D back.
+    pinned = torch.from_numpy(U0.view(np.float64).copy()).pin_memory()
+    e2e_steps = max(3, min(args.steps, 50))
+    opf.opf_step(h, 1)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    for _ in range(e2e_steps):
+        opf.lib().opf_set_state(h.ptr, pinned.data_ptr())
+        opf.opf_step(h, 1)
+        E = opf.opf_energy(h)
+    torch.cuda.synchronize()
+    e2e_s = time.time() - t0
+    e2e_rate = e2e_steps / e2e_s
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_rate = e2e_steps * world / float(t.item())
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    value = args.steps * world / (total_ms / 1000.0)
+    peaks, peak_kind = load_peaks()
+    costs = kernel_costs(w)
+    # dominant kernel by device time over the timed region
+    dom = max(ktimes, key=lambda k: ktimes[k][0])
+    dom_ms = ktimes[dom][0] / max(1, ktimes[dom][1])
+    achieved = costs[dom]["flops"] / (dom_ms * 1e-3) / 1e12
+    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "FP64 from unit counts (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+            "launch_ms": dom_ms,
+            "share": {k: v[0] / sum(x[0] for x in ktimes.values()) for k, v in ktimes.items()}}
+    hbm_frac = step_algorithmic_bytes(w, args.precision) * value / world / (peaks["hbm_gbs"] * 1e9)
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        sps, n, setup, secs = oracle_timing(seconds_budget=15.0)
+        cpu = {"value": sps, "unit": "timesteps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} full oracle steps of the same workload after 1 setup step "
+                         f"({setup:.1f} s), {secs:.1f} s, single thread"}
+    launches_per_step = 5 * 2  # 4 nonlinear-term kernels + 1 solve, predictor + corrector
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "timesteps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.precision == 0 else "f32+f64",
+        "data": "synthetic",
+        "config": config_dict(w, args.precision),
+        "gdof_steps_per_s": value * dof(w) / 1e9,
+        "hbm_roofline_frac": hbm_frac,
+        "hbm_peak_gbs": peaks["hbm_gbs"],
+        "hbm_peak_source": peak_kind,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_rate, "unit": "timesteps/s",
+                "h2d_bytes_per_step": int(U0.nbytes), "d2h_bytes_per_step": 24},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "wall_s_timed_region": wall,
+        "energy_EID": [float(x) for x in E],
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    w = workload_params()
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

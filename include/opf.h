@@ -1,0 +1,138 @@
+/*
+ * opf.h -- C ABI of libopf.so, a GB300 (sm_103a) implementation of the
+ * pipe-flow Navier-Stokes time step described in Willis (2017), "The
+ * Openpipeflow Navier-Stokes solver", SoftwareX 6:124-127.
+ *
+ * Problem (paper section 2): incompressible flow in the periodic pipe
+ * (r, theta, z) in [0,1] x [0, 2pi/m_p) x [0, 2pi/alpha), lengths in units of
+ * the radius R and velocities in units of the laminar centre-line speed,
+ * Re = U_cl R / nu (= D U_bulk / nu, section 1).  Each field is expanded as in
+ * Eq. 1:  A(r,theta,z) = sum_{|k|<K} sum_{|m|<M} A_km(r_n) e^{i(alpha k z + m_p m theta)},
+ * n = 1..N radial points, negative m by complex conjugation.
+ *
+ * STATE LAYOUT (all host/device state buffers below): interleaved complex
+ * double, array [3][M][2K-1][N] = (u_r, u_theta, u_z)[m][k + K - 1][n],
+ * n fastest, r_N = 1 is the wall.  The state is the TOTAL velocity (the
+ * laminar profile 1 - r^2 sits in the (k,m) = (0,0) u_z coefficient).
+ * Size in doubles: 2 * 3 * M * (2K-1) * N.
+ *
+ * ERRORS: every int-returning call returns OPF_OK (0) or a negative code; the
+ * reason is available from opf_last_error() (thread-local, library-owned
+ * string, valid until the next failing call on the same thread).
+ * Buffers passed in are owned by the caller and only read/written during the
+ * call.  Calls on one handle must not overlap; different handles are
+ * independent.  All compute runs on the CUDA device current at opf_create.
+ */
+#ifndef OPF_H
+#define OPF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OPF_OK 0
+#define OPF_EINVAL -1   /* bad argument (NULL, size, unknown option) */
+#define OPF_ECUDA -2    /* a CUDA runtime call failed */
+#define OPF_ENAN -3     /* non-finite values in a state */
+#define OPF_ETIMEOUT -4 /* a bounded device-side wait expired */
+#define OPF_ENOMEM -5   /* device or host allocation failed */
+
+typedef struct opf_ctx opf_t; /* opaque; owned by the library */
+
+/* Create a solver for resolution (N, K, M), rotational symmetry m_p, axial
+ * wavenumber alpha, Reynolds number Re and time step dt (paper section 2).
+ * Builds the radial mesh (Chebyshev-clustered points, section 2), the 9-point
+ * finite-difference operators, one banded LU factorisation per radial
+ * operator (section 2.2), the influence-matrix boundary data (section 2) and
+ * the fixed-flux response, and allocates device memory.  Requires N >= 9,
+ * K >= 1, M >= 1, m_p >= 1, alpha > 0, Re > 0, dt > 0, and 3K, 3M with no
+ * prime factor other than 2, 3, 5.  Returns NULL on failure (opf_last_error). */
+opf_t* opf_create(int N, int K, int M, int m_p, double alpha, double Re, double dt);
+
+/* Release the handle and its device memory.  NULL is ignored. */
+void opf_destroy(opf_t* h);
+
+/* Reason for the last failing call on this thread ("" if none). */
+const char* opf_last_error(void);
+
+/* Load a state from a host buffer (layout above).  The m = 0 coefficients are
+ * projected onto Hermitian symmetry A(-k,0) = conj A(k,0) (real fields).
+ * OPF_ENAN if the buffer holds a NaN/Inf (the previous state is kept). */
+int opf_set_state(opf_t* h, const double* coeffs);
+
+/* Copy the current state into a host buffer (layout above). */
+int opf_get_state(opf_t* h, double* coeffs);
+
+/* Same as opf_set_state / opf_get_state with DEVICE pointers (layout above),
+ * for callers that keep states resident on the GPU. */
+int opf_set_state_device(opf_t* h, const double* d_coeffs);
+int opf_get_state_device(opf_t* h, double* d_coeffs);
+
+/* Advance n >= 0 time steps of the second-order predictor-corrector
+ * (section 2): per step the nonlinear term u x omega is evaluated
+ * pseudo-spectrally on the 3K x 3M grid (section 2.2), then for every Fourier
+ * mode a pressure-Poisson solve and implicit viscous solves for
+ * u+- = u_r +- i u_theta and u_z (banded LU, section 2.2), the
+ * influence-matrix correction that zeroes the boundary vector g (no-slip and
+ * wall divergence, section 2), and the fixed-flux correction (section 1).
+ * Synchronous: returns when the steps are complete.  OPF_ENAN if the state
+ * became non-finite (detected when opf_energy/opf_check runs). */
+int opf_step(opf_t* h, int n);
+
+/* Kinetic energy E, energy input I and dissipation D, each normalised by its
+ * laminar value (section 3.2, the columns of vel_totEID.dat):
+ * out[0] = E/E_lam, out[1] = I/I_lam, out[2] = D/D_lam.  OPF_ENAN if any of
+ * them is not finite. */
+int opf_energy(opf_t* h, double out[3]);
+
+/* Boundary residuals of the current state: out[0] = max |u(r=1)| over all
+ * modes and components, out[1] = max |div u (r=1)| over modes (k,m) != (0,0)
+ * (the vector g of section 2). */
+int opf_wall_residual(opf_t* h, double out[2]);
+
+/* Evaluate the nonlinear term N = u x omega (+ the base axial forcing 4/Re in
+ * the (0,0) mode) of a host state, pseudo-spectrally with 3/2 dealiasing
+ * (section 2), writing N in the state layout (N_r, N_theta, N_z) to a host
+ * buffer.  The handle's current state is not modified. */
+int opf_nonlinear(opf_t* h, const double* coeffs, double* out);
+
+/* Options:
+ *   "precision": 0 = FP64 throughout (default), 1 = mixed (FP32 transforms and
+ *                product, FP64 radial solves and boundary correction)
+ *   "n_corr":    corrector iterations per step (default 1)
+ *   "graph":     1 = replay the step as a CUDA graph (default), 0 = plain launches
+ * Unknown keys or out-of-range values: OPF_EINVAL. */
+int opf_set_option(opf_t* h, const char* key, double value);
+int opf_get_option(opf_t* h, const char* key, double* value);
+
+/* Time step, simulated time, and the excess pressure gradient beta of the
+ * last step (driving force (4/Re)(1 + beta), fixed flux). */
+int opf_get_dt(opf_t* h, double* dt);
+int opf_get_time(opf_t* h, double* t);
+int opf_get_beta(opf_t* h, double* beta);
+
+/* Launch subsequent work on this CUDA stream (a cudaStream_t; NULL = the
+ * library's own stream).  The caller keeps the stream alive while in use. */
+int opf_set_stream(opf_t* h, void* stream);
+
+/* Per-kernel device time of the steps run since the last call with reset=1:
+ * names[i] (library-owned) and total_ms[i], launches[i] for i < *count
+ * (capacity cap).  Collected only while option "timing" = 1. */
+int opf_kernel_times(opf_t* h, int cap, int* count, const char** names,
+                     double* total_ms, int* launches, int reset);
+
+/* Host-only diagnostics (no GPU needed): build the radial setup that
+ * opf_create would build for these parameters and copy one array into
+ * out[0..cap).  what = "r" (N radial points), "wq" (N quadrature weights,
+ * sum wq f ~ int_0^1 f r dr for even f), "d1" / "d2" ([2][N][9] first/second
+ * derivative stencils, [0] = even axis parity, [1] = odd, row n against
+ * columns clamp(n-4, 0, N-9) + t), "G" (N, fixed-flux response),
+ * "basis" ([K][M][6][N] influence-matrix responses).  *len receives the
+ * full length; OPF_EINVAL if cap is too small or what is unknown. */
+int opf_setup_query(int N, int K, int M, int m_p, double alpha, double Re, double dt,
+                    const char* what, double* out, long cap, long* len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OPF_H */

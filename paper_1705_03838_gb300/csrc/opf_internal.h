@@ -1,0 +1,108 @@
+// Internal declarations of libopf: host setup data, device buffers, kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/opf.h"
+
+namespace opf {
+
+constexpr int kStencil = 9;   // 9-point radial finite differences (section 2)
+constexpr int kLuSlots = 13;  // per LU row: 8 L entries, 1/U_ii, 4 U entries
+constexpr int kMaxRadix = 8;  // FFT plans: at most 8 stages of radix 2/3/4/5
+
+// Mixed-radix plan for one transform length (Stockham, radices 2, 3, 4, 5).
+struct FftPlan {
+  int n;
+  int nst;
+  int rad[kMaxRadix];
+};
+
+bool make_plan(int n, FftPlan* p);
+
+// ---------------------------------------------------------------- host setup
+// Everything the device path needs that does not change during stepping
+// (rebuilt only when dt or c changes).  Written independently of the CPU
+// oracle: Fornberg recursion for the stencils, pivot-free banded LU.
+struct Setup {
+  int N = 0, K = 0, M = 0, m_p = 1;
+  double alpha = 0, Re = 0, dt = 0, c = 0.5;
+  std::vector<double> r, rinv;
+  std::vector<double> d1;     // [2 parity: 0 even, 1 odd][N][9] first derivative
+  std::vector<double> d2;     // same layout, second derivative
+  std::vector<double> wq;     // quadrature: sum wq f ~ int_0^1 f r dr (f even)
+  int nJ = 0;                 // number of distinct |j| used by Helmholtz operators
+  std::vector<int> jidx;      // |j| -> compact index (or -1)
+  std::vector<int> hop;       // [M][3] compact |j| index for (m, field u+,u-,u_z)
+  std::vector<double> luH;    // [K][nJ][N][13]   Helmholtz (Dirichlet wall row)
+  std::vector<double> luP;    // [K*M + 1][N][13] Poisson (Neumann wall row);
+                              // the extra last operator is (0,0) with p(1) = 0
+  std::vector<double> basis;  // [K][M][6][N] influence-matrix responses
+  std::vector<double> ainv;   // [M][2K-1][16][2] inverse influence matrices
+  std::vector<double> G;      // fixed-flux response of the (0,0) axial mode
+  double flux_G = 0;          // 2 pi sum wq G
+};
+
+bool build_setup(Setup* s, std::string* err);
+
+// --------------------------------------------------------------- device side
+struct DevSetup {
+  double* rinv = nullptr;
+  double* d1 = nullptr;
+  double* wq = nullptr;
+  int* hop = nullptr;
+  double* luH = nullptr;
+  double* luP = nullptr;
+  double* basis = nullptr;
+  double2* ainv = nullptr;
+  double* G = nullptr;
+  double2* tw_z = nullptr;   // e^{+2 pi i t / nz}, t < nz
+  double2* tw_th = nullptr;  // e^{+2 pi i t / nth}
+  float2* tw_z32 = nullptr;
+  float2* tw_th32 = nullptr;
+};
+
+// Spectral fields are stored [field][m][n][kk] (kk = k + K - 1 fastest).
+// Physical-in-z intermediates are stored [field][n][z][m] (m fastest).
+struct Dims {
+  int N, K, M, m_p, nk, nz, nth;
+  double alpha, Re, dt, c;
+  long F;         // complex values per spectral field = M * N * nk
+  int mcz, mca;   // m columns per block: z synthesis, z analysis
+  int zc;         // z rows per block in the theta/product kernel
+};
+
+void choose_chunks(Dims* d);
+bool prepare_kernel_attrs(const Dims& d);
+void prepare_solve_attrs(const Dims& d);
+
+// Launch wrappers (kernels live in opf_kernels.cu).
+void launch_abi_to_internal(const Dims& d, const double2* abi, double2* U, cudaStream_t st);
+void launch_internal_to_abi(const Dims& d, const double2* U, double2* abi, int components_rtz,
+                            cudaStream_t st);
+void launch_curl(const Dims& d, const DevSetup& s, const double2* U, double2* W6, cudaStream_t st);
+void launch_zsynth(const Dims& d, const DevSetup& s, const FftPlan& pz, const double2* W6,
+                   double2* Z6, cudaStream_t st);
+void launch_product(const Dims& d, const DevSetup& s, const FftPlan& pth, const double2* Z6,
+                    double2* ZN, cudaStream_t st);
+void launch_zanalysis(const Dims& d, const DevSetup& s, const FftPlan& pz, const double2* ZN,
+                      double2* Nout, cudaStream_t st);
+struct SolveArgs {
+  const double2* Uj;
+  const double2* Na;
+  const double2* Nb;
+  double wa, wb;
+  double2* Uout;
+  double* beta_p;  // device scalar: beta' of this solve (written by the (0,0) mode)
+};
+void launch_solve(const Dims& d, const DevSetup& s, const SolveArgs& a, double sumwG, int nJ,
+                  cudaStream_t st);
+void launch_energy(const Dims& d, const DevSetup& s, const double2* U, const double2* W6,
+                   const double* beta_p, double* partial, int nblk, double* out3, cudaStream_t st);
+int energy_blocks(const Dims& d);
+void launch_wall(const Dims& d, const DevSetup& s, const double2* U, double* out2, cudaStream_t st);
+void launch_nan_check(const double* x, long n, int* flag, cudaStream_t st);
+
+}  // namespace opf

@@ -1,0 +1,654 @@
+// Device kernels of the pipe-flow time step (paper section 2).
+//
+// Nonlinear term (section 2.2, evaluated pseudo-spectrally):
+//   k_curl      spectral u+-, u_z -> (u_r, u_theta, u_z, w_r, w_theta, w_z)
+//   k_zsynth    inverse FFT in z (2K-1 modes zero-padded to 3K points)
+//   k_product   per (r, z) row: C2R in theta (M modes -> 3M points), u x w,
+//               R2C in theta keeping m < M
+//   k_zanalysis forward FFT in z keeping |k| < K, 1/(3K 3M) scaling,
+//               (N_r, N_theta) -> N+-, base forcing 4/Re on the (0,0) mode
+// Linear part (section 2.2, banded LU per Fourier mode; section 2 influence
+// matrix): k_solve, one block per tile of T modes at fixed m.
+#include <cstdio>
+
+#include "opf_fft.cuh"
+#include "opf_internal.h"
+
+namespace opf {
+
+__device__ __forceinline__ int row_lo_d(int i, int N) { return min(max(i - 4, 0), N - 9); }
+
+// ------------------------------------------------------------------ ABI <-> internal
+// abi: [3][M][nk][N] (u_r, u_theta, u_z); internal: [3][M][N][nk] (u+, u-, u_z).
+__global__ void k_abi_to_internal(Dims d, const double2* __restrict__ abi, double2* __restrict__ U) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= d.F) return;
+  const int n = idx % d.N;
+  const long t = idx / d.N;
+  const int kk = t % d.nk;
+  const int m = t / d.nk;
+  const long fs = d.F;
+  auto ld = [&](int c, int kq) { return abi[c * fs + ((long)m * d.nk + kq) * d.N + n]; };
+  double2 ur = ld(0, kk), ut = ld(1, kk), uz = ld(2, kk);
+  if (m == 0) {  // Hermitian projection A(-k,0) = conj A(k,0)
+    const int kq = d.nk - 1 - kk;
+    const double2 vr = ld(0, kq), vt = ld(1, kq), vz = ld(2, kq);
+    ur = double2{0.5 * (ur.x + vr.x), 0.5 * (ur.y - vr.y)};
+    ut = double2{0.5 * (ut.x + vt.x), 0.5 * (ut.y - vt.y)};
+    uz = double2{0.5 * (uz.x + vz.x), 0.5 * (uz.y - vz.y)};
+  }
+  const long o = ((long)m * d.N + n) * d.nk + kk;
+  U[0 * fs + o] = double2{ur.x - ut.y, ur.y + ut.x};  // u+ = u_r + i u_theta
+  U[1 * fs + o] = double2{ur.x + ut.y, ur.y - ut.x};  // u- = u_r - i u_theta
+  U[2 * fs + o] = uz;
+}
+
+__global__ void k_internal_to_abi(Dims d, const double2* __restrict__ U, double2* __restrict__ abi) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= d.F) return;
+  const int n = idx % d.N;
+  const long t = idx / d.N;
+  const int kk = t % d.nk;
+  const int m = t / d.nk;
+  const long fs = d.F;
+  const long i = ((long)m * d.N + n) * d.nk + kk;
+  const double2 a = U[i], b = U[fs + i];
+  const long o = ((long)m * d.nk + kk) * d.N + n;
+  abi[o] = double2{0.5 * (a.x + b.x), 0.5 * (a.y + b.y)};           // u_r
+  abi[fs + o] = double2{0.5 * (a.y - b.y), -0.5 * (a.x - b.x)};      // u_theta
+  abi[2 * fs + o] = U[2 * fs + i];
+}
+
+void launch_abi_to_internal(const Dims& d, const double2* abi, double2* U, cudaStream_t st) {
+  const int nb = (int)((d.F + 255) / 256);
+  k_abi_to_internal<<<nb, 256, 0, st>>>(d, abi, U);
+}
+void launch_internal_to_abi(const Dims& d, const double2* U, double2* abi, int, cudaStream_t st) {
+  const int nb = (int)((d.F + 255) / 256);
+  k_internal_to_abi<<<nb, 256, 0, st>>>(d, U, abi);
+}
+
+// ------------------------------------------------------------------ curl (A1)
+template <typename V>
+__global__ void __launch_bounds__(256) k_curl(Dims d, const double* __restrict__ d1,
+                                              const double* __restrict__ rinv,
+                                              const double2* __restrict__ U, V* __restrict__ W6) {
+  using T = typename Scalar<V>::T;
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= d.F) return;
+  const int kk = idx % d.nk;
+  const long t = idx / d.nk;
+  const int n = t % d.N;
+  const int m = t / d.N;
+  const int N = d.N, nk = d.nk;
+  const long fs = d.F;
+  const int mt = d.m_p * m;
+  const double ak = d.alpha * (kk - (d.K - 1));
+  const int ps = mt & 1, pv = ps ^ 1;
+  const double2* up = U + ((long)m * N) * nk + kk;
+  const double2* um = up + fs;
+  const double2* uz = up + 2 * fs;
+  const int lo = row_lo_d(n, N);
+  const double* wv = d1 + ((long)pv * N + n) * 9;
+  const double* ws = d1 + ((long)ps * N + n) * 9;
+  double dtx = 0, dty = 0, dzx = 0, dzy = 0;  // d/dr of u_theta and u_z
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    const long o = (long)(lo + q) * nk;
+    const double2 a = up[o], b = um[o], c = uz[o];
+    dtx += wv[q] * 0.5 * (a.y - b.y);
+    dty -= wv[q] * 0.5 * (a.x - b.x);
+    dzx += ws[q] * c.x;
+    dzy += ws[q] * c.y;
+  }
+  const long o = (long)n * nk;
+  const double2 a = up[o], b = um[o], c = uz[o];
+  const double urx = 0.5 * (a.x + b.x), ury = 0.5 * (a.y + b.y);
+  const double utx = 0.5 * (a.y - b.y), uty = -0.5 * (a.x - b.x);
+  const double ri = rinv[n];
+  // w_r = i (m~ u_z / r - ak u_theta)
+  const double xr = mt * ri * c.x - ak * utx, xi = mt * ri * c.y - ak * uty;
+  // w_theta = i ak u_r - d_r u_z
+  const double wtx = -ak * ury - dzx, wty = ak * urx - dzy;
+  // w_z = d_r u_theta + u_theta / r - i m~ u_r / r
+  const double wzx = dtx + ri * utx + mt * ri * ury, wzy = dty + ri * uty - mt * ri * urx;
+  const long w = ((long)m * N + n) * nk + kk;
+  W6[0 * fs + w] = V{(T)urx, (T)ury};
+  W6[1 * fs + w] = V{(T)utx, (T)uty};
+  W6[2 * fs + w] = V{(T)c.x, (T)c.y};
+  W6[3 * fs + w] = V{(T)(-xi), (T)xr};
+  W6[4 * fs + w] = V{(T)wtx, (T)wty};
+  W6[5 * fs + w] = V{(T)wzx, (T)wzy};
+}
+
+void launch_curl(const Dims& d, const DevSetup& s, const double2* U, double2* W6, cudaStream_t st) {
+  const int nb = (int)((d.F + 255) / 256);
+  k_curl<double2><<<nb, 256, 0, st>>>(d, s.d1, s.rinv, U, W6);
+}
+
+// ------------------------------------------------------------------ z synthesis (A2)
+
+template <typename V>
+__global__ void __launch_bounds__(128) k_zsynth(Dims d, FftPlan pz, const V* __restrict__ twz,
+                                                const V* __restrict__ W6, V* __restrict__ Z6) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nz = d.nz, ld = nz + 1, MC = d.mcz;
+  V* A = (V*)smraw;
+  V* B = A + MC * ld;
+  V* tw = B + MC * ld;
+  const int m0 = blockIdx.x * MC, n = blockIdx.y, f = blockIdx.z;
+  const int K = d.K;
+  for (int e = threadIdx.x; e < nz; e += blockDim.x) tw[e] = twz[e];
+  const long fs = d.F;
+  for (int e = threadIdx.x; e < MC * nz; e += blockDim.x) {
+    const int z = e % nz, mc = e / nz, m = m0 + mc;
+    int k = z < K ? z : z - nz;
+    V v = V{0, 0};
+    if (m < d.M && (z < K || z > nz - K)) v = W6[f * fs + ((long)m * d.N + n) * d.nk + k + K - 1];
+    A[mc * ld + z] = v;
+  }
+  __syncthreads();
+  const V* res = block_fft(A, B, MC, ld, pz, tw, +1);
+  const int mcn = min(MC, d.M - m0);
+  for (int e = threadIdx.x; e < mcn * nz; e += blockDim.x) {
+    const int mc = e % mcn, z = e / mcn;
+    Z6[(((long)f * d.N + n) * nz + z) * d.M + m0 + mc] = res[mc * ld + z];
+  }
+}
+
+size_t zsynth_smem(const Dims& d, int mc, size_t vb) { return (2 * (size_t)mc * (d.nz + 1) + d.nz) * vb; }
+
+void launch_zsynth(const Dims& d, const DevSetup& s, const FftPlan& pz, const double2* W6,
+                   double2* Z6, cudaStream_t st) {
+  dim3 g((d.M + d.mcz - 1) / d.mcz, d.N, 6);
+  k_zsynth<double2><<<g, 128, zsynth_smem(d, d.mcz, sizeof(double2)), st>>>(d, pz, s.tw_z, W6, Z6);
+}
+
+// ------------------------------------------------------------------ product (A3)
+
+template <typename V>
+__global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* __restrict__ twth,
+                                                 const V* __restrict__ Z6, V* __restrict__ ZN) {
+  using T = typename Scalar<V>::T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nth = d.nth, ld = nth, M = d.M;
+  const int ZC = d.zc;
+  V* A = (V*)smraw;            // 3 * ZC sequences
+  V* B = A + 3 * ZC * ld;      // 3 * ZC sequences
+  V* tw = B + 3 * ZC * ld;
+  const int z0 = blockIdx.x * ZC, n = blockIdx.y, nz = d.nz;
+  const int zc = min(ZC, nz - z0);
+  for (int e = threadIdx.x; e < nth; e += blockDim.x) tw[e] = twth[e];
+  const long fstride = (long)d.N * nz * M;
+  // spectra of the pairs (u_r,u_t), (u_z,w_r), (w_t,w_z):  Z = A + i B
+  for (int e = threadIdx.x; e < zc * 3 * nth; e += blockDim.x) {
+    const int q = e % nth, pr = (e / nth) % 3, zr = e / (3 * nth);
+    const long rowa = ((long)(2 * pr) * d.N + n) * nz + z0 + zr;
+    V v = V{0, 0};
+    if (q < M) {
+      V a = Z6[rowa * M + q], b = Z6[(rowa + (long)d.N * nz) * M + q];
+      if (q == 0) { a.y = 0; b.y = 0; }
+      v = V{a.x - b.y, a.y + b.x};
+    } else if (q > nth - M) {
+      const int m = nth - q;
+      const V a = Z6[rowa * M + m], b = Z6[(rowa + (long)d.N * nz) * M + m];
+      v = V{a.x + b.y, -a.y + b.x};  // conj(a) + i conj(b)
+    }
+    A[(zr * 3 + pr) * ld + q] = v;
+  }
+  __syncthreads();
+  V* res = block_fft(A, B, 3 * zc, ld, pth, tw, +1);
+  V* C = (res == A) ? B : A;
+  for (int e = threadIdx.x; e < zc * nth; e += blockDim.x) {
+    const int q = e % nth, zr = e / nth;
+    const V x0 = res[(zr * 3 + 0) * ld + q], x1 = res[(zr * 3 + 1) * ld + q], x2 = res[(zr * 3 + 2) * ld + q];
+    const T ur = x0.x, ut = x0.y, uz = x1.x, wr = x1.y, wt = x2.x, wz = x2.y;
+    C[(zr * 2 + 0) * ld + q] = V{ut * wz - uz * wt, uz * wr - ur * wz};
+    C[(zr * 2 + 1) * ld + q] = V{ur * wt - ut * wr, (T)0};
+  }
+  __syncthreads();
+  V* D = (C == A) ? B : A;
+  const V* out = block_fft(C, D, 2 * zc, ld, pth, tw, -1);
+  for (int e = threadIdx.x; e < zc * M; e += blockDim.x) {
+    const int m = e % M, zr = e / M;
+    const V y = out[(zr * 2 + 0) * ld + m];
+    const V yc = out[(zr * 2 + 0) * ld + (m == 0 ? 0 : nth - m)];
+    const V nr = V{(T)0.5 * (y.x + yc.x), (T)0.5 * (y.y - yc.y)};
+    const V nt = V{(T)0.5 * (y.y + yc.y), (T)-0.5 * (y.x - yc.x)};
+    const long row = ((long)n * nz + z0 + zr) * M + m;
+    ZN[row] = nr;
+    ZN[fstride + row] = nt;
+    ZN[2 * fstride + row] = out[(zr * 2 + 1) * ld + m];
+  }
+}
+
+size_t product_smem(const Dims& d, int zc, size_t vb) { return (2 * 3 * (size_t)zc * d.nth + d.nth) * vb; }
+
+void launch_product(const Dims& d, const DevSetup& s, const FftPlan& pth, const double2* Z6,
+                    double2* ZN, cudaStream_t st) {
+  dim3 g((d.nz + d.zc - 1) / d.zc, d.N);
+  k_product<double2><<<g, 128, product_smem(d, d.zc, sizeof(double2)), st>>>(d, pth, s.tw_th, Z6, ZN);
+}
+
+// ------------------------------------------------------------------ z analysis (A4)
+template <typename V>
+__global__ void __launch_bounds__(128) k_zanalysis(Dims d, FftPlan pz, const V* __restrict__ twz,
+                                                   const V* __restrict__ ZN, double2* __restrict__ Nout) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nz = d.nz, ld = nz + 1, M = d.M, K = d.K, nk = d.nk;
+  const int MC = d.mca;
+  V* A = (V*)smraw;
+  V* B = A + 3 * MC * ld;
+  V* tw = B + 3 * MC * ld;
+  const int m0 = blockIdx.x * MC, n = blockIdx.y;
+  const int mcn = min(MC, M - m0);
+  for (int e = threadIdx.x; e < nz; e += blockDim.x) tw[e] = twz[e];
+  const long fstride = (long)d.N * nz * M;
+  for (int e = threadIdx.x; e < 3 * MC * nz; e += blockDim.x) {
+    const int mc = e % MC, z = (e / MC) % nz, f = e / (MC * nz);
+    V v = V{0, 0};
+    if (mc < mcn) v = ZN[f * fstride + ((long)n * nz + z) * M + m0 + mc];
+    A[(f * MC + mc) * ld + z] = v;
+  }
+  __syncthreads();
+  const V* res = block_fft(A, B, 3 * MC, ld, pz, tw, -1);
+  const double sc = 1.0 / ((double)nz * d.nth);
+  const long fs = d.F;
+  for (int e = threadIdx.x; e < mcn * nk; e += blockDim.x) {
+    const int kk = e % nk, mc = e / nk, m = m0 + mc;
+    const int k = kk - (K - 1);
+    const int zp = k < 0 ? k + nz : k;
+    const V r_ = res[(0 * MC + mc) * ld + zp], t_ = res[(1 * MC + mc) * ld + zp];
+    const V z_ = res[(2 * MC + mc) * ld + zp];
+    const double nrx = sc * r_.x, nry = sc * r_.y, ntx = sc * t_.x, nty = sc * t_.y;
+    double2 nz2 = double2{sc * z_.x, sc * z_.y};
+    if (k == 0 && m == 0) nz2.x += 4.0 / d.Re;  // base driving force (laminar balance)
+    const long o = ((long)m * d.N + n) * nk + kk;
+    Nout[o] = double2{nrx - nty, nry + ntx};           // N+ = N_r + i N_theta
+    Nout[fs + o] = double2{nrx + nty, nry - ntx};      // N- = N_r - i N_theta
+    Nout[2 * fs + o] = nz2;
+  }
+}
+
+size_t zanalysis_smem(const Dims& d, int mc, size_t vb) {
+  return (2 * 3 * (size_t)mc * (d.nz + 1) + d.nz) * vb;
+}
+
+void launch_zanalysis(const Dims& d, const DevSetup& s, const FftPlan& pz, const double2* ZN,
+                      double2* Nout, cudaStream_t st) {
+  dim3 g((d.M + d.mca - 1) / d.mca, d.N);
+  k_zanalysis<double2><<<g, 128, zanalysis_smem(d, d.mca, sizeof(double2)), st>>>(d, pz, s.tw_z, ZN, Nout);
+}
+
+// ------------------------------------------------------------------ linear solve (A5-A7)
+struct SolveDev {
+  const double* d1;
+  const double* rinv;
+  const double* wq;
+  const int* hop;
+  const double* luH;
+  const double* luP;
+  const double* basis;
+  const double2* ainv;
+  const double* G;
+  double sumwG;
+  int nJ;
+};
+
+// One block: T consecutive k at fixed m.  6T threads = (field u+,u-,u_z) x
+// T modes x (re, im); each thread runs one real banded solve.
+template <int T>
+__global__ void __launch_bounds__(6 * T) k_solve(Dims d, SolveDev s, SolveArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int N = d.N, nk = d.nk, M = d.M, K = d.K;
+  double2* NE = (double2*)smraw;      // [3][N][T]  N_eff
+  double2* S = NE + 3 * N * T;        // [N][T]     N+ + N-
+  double2* P = S + N * T;             // [N][T]     pressure
+  double2* coef = P + N * T;          // [T][4]     influence coefficients
+  double* X = (double*)(coef + 4 * T);  // [N][6T] solve vectors
+  const int m = blockIdx.y, kk0 = blockIdx.x * T, tid = threadIdx.x;
+  const int mt = d.m_p * m, ps = mt & 1, pv = ps ^ 1;
+  const double* wv = s.d1 + (long)pv * N * 9;
+  const double* ws = s.d1 + (long)ps * N * 9;
+  const double ci = 1.0 / (d.c * d.dt), cu = (1.0 - d.c) / d.c;
+  const long fs = d.F;
+  const long base = (long)m * N * nk;
+
+  // N_eff = wa Na + wb Nb, and S = N+ + N-
+  for (int e = tid; e < 3 * N * T; e += blockDim.x) {
+    const int mi = e % T, i = (e / T) % N, f = e / (T * N);
+    const int kk = min(kk0 + mi, nk - 1);
+    const long g = f * fs + base + (long)i * nk + kk;
+    const double2 u = a.Na[g];
+    double2 v = double2{a.wa * u.x, a.wa * u.y};
+    if (a.Nb) {
+      const double2 w = a.Nb[g];
+      v.x += a.wb * w.x;
+      v.y += a.wb * w.y;
+    }
+    NE[(f * N + i) * T + mi] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < N * T; e += blockDim.x) {
+    const double2 p = NE[e], q = NE[N * T + e];
+    S[e] = double2{p.x + q.x, p.y + q.y};
+  }
+  __syncthreads();
+
+  // ---- pressure-Poisson: lap p = div N_eff, provisional wall condition dp/dr = 0
+  if (tid < 2 * T) {
+    const int part = tid & 1, mi = tid >> 1;
+    const int kk = min(kk0 + mi, nk - 1);
+    const int k = kk - (K - 1), ik = abs(k);
+    const double ak = d.alpha * k;
+    const int op = (ik == 0 && m == 0) ? K * M : ik * M + m;
+    const double* L = s.luP + (long)op * N * kLuSlots;
+    double* Pp = (double*)P + 2 * mi + part;
+    const double* Sp = (const double*)S + 2 * mi + part;
+    const int st = 2 * T;
+    for (int i = 0; i < N; ++i) {
+      double b = 0.0;
+      if (i < N - 1) {
+        const int lo = row_lo_d(i, N);
+        double acc = 0.0;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) acc += wv[i * 9 + q] * Sp[(lo + q) * st];
+        const double2 np = NE[i * T + mi], nm = NE[(N + i) * T + mi], nz = NE[(2 * N + i) * T + mi];
+        const double ri = 0.5 * s.rinv[i];
+        b = part == 0 ? 0.5 * acc + ri * ((1 + mt) * np.x + (1 - mt) * nm.x) - ak * nz.y
+                      : 0.5 * acc + ri * ((1 + mt) * np.y + (1 - mt) * nm.y) + ak * nz.x;
+      }
+      const double* Lr = L + i * kLuSlots;
+      for (int q = 8 - (i - row_lo_d(i, N)); q < 8; ++q) b -= Lr[q] * Pp[(i - 8 + q) * st];
+      Pp[i * st] = b;
+    }
+    for (int i = N - 1; i >= 0; --i) {
+      const double* Lr = L + i * kLuSlots;
+      double x = Pp[i * st];
+      const int nu = min(i + 4, N - 1) - i;
+      for (int q = 1; q <= nu; ++q) x -= Lr[8 + q] * Pp[(i + q) * st];
+      Pp[i * st] = x * Lr[8];
+    }
+  }
+  __syncthreads();
+
+  // ---- implicit viscous solves: (1/dt - cL) u = R - grad p, Dirichlet 0
+  const int part = tid & 1, mi = (tid >> 1) % T, f = (tid >> 1) / T;
+  const int kk = min(kk0 + mi, nk - 1);
+  const int k = kk - (K - 1), ik = abs(k);
+  const double ak = d.alpha * k;
+  const int st6 = 6 * T;
+  double* Xc = X + tid;
+  const double2* Uj = a.Uj + f * fs + base + kk;
+  {
+    const int op = ik * s.nJ + s.hop[3 * m + f];
+    const double* L = s.luH + (long)op * N * kLuSlots;
+    const double* Pr = (const double*)P + 2 * mi;
+    for (int i = 0; i < N; ++i) {
+      double b = 0.0;
+      if (i < N - 1) {
+        double gp;
+        if (f < 2) {
+          const int lo = row_lo_d(i, N);
+          double acc = 0.0;
+#pragma unroll
+          for (int q = 0; q < 9; ++q) acc += ws[i * 9 + q] * Pr[(lo + q) * 2 * T + part];
+          const double pp = mt * s.rinv[i] * Pr[i * 2 * T + part];
+          gp = f == 0 ? acc - pp : acc + pp;
+        } else {
+          gp = part == 0 ? -ak * Pr[i * 2 * T + 1] : ak * Pr[i * 2 * T];
+        }
+        const double2 u = Uj[(long)i * nk];
+        const double2 ne = NE[(f * N + i) * T + mi];
+        b = ci * (part ? u.y : u.x) + (part ? ne.y : ne.x) - gp;
+      }
+      const double* Lr = L + i * kLuSlots;
+      for (int q = 8 - (i - row_lo_d(i, N)); q < 8; ++q) b -= Lr[q] * Xc[(i - 8 + q) * st6];
+      Xc[i * st6] = b;
+    }
+    for (int i = N - 1; i >= 0; --i) {
+      const double* Lr = L + i * kLuSlots;
+      double x = Xc[i * st6];
+      const int nu = min(i + 4, N - 1) - i;
+      for (int q = 1; q <= nu; ++q) x -= Lr[8 + q] * Xc[(i + q) * st6];
+      Xc[i * st6] = x * Lr[8];
+    }
+    // u = v - ((1-c)/c) u_j, applied only once the back substitution is done
+    for (int i = 0; i < N; ++i) {
+      const double2 u = Uj[(long)i * nk];
+      Xc[i * st6] -= cu * (part ? u.y : u.x);
+    }
+  }
+  __syncthreads();
+
+  // ---- influence matrix: g = (u+(1), u-(1), u_z(1), div u(1)), a = -A^{-1} g
+  if (tid < T && kk0 + tid < nk) {
+    const int mj = tid, kj = kk0 + tid;
+    const double akj = d.alpha * (kj - (K - 1));
+    auto xv = [&](int ff, int i) {
+      const int c = (ff * T + mj) << 1;
+      return double2{X[i * st6 + c], X[i * st6 + c + 1]};
+    };
+    const double2 g0 = xv(0, N - 1), g1 = xv(1, N - 1), g2 = xv(2, N - 1);
+    const int lo = N - 9;
+    double ax = 0.0, ay = 0.0;
+    for (int q = 0; q < 9; ++q) {
+      const double w = wv[(N - 1) * 9 + q];
+      const double2 p = xv(0, lo + q), mm = xv(1, lo + q);
+      ax += w * (p.x + mm.x);
+      ay += w * (p.y + mm.y);
+    }
+    const double ri = 0.5 * s.rinv[N - 1];
+    double2 g[4] = {g0, g1, g2,
+                    double2{0.5 * ax + ri * ((1 + mt) * g0.x + (1 - mt) * g1.x) - akj * g2.y,
+                            0.5 * ay + ri * ((1 + mt) * g0.y + (1 - mt) * g1.y) + akj * g2.x}};
+    const double2* Ai = s.ainv + ((long)m * nk + kj) * 16;
+    for (int r = 0; r < 4; ++r) {
+      double sx = 0.0, sy = 0.0;
+      for (int c = 0; c < 4; ++c) {
+        const double2 A = Ai[r * 4 + c];
+        sx += A.x * g[c].x - A.y * g[c].y;
+        sy += A.x * g[c].y + A.y * g[c].x;
+      }
+      coef[mj * 4 + r] = double2{-sx, -sy};
+    }
+  }
+  __syncthreads();
+
+  // ---- add basis responses, fixed-flux correction of (0,0), write out
+  if (kk0 + mi < nk) {
+    const double* Bv = s.basis + ((long)(ik * M + m) * 6) * N;
+    const double2 a0 = coef[mi * 4 + 0], ax = coef[mi * 4 + 1 + f];
+    const double sk = k > 0 ? 1.0 : (k < 0 ? -1.0 : 0.0);
+    const double c0 = f == 2 ? (part ? sk * a0.x : -sk * a0.y) : (part ? a0.y : a0.x);
+    const double c1 = part ? ax.y : ax.x;
+    const double* b0 = Bv + f * N;
+    const double* b1 = Bv + (3 + f) * N;
+    for (int i = 0; i < N; ++i) Xc[i * st6] += c0 * b0[i] + c1 * b1[i];
+    if (k == 0 && m == 0 && f == 2 && part == 0) {
+      double q = 0.0;
+      for (int i = 0; i < N; ++i) q += s.wq[i] * Xc[i * st6];
+      const double bp = (0.25 - q) / s.sumwG;  // 2 pi int u_z r dr = pi/2
+      for (int i = 0; i < N; ++i) Xc[i * st6] += bp * s.G[i];
+      *a.beta_p = bp;
+    }
+    double* out = (double*)(a.Uout + f * fs + base + kk) + part;
+    for (int i = 0; i < N; ++i) out[(long)i * nk * 2] = Xc[i * st6];
+  }
+}
+
+static size_t solve_smem(int N, int T) { return (size_t)(5 * N * T + 4 * T) * 16 + (size_t)6 * N * T * 8; }
+
+// Chunk sizes keep every transform block within ~96 KB of shared memory (two
+// blocks per SM), then raise each kernel's dynamic shared-memory limit.
+void choose_chunks(Dims* d) {
+  const size_t budget = 96 * 1024, vb = sizeof(double2);
+  d->mcz = 8;
+  while (d->mcz > 1 && zsynth_smem(*d, d->mcz, vb) > budget) d->mcz /= 2;
+  d->mca = 8;
+  while (d->mca > 1 && zanalysis_smem(*d, d->mca, vb) > budget) d->mca /= 2;
+  d->zc = 4;
+  while (d->zc > 1 && product_smem(*d, d->zc, vb) > budget) d->zc /= 2;
+}
+
+bool prepare_kernel_attrs(const Dims& d) {
+  const size_t vb = sizeof(double2);
+  const size_t lim = 227 * 1024;
+  if (zsynth_smem(d, d.mcz, vb) > lim || zanalysis_smem(d, d.mca, vb) > lim ||
+      product_smem(d, d.zc, vb) > lim || solve_smem(d.N, d.N <= 64 ? 16 : (d.N <= 128 ? 8 : 4)) > lim)
+    return false;
+  cudaFuncSetAttribute(k_zsynth<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)zsynth_smem(d, d.mcz, vb));
+  cudaFuncSetAttribute(k_zanalysis<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)zanalysis_smem(d, d.mca, vb));
+  cudaFuncSetAttribute(k_product<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)product_smem(d, d.zc, vb));
+  prepare_solve_attrs(d);
+  return true;
+}
+
+void prepare_solve_attrs(const Dims& d) {
+  cudaFuncSetAttribute(k_solve<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(d.N, 16));
+  cudaFuncSetAttribute(k_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(d.N, 8));
+  cudaFuncSetAttribute(k_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(d.N, 4));
+}
+
+void launch_solve(const Dims& d, const DevSetup& s, const SolveArgs& a, double sumwG, int nJ,
+                  cudaStream_t st) {
+  SolveDev sd{s.d1, s.rinv, s.wq, s.hop, s.luH, s.luP, s.basis, s.ainv, s.G, sumwG, nJ};
+  if (d.N <= 64) {
+    dim3 g((d.nk + 15) / 16, d.M);
+    k_solve<16><<<g, 96, solve_smem(d.N, 16), st>>>(d, sd, a);
+  } else if (d.N <= 128) {
+    dim3 g((d.nk + 7) / 8, d.M);
+    k_solve<8><<<g, 48, solve_smem(d.N, 8), st>>>(d, sd, a);
+  } else {
+    dim3 g((d.nk + 3) / 4, d.M);
+    k_solve<4><<<g, 24, solve_smem(d.N, 4), st>>>(d, sd, a);
+  }
+}
+
+// ------------------------------------------------------------------ diagnostics
+// E/E_lam = 6 sum' w |u|^2, D/D_lam = sum' w |w|^2, I/I_lam = 4 (1 + beta) int u_z00 r dr
+__global__ void __launch_bounds__(256) k_energy(Dims d, const double* __restrict__ wq,
+                                                const double2* __restrict__ W6, double* partial) {
+  __shared__ double su[256], sw[256];
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  double eu = 0.0, ew = 0.0;
+  if (idx < d.F) {
+    const int n = (idx / d.nk) % d.N;
+    const int m = idx / ((long)d.nk * d.N);
+    const double w = (m == 0 ? 1.0 : 2.0) * wq[n];
+    for (int f = 0; f < 3; ++f) {
+      const double2 u = W6[f * d.F + idx], o = W6[(3 + f) * d.F + idx];
+      eu += u.x * u.x + u.y * u.y;
+      ew += o.x * o.x + o.y * o.y;
+    }
+    eu *= w;
+    ew *= w;
+  }
+  su[threadIdx.x] = eu;
+  sw[threadIdx.x] = ew;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      su[threadIdx.x] += su[threadIdx.x + h];
+      sw[threadIdx.x] += sw[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = su[0];
+    partial[2 * blockIdx.x + 1] = sw[0];
+  }
+}
+
+__global__ void k_energy_final(Dims d, const double* __restrict__ partial, int nblk,
+                               const double* __restrict__ wq, const double2* __restrict__ U,
+                               const double* beta_p, double* out3) {
+  __shared__ double su[256], sw[256];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+    a += partial[2 * i];
+    b += partial[2 * i + 1];
+  }
+  su[threadIdx.x] = a;
+  sw[threadIdx.x] = b;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      su[threadIdx.x] += su[threadIdx.x + h];
+      sw[threadIdx.x] += sw[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double flux = 0.0;
+    const double2* uz = U + 2 * d.F + (d.K - 1);  // (k,m) = (0,0), u_z
+    for (int n = 0; n < d.N; ++n) flux += wq[n] * uz[(long)n * d.nk].x;
+    const double beta = *beta_p * d.Re / 4.0;
+    out3[0] = 6.0 * su[0];
+    out3[1] = 4.0 * (1.0 + beta) * flux;
+    out3[2] = sw[0];
+  }
+}
+
+int energy_blocks(const Dims& d) { return (int)((d.F + 255) / 256); }
+
+void launch_energy(const Dims& d, const DevSetup& s, const double2* U, const double2* W6,
+                   const double* beta_p, double* partial, int nblk, double* out3, cudaStream_t st) {
+  k_energy<<<nblk, 256, 0, st>>>(d, s.wq, W6, partial);
+  k_energy_final<<<1, 256, 0, st>>>(d, partial, nblk, s.wq, U, beta_p, out3);
+}
+
+// Boundary vector g of section 2 over all modes: max |u(1)| and max |div u(1)|.
+__global__ void k_wall(Dims d, const double* __restrict__ d1, const double2* __restrict__ U,
+                       unsigned long long* out2) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= d.M * d.nk) return;
+  const int m = idx / d.nk, kk = idx % d.nk, N = d.N;
+  const long fs = d.F;
+  const double2* up = U + ((long)m * N) * d.nk + kk;
+  const double2* um = up + fs;
+  const double2* uz = up + 2 * fs;
+  const long w = (long)(N - 1) * d.nk;
+  const double2 a = up[w], b = um[w], c = uz[w];
+  const double ur = hypot(0.5 * (a.x + b.x), 0.5 * (a.y + b.y));
+  const double ut = hypot(0.5 * (a.y - b.y), 0.5 * (a.x - b.x));
+  const double umax = fmax(fmax(ur, ut), hypot(c.x, c.y));
+  atomicMax(out2, __double_as_longlong(umax));
+  if (m == 0 && kk == d.K - 1) return;
+  const int mt = d.m_p * m;
+  const double ak = d.alpha * (kk - (d.K - 1));
+  const double* wr = d1 + ((long)((mt & 1) ^ 1) * N + N - 1) * 9;
+  double sx = 0.0, sy = 0.0;
+  for (int q = 0; q < 9; ++q) {
+    const long o = (long)(N - 9 + q) * d.nk;
+    sx += wr[q] * (up[o].x + um[o].x);
+    sy += wr[q] * (up[o].y + um[o].y);
+  }
+  const double dx = 0.5 * sx + 0.5 * ((1 + mt) * a.x + (1 - mt) * b.x) - ak * c.y;
+  const double dy = 0.5 * sy + 0.5 * ((1 + mt) * a.y + (1 - mt) * b.y) + ak * c.x;
+  atomicMax(out2 + 1, __double_as_longlong(hypot(dx, dy)));
+}
+
+void launch_wall(const Dims& d, const DevSetup& s, const double2* U, double* out2, cudaStream_t st) {
+  cudaMemsetAsync(out2, 0, 2 * sizeof(double), st);
+  const int nm = d.M * d.nk;
+  k_wall<<<(nm + 127) / 128, 128, 0, st>>>(d, s.d1, U, (unsigned long long*)out2);
+}
+
+__global__ void k_nan(const double* __restrict__ x, long n, int* flag) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) {
+      atomicOr(flag, 1);
+      return;
+    }
+}
+
+void launch_nan_check(const double* x, long n, int* flag, cudaStream_t st) {
+  cudaMemsetAsync(flag, 0, sizeof(int), st);
+  k_nan<<<304, 256, 0, st>>>(x, n, flag);
+}
+
+}  // namespace opf

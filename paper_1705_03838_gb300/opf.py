@@ -1,0 +1,206 @@
+"""Thin ctypes binding of libopf.so (include/opf.h), same names as the C ABI.
+
+Argument marshalling only: every step of the time step runs in the library's
+CUDA kernels.  If the library has not been built this module raises -- there
+is no fallback path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libopf.so")
+
+OPF_OK, OPF_EINVAL, OPF_ECUDA, OPF_ENAN, OPF_ETIMEOUT, OPF_ENOMEM = 0, -1, -2, -3, -4, -5
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class OpfError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"opf error {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load libopf.so once (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                "libopf.so is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d, cp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_char_p
+        L.opf_create.restype = vp
+        L.opf_create.argtypes = [i, i, i, i, d, d, d]
+        L.opf_destroy.restype = None
+        L.opf_destroy.argtypes = [vp]
+        L.opf_last_error.restype = cp
+        L.opf_last_error.argtypes = []
+        for name in ("opf_set_state", "opf_get_state", "opf_set_state_device", "opf_get_state_device"):
+            getattr(L, name).restype = i
+            getattr(L, name).argtypes = [vp, vp]
+        L.opf_step.restype = i
+        L.opf_step.argtypes = [vp, i]
+        L.opf_energy.restype = i
+        L.opf_energy.argtypes = [vp, _dp]
+        L.opf_wall_residual.restype = i
+        L.opf_wall_residual.argtypes = [vp, _dp]
+        L.opf_nonlinear.restype = i
+        L.opf_nonlinear.argtypes = [vp, vp, vp]
+        L.opf_set_option.restype = i
+        L.opf_set_option.argtypes = [vp, cp, d]
+        L.opf_get_option.restype = i
+        L.opf_get_option.argtypes = [vp, cp, _dp]
+        for name in ("opf_get_dt", "opf_get_time", "opf_get_beta"):
+            getattr(L, name).restype = i
+            getattr(L, name).argtypes = [vp, _dp]
+        L.opf_set_stream.restype = i
+        L.opf_set_stream.argtypes = [vp, vp]
+        L.opf_kernel_times.restype = i
+        L.opf_kernel_times.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(cp), _dp,
+                                       ctypes.POINTER(i), i]
+        L.opf_setup_query.restype = i
+        L.opf_setup_query.argtypes = [i, i, i, i, d, d, d, cp, _dp, ctypes.c_long,
+                                      ctypes.POINTER(ctypes.c_long)]
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != OPF_OK:
+        raise OpfError(rc, lib().opf_last_error().decode())
+
+
+class Handle:
+    """Owns an opf_t*; shape information for marshalling."""
+
+    def __init__(self, ptr, N, K, M):
+        self.ptr, self.N, self.K, self.M = ptr, N, K, M
+        self.shape = (3, M, 2 * K - 1, N)
+
+    def __del__(self):
+        try:
+            opf_destroy(self)
+        except Exception:
+            pass
+
+
+def _state_buffer(h, arr):
+    a = np.ascontiguousarray(arr, dtype=np.complex128)
+    if a.shape != h.shape:
+        raise ValueError(f"state must have shape {h.shape}, got {a.shape}")
+    return a
+
+
+def opf_create(N, K, M, m_p, alpha, Re, dt):
+    ptr = lib().opf_create(N, K, M, m_p, alpha, Re, dt)
+    if not ptr:
+        raise OpfError(OPF_EINVAL, lib().opf_last_error().decode())
+    return Handle(ptr, N, K, M)
+
+
+def opf_destroy(h):
+    if h.ptr:
+        lib().opf_destroy(h.ptr)
+        h.ptr = None
+
+
+def opf_set_state(h, state):
+    a = _state_buffer(h, state)
+    _check(lib().opf_set_state(h.ptr, a.ctypes.data))
+
+
+def opf_get_state(h, out=None):
+    out = np.empty(h.shape, dtype=np.complex128) if out is None else out
+    if out.shape != h.shape or out.dtype != np.complex128 or not out.flags.c_contiguous:
+        raise ValueError("output must be a C-contiguous complex128 array of the state shape")
+    _check(lib().opf_get_state(h.ptr, out.ctypes.data))
+    return out
+
+
+def opf_set_state_device(h, dev_ptr):
+    """dev_ptr: integer device address of a complex128 state (e.g. tensor.data_ptr())."""
+    _check(lib().opf_set_state_device(h.ptr, ctypes.c_void_p(dev_ptr)))
+
+
+def opf_get_state_device(h, dev_ptr):
+    _check(lib().opf_get_state_device(h.ptr, ctypes.c_void_p(dev_ptr)))
+
+
+def opf_step(h, n=1):
+    _check(lib().opf_step(h.ptr, int(n)))
+
+
+def opf_energy(h):
+    out = (ctypes.c_double * 3)()
+    _check(lib().opf_energy(h.ptr, out))
+    return np.array(out[:])
+
+
+def opf_wall_residual(h):
+    out = (ctypes.c_double * 2)()
+    _check(lib().opf_wall_residual(h.ptr, out))
+    return np.array(out[:])
+
+
+def opf_nonlinear(h, state):
+    a = _state_buffer(h, state)
+    out = np.empty(h.shape, dtype=np.complex128)
+    _check(lib().opf_nonlinear(h.ptr, a.ctypes.data, out.ctypes.data))
+    return out
+
+
+def opf_set_option(h, key, value):
+    _check(lib().opf_set_option(h.ptr, key.encode(), float(value)))
+
+
+def opf_get_option(h, key):
+    v = ctypes.c_double()
+    _check(lib().opf_get_option(h.ptr, key.encode(), ctypes.byref(v)))
+    return v.value
+
+
+def _get_scalar(fn, h):
+    v = ctypes.c_double()
+    _check(fn(h.ptr, ctypes.byref(v)))
+    return v.value
+
+
+def opf_get_dt(h):
+    return _get_scalar(lib().opf_get_dt, h)
+
+
+def opf_get_time(h):
+    return _get_scalar(lib().opf_get_time, h)
+
+
+def opf_get_beta(h):
+    return _get_scalar(lib().opf_get_beta, h)
+
+
+def opf_set_stream(h, stream_handle):
+    """stream_handle: integer cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream)."""
+    _check(lib().opf_set_stream(h.ptr, ctypes.c_void_p(stream_handle)))
+
+
+def opf_kernel_times(h, reset=False):
+    cap = 16
+    count = ctypes.c_int()
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_double * cap)()
+    n = (ctypes.c_int * cap)()
+    _check(lib().opf_kernel_times(h.ptr, cap, ctypes.byref(count), names, ms, n, int(reset)))
+    return {names[i].decode(): (ms[i], n[i]) for i in range(count.value)}
+
+
+def opf_setup_query(N, K, M, m_p, alpha, Re, dt, what):
+    L = lib()
+    n = ctypes.c_long()
+    _check(L.opf_setup_query(N, K, M, m_p, alpha, Re, dt, what.encode(), None, 0, ctypes.byref(n)))
+    out = np.empty(n.value, dtype=np.float64)
+    _check(L.opf_setup_query(N, K, M, m_p, alpha, Re, dt, what.encode(),
+                             out.ctypes.data_as(_dp), n.value, ctypes.byref(n)))
+    return out
