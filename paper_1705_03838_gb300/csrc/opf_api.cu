@@ -121,11 +121,12 @@ void free_all(opf_ctx* h) {
 void begin(opf_ctx* h, int name) {
   if (!h->timing || h->nslots >= kMaxSlots) return;
   h->slot_name[h->nslots] = name;
-  cudaEventRecord(h->ev[h->nslots][0], h->stream);
+  // external: inside stream capture this becomes an event-record node
+  cudaEventRecordWithFlags(h->ev[h->nslots][0], h->stream, cudaEventRecordExternal);
 }
 void end(opf_ctx* h) {
   if (!h->timing || h->nslots >= kMaxSlots) return;
-  cudaEventRecord(h->ev[h->nslots][1], h->stream);
+  cudaEventRecordWithFlags(h->ev[h->nslots][1], h->stream, cudaEventRecordExternal);
   ++h->nslots;
 }
 
