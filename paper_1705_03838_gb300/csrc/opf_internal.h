@@ -76,7 +76,6 @@ struct Dims {
 
 void choose_chunks(Dims* d);
 bool prepare_kernel_attrs(const Dims& d);
-void prepare_solve_attrs(const Dims& d);
 
 // Launch wrappers (kernels live in opf_kernels.cu).
 void launch_abi_to_internal(const Dims& d, const double2* abi, double2* U, cudaStream_t st);

@@ -491,26 +491,27 @@ void choose_chunks(Dims* d) {
   while (d->zc > 1 && product_smem(*d, d->zc, vb) > budget) d->zc /= 2;
 }
 
+// The dynamic shared-memory limit is a per-kernel, process-wide attribute, so
+// it is raised to the device's opt-in maximum (never lowered): handles of
+// different sizes then never restrict one another.
 bool prepare_kernel_attrs(const Dims& d) {
   const size_t vb = sizeof(double2);
-  const size_t lim = 227 * 1024;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return false;
+  const size_t lim = (size_t)optin;
   if (zsynth_smem(d, d.mcz, vb) > lim || zanalysis_smem(d, d.mca, vb) > lim ||
       product_smem(d, d.zc, vb) > lim || solve_smem(d.N, d.N <= 64 ? 16 : (d.N <= 128 ? 8 : 4)) > lim)
     return false;
-  cudaFuncSetAttribute(k_zsynth<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)zsynth_smem(d, d.mcz, vb));
-  cudaFuncSetAttribute(k_zanalysis<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)zanalysis_smem(d, d.mca, vb));
-  cudaFuncSetAttribute(k_product<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)product_smem(d, d.zc, vb));
-  prepare_solve_attrs(d);
-  return true;
-}
-
-void prepare_solve_attrs(const Dims& d) {
-  cudaFuncSetAttribute(k_solve<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(d.N, 16));
-  cudaFuncSetAttribute(k_solve<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(d.N, 8));
-  cudaFuncSetAttribute(k_solve<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem(d.N, 4));
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  bool ok = cudaFuncSetAttribute(k_zsynth<double2>, a, optin) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_zanalysis<double2>, a, optin) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_product<double2>, a, optin) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_solve<16>, a, optin) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_solve<8>, a, optin) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_solve<4>, a, optin) == cudaSuccess;
+  return ok;
 }
 
 void launch_solve(const Dims& d, const DevSetup& s, const SolveArgs& a, double sumwG, int nJ,

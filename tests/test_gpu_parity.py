@@ -169,3 +169,17 @@ def test_two_correctors_match_oracle(opf):
     ref = o.step(U0, 2)
     h, U = gpu_run(opf, N, K, M, 1, alpha, Re, dt, U0, 2, n_corr=2)
     assert rel(U, ref) < 1e-12
+
+
+def test_handles_of_different_sizes_coexist(opf):
+    """A large handle keeps working after a smaller one is created (kernel
+    shared-memory limits are process-wide)."""
+    w = inputs.WORKLOADS["medium"]
+    args = (w["N"], w["K"], w["M"], w["m_p"], w["alpha"], w["Re"], w["dt"])
+    big = opf.opf_create(*args)
+    opf.opf_set_state(big, inputs.workload_state("medium"))
+    small = opf.opf_create(12, 2, 2, 1, 1.0, 100.0, 0.01)
+    opf.opf_set_state(small, inputs.laminar_state(12, 2, 2))
+    opf.opf_step(small, 1)
+    opf.opf_step(big, 2)
+    assert np.isfinite(opf.opf_energy(big)).all()
