@@ -121,6 +121,25 @@ int opf_set_stream(opf_t* h, void* stream);
 int opf_kernel_times(opf_t* h, int cap, int* count, const char** names,
                      double* total_ms, int* launches, int reset);
 
+/* No counterpart in the paper: an allocation-free variant of opf_nonlinear
+ * for callers that must not allocate device memory when they call (their
+ * device memory is all owned by their own pool, cudaMalloc/cudaFree could
+ * synchronise the device at a bad moment, or they forbid allocation after
+ * start-up).  Same result as opf_nonlinear on a handle created with the same
+ * (N, K, M, m_p, alpha, Re), but without a handle: d_state and d_out are
+ * DEVICE buffers in the state layout, stream is a cudaStream_t (NULL = the
+ * default stream); the call returns when the result is in d_out.  All
+ * intermediates (stencils, twiddles, transforms) live in one fixed 16 MiB
+ * device array inside the library, held on every GPU that loads it until
+ * the process exits; OPF_EINVAL if the resolution needs more (the small
+ * N=32, |k|<16, m<16 case needs 6.6 MB).  The first call on a device looks
+ * up that array's address there, so make it before any stream capture.
+ * Calls share the array: calls whose GPU work overlaps race.  On success
+ * it calls no allocator at all (no cudaMalloc, cudaFree or allocating
+ * library routine); a failure only stores its message for opf_last_error. */
+int opf_nonlinear_noalloc(int N, int K, int M, int m_p, double alpha, double Re,
+                          const double* d_state, double* d_out, void* stream);
+
 /* Host-only diagnostics (no GPU needed): build the radial setup that
  * opf_create would build for these parameters and copy one array into
  * out[0..cap).  what = "r" (N radial points), "wq" (N quadrature weights,

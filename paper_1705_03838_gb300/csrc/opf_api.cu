@@ -23,6 +23,13 @@ int fail(int code, const std::string& msg) {
       return fail(OPF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));           \
   } while (0)
 
+}  // namespace
+
+namespace opf {
+void set_last_error(const std::string& m) { g_err = m; }
+}  // namespace opf
+
+namespace {
 constexpr int kMaxSlots = 32;
 const char* kNames[] = {"curl", "zsynth", "product", "zanalysis", "solve"};
 constexpr int kNumNames = 5;

@@ -76,6 +76,7 @@ struct Dims {
 
 void choose_chunks(Dims* d);
 bool prepare_kernel_attrs(const Dims& d);
+void set_last_error(const std::string& m);  // text returned by opf_last_error()
 
 // Launch wrappers (kernels live in opf_kernels.cu).
 void launch_abi_to_internal(const Dims& d, const double2* abi, double2* U, cudaStream_t st);

@@ -62,6 +62,8 @@ def lib():
         L.opf_kernel_times.restype = i
         L.opf_kernel_times.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(cp), _dp,
                                        ctypes.POINTER(i), i]
+        L.opf_nonlinear_noalloc.restype = i
+        L.opf_nonlinear_noalloc.argtypes = [i, i, i, i, d, d, vp, vp, vp]
         L.opf_setup_query.restype = i
         L.opf_setup_query.argtypes = [i, i, i, i, d, d, d, cp, _dp, ctypes.c_long,
                                       ctypes.POINTER(ctypes.c_long)]
@@ -151,6 +153,14 @@ def opf_nonlinear(h, state):
     out = np.empty(h.shape, dtype=np.complex128)
     _check(lib().opf_nonlinear(h.ptr, a.ctypes.data, out.ctypes.data))
     return out
+
+
+def opf_nonlinear_noalloc(N, K, M, m_p, alpha, Re, d_state, d_out, stream=0):
+    """Allocation-free nonlinear term; d_state / d_out are integer device
+    addresses of complex128 buffers in the state layout (e.g. data_ptr())."""
+    _check(lib().opf_nonlinear_noalloc(int(N), int(K), int(M), int(m_p), float(alpha), float(Re),
+                                       ctypes.c_void_p(d_state), ctypes.c_void_p(d_out),
+                                       ctypes.c_void_p(stream)))
 
 
 def opf_set_option(h, key, value):
