@@ -295,27 +295,82 @@ struct SolveDev {
   int nJ;
 };
 
-// One block: T consecutive k at fixed m.  6T threads = (field u+,u-,u_z) x
-// T modes x (re, im); each thread runs one real banded solve.
+// Banded substitution on one real right-hand side held in shared memory at
+// x[i * st], i < N: forward with the unit lower factor, backward with the
+// upper factor (13-slot rows: 8 L, 1/U_ii, 4 U).  Warps issue in order, so
+// each row first issues the work that does not depend on the row just
+// finished (next-row factor prefetch, older band terms) and ends with the one
+// multiply-add on the previous row's value, which is kept in a register.
+__device__ __forceinline__ void band_solve(const double* __restrict__ L, double* x, int st, int N) {
+  double cur[kLuSlots], nxt[kLuSlots];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) cur[q] = L[q];
+  double prev = 0.0;
+  for (int i = 0; i < N; ++i) {
+    const int ip = min(i + 1, N - 1);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) nxt[q] = L[ip * kLuSlots + q];
+    const int q0 = 8 - (i - row_lo_d(i, N));
+    double b0 = x[i * st], b1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < 7; q += 2) {
+      if (q >= q0) b0 -= cur[q] * x[(i - 8 + q) * st];
+      if (q + 1 < 7 && q + 1 >= q0) b1 -= cur[q + 1] * x[(i - 7 + q) * st];
+    }
+    b0 += b1;
+    if (i > 0) b0 -= cur[7] * prev;
+    x[i * st] = b0;
+    prev = b0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cur[q] = nxt[q];
+  }
+#pragma unroll
+  for (int q = 8; q < kLuSlots; ++q) cur[q] = L[(N - 1) * kLuSlots + q];
+  prev = 0.0;
+  for (int i = N - 1; i >= 0; --i) {
+    const int im = max(i - 1, 0);
+#pragma unroll
+    for (int q = 8; q < kLuSlots; ++q) nxt[q] = L[im * kLuSlots + q];
+    const int nu = min(i + 4, N - 1) - i;
+    double v0 = x[i * st], v1 = 0.0;
+    if (nu >= 2) v0 -= cur[10] * x[(i + 2) * st];
+    if (nu >= 3) v1 -= cur[11] * x[(i + 3) * st];
+    if (nu >= 4) v0 -= cur[12] * x[(i + 4) * st];
+    v0 += v1;
+    if (nu >= 1) v0 -= cur[9] * prev;
+    v0 *= cur[8];
+    x[i * st] = v0;
+    prev = v0;
+#pragma unroll
+    for (int q = 8; q < kLuSlots; ++q) cur[q] = nxt[q];
+  }
+}
+
+// One block: T consecutive k at fixed m.  Row-parallel phases use all 6T
+// threads over (chain, row); only the banded substitutions are sequential in r
+// (one thread per real right-hand side: 2T pressure chains, then 6T velocity
+// chains = (u+, u-, u_z) x T modes x (re, im)).
 template <int T>
-__global__ void __launch_bounds__(6 * T) k_solve(Dims d, SolveDev s, SolveArgs a) {
+__global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = d.N, nk = d.nk, M = d.M, K = d.K;
-  double2* NE = (double2*)smraw;      // [3][N][T]  N_eff
-  double2* S = NE + 3 * N * T;        // [N][T]     N+ + N-
-  double2* P = S + N * T;             // [N][T]     pressure
-  double2* coef = P + N * T;          // [T][4]     influence coefficients
-  double* X = (double*)(coef + 4 * T);  // [N][6T] solve vectors
+  constexpr int NT = 6 * T;   // velocity chains
+  constexpr int NB = 24 * T;  // threads in the block (row-parallel phases)
+  double2* NE = (double2*)smraw;        // [3][N][T]  N_eff
+  double2* S = NE + 3 * N * T;          // [N][T]     N+ + N-, later d_r p
+  double2* P = S + N * T;               // [N][T]     pressure
+  double2* coef = P + N * T;            // [T][4]     influence coefficients
+  double* X = (double*)(coef + 4 * T);  // [N][6T]    velocity chains
+  double* W1 = X + N * NT;              // [2][N][9]  first-derivative stencils
+  double* misc = W1 + 2 * N * 9;        // [2]        flux correction
   const int m = blockIdx.y, kk0 = blockIdx.x * T, tid = threadIdx.x;
   const int mt = d.m_p * m, ps = mt & 1, pv = ps ^ 1;
-  const double* wv = s.d1 + (long)pv * N * 9;
-  const double* ws = s.d1 + (long)ps * N * 9;
   const double ci = 1.0 / (d.c * d.dt), cu = (1.0 - d.c) / d.c;
   const long fs = d.F;
   const long base = (long)m * N * nk;
 
-  // N_eff = wa Na + wb Nb, and S = N+ + N-
-  for (int e = tid; e < 3 * N * T; e += blockDim.x) {
+  for (int e = tid; e < 2 * N * 9; e += NB) W1[e] = s.d1[e];
+  for (int e = tid; e < 3 * N * T; e += NB) {
     const int mi = e % T, i = (e / T) % N, f = e / (T * N);
     const int kk = min(kk0 + mi, nk - 1);
     const long g = f * fs + base + (long)i * nk + kk;
@@ -329,105 +384,110 @@ __global__ void __launch_bounds__(6 * T) k_solve(Dims d, SolveDev s, SolveArgs a
     NE[(f * N + i) * T + mi] = v;
   }
   __syncthreads();
-  for (int e = tid; e < N * T; e += blockDim.x) {
+  for (int e = tid; e < N * T; e += NB) {
     const double2 p = NE[e], q = NE[N * T + e];
     S[e] = double2{p.x + q.x, p.y + q.y};
   }
   __syncthreads();
+  const double* wv = W1 + pv * N * 9;
+  const double* ws = W1 + ps * N * 9;
 
-  // ---- pressure-Poisson: lap p = div N_eff, provisional wall condition dp/dr = 0
+  // ---- pressure right-hand side: div N_eff (rows < N-1), 0 at the wall
+  for (int e = tid; e < N * T; e += NB) {
+    const int mi = e % T, i = e / T;
+    const int k = min(kk0 + mi, nk - 1) - (K - 1);
+    const double ak = d.alpha * k;
+    double2 b = double2{0.0, 0.0};
+    if (i < N - 1) {
+      const int lo = row_lo_d(i, N);
+      double ax = 0.0, ay = 0.0;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const double2 sv = S[(lo + q) * T + mi];
+        ax += wv[i * 9 + q] * sv.x;
+        ay += wv[i * 9 + q] * sv.y;
+      }
+      const double2 np = NE[i * T + mi], nm = NE[(N + i) * T + mi], nz = NE[(2 * N + i) * T + mi];
+      const double ri = 0.5 * s.rinv[i];
+      b.x = 0.5 * ax + ri * ((1 + mt) * np.x + (1 - mt) * nm.x) - ak * nz.y;
+      b.y = 0.5 * ay + ri * ((1 + mt) * np.y + (1 - mt) * nm.y) + ak * nz.x;
+    }
+    P[i * T + mi] = b;
+  }
+  __syncthreads();
+
+  // ---- pressure-Poisson solve (provisional dp/dr(1) = 0; (0,0): p(1) = 0)
   if (tid < 2 * T) {
     const int part = tid & 1, mi = tid >> 1;
-    const int kk = min(kk0 + mi, nk - 1);
-    const int k = kk - (K - 1), ik = abs(k);
-    const double ak = d.alpha * k;
+    const int k = min(kk0 + mi, nk - 1) - (K - 1), ik = abs(k);
     const int op = (ik == 0 && m == 0) ? K * M : ik * M + m;
-    const double* L = s.luP + (long)op * N * kLuSlots;
-    double* Pp = (double*)P + 2 * mi + part;
-    const double* Sp = (const double*)S + 2 * mi + part;
-    const int st = 2 * T;
-    for (int i = 0; i < N; ++i) {
-      double b = 0.0;
-      if (i < N - 1) {
-        const int lo = row_lo_d(i, N);
-        double acc = 0.0;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) acc += wv[i * 9 + q] * Sp[(lo + q) * st];
-        const double2 np = NE[i * T + mi], nm = NE[(N + i) * T + mi], nz = NE[(2 * N + i) * T + mi];
-        const double ri = 0.5 * s.rinv[i];
-        b = part == 0 ? 0.5 * acc + ri * ((1 + mt) * np.x + (1 - mt) * nm.x) - ak * nz.y
-                      : 0.5 * acc + ri * ((1 + mt) * np.y + (1 - mt) * nm.y) + ak * nz.x;
-      }
-      const double* Lr = L + i * kLuSlots;
-      for (int q = 8 - (i - row_lo_d(i, N)); q < 8; ++q) b -= Lr[q] * Pp[(i - 8 + q) * st];
-      Pp[i * st] = b;
-    }
-    for (int i = N - 1; i >= 0; --i) {
-      const double* Lr = L + i * kLuSlots;
-      double x = Pp[i * st];
-      const int nu = min(i + 4, N - 1) - i;
-      for (int q = 1; q <= nu; ++q) x -= Lr[8 + q] * Pp[(i + q) * st];
-      Pp[i * st] = x * Lr[8];
-    }
+    band_solve(s.luP + (long)op * N * kLuSlots, (double*)P + 2 * mi + part, 2 * T, N);
   }
   __syncthreads();
 
-  // ---- implicit viscous solves: (1/dt - cL) u = R - grad p, Dirichlet 0
-  const int part = tid & 1, mi = (tid >> 1) % T, f = (tid >> 1) / T;
-  const int kk = min(kk0 + mi, nk - 1);
-  const int k = kk - (K - 1), ik = abs(k);
-  const double ak = d.alpha * k;
-  const int st6 = 6 * T;
-  double* Xc = X + tid;
-  const double2* Uj = a.Uj + f * fs + base + kk;
-  {
+  // ---- d_r p once per (mode, row) into S, then velocity right-hand sides
+  for (int e = tid; e < N * T; e += NB) {
+    const int mi = e % T, i = e / T;
+    const int lo = row_lo_d(i, N);
+    double ax = 0.0, ay = 0.0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const double2 pv2 = P[(lo + q) * T + mi];
+      ax += ws[i * 9 + q] * pv2.x;
+      ay += ws[i * 9 + q] * pv2.y;
+    }
+    S[i * T + mi] = double2{ax, ay};
+  }
+  __syncthreads();
+  for (int e = tid; e < N * NT; e += NB) {
+    const int c = e % NT, i = e / NT;
+    const int part = c & 1, mi = (c >> 1) % T, f = (c >> 1) / T;
+    const int kk = min(kk0 + mi, nk - 1);
+    const double ak = d.alpha * (kk - (K - 1));
+    double b = 0.0;
+    if (i < N - 1) {
+      const double2 pp = P[i * T + mi];
+      double gp;
+      if (f < 2) {
+        const double2 dp = S[i * T + mi];
+        const double q = mt * s.rinv[i] * (part ? pp.y : pp.x);
+        gp = (part ? dp.y : dp.x) + (f == 0 ? -q : q);
+      } else {
+        gp = part == 0 ? -ak * pp.y : ak * pp.x;
+      }
+      const double2 u = a.Uj[f * fs + base + (long)i * nk + kk];
+      const double2 ne = NE[(f * N + i) * T + mi];
+      b = ci * (part ? u.y : u.x) + (part ? ne.y : ne.x) - gp;
+    }
+    X[i * NT + c] = b;
+  }
+  __syncthreads();
+
+  // ---- implicit viscous solves (1/dt - cL) v = rhs, Dirichlet 0
+  if (tid < NT) {
+    const int part = tid & 1, mi = (tid >> 1) % T, f = (tid >> 1) / T;
+    (void)part;
+    const int k = min(kk0 + mi, nk - 1) - (K - 1), ik = abs(k);
     const int op = ik * s.nJ + s.hop[3 * m + f];
-    const double* L = s.luH + (long)op * N * kLuSlots;
-    const double* Pr = (const double*)P + 2 * mi;
-    for (int i = 0; i < N; ++i) {
-      double b = 0.0;
-      if (i < N - 1) {
-        double gp;
-        if (f < 2) {
-          const int lo = row_lo_d(i, N);
-          double acc = 0.0;
-#pragma unroll
-          for (int q = 0; q < 9; ++q) acc += ws[i * 9 + q] * Pr[(lo + q) * 2 * T + part];
-          const double pp = mt * s.rinv[i] * Pr[i * 2 * T + part];
-          gp = f == 0 ? acc - pp : acc + pp;
-        } else {
-          gp = part == 0 ? -ak * Pr[i * 2 * T + 1] : ak * Pr[i * 2 * T];
-        }
-        const double2 u = Uj[(long)i * nk];
-        const double2 ne = NE[(f * N + i) * T + mi];
-        b = ci * (part ? u.y : u.x) + (part ? ne.y : ne.x) - gp;
-      }
-      const double* Lr = L + i * kLuSlots;
-      for (int q = 8 - (i - row_lo_d(i, N)); q < 8; ++q) b -= Lr[q] * Xc[(i - 8 + q) * st6];
-      Xc[i * st6] = b;
-    }
-    for (int i = N - 1; i >= 0; --i) {
-      const double* Lr = L + i * kLuSlots;
-      double x = Xc[i * st6];
-      const int nu = min(i + 4, N - 1) - i;
-      for (int q = 1; q <= nu; ++q) x -= Lr[8 + q] * Xc[(i + q) * st6];
-      Xc[i * st6] = x * Lr[8];
-    }
-    // u = v - ((1-c)/c) u_j, applied only once the back substitution is done
-    for (int i = 0; i < N; ++i) {
-      const double2 u = Uj[(long)i * nk];
-      Xc[i * st6] -= cu * (part ? u.y : u.x);
-    }
+    band_solve(s.luH + (long)op * N * kLuSlots, X + tid, NT, N);
   }
   __syncthreads();
 
-  // ---- influence matrix: g = (u+(1), u-(1), u_z(1), div u(1)), a = -A^{-1} g
+  // ---- u = v - ((1-c)/c) u_j; influence matrix: g = (u+(1), u-(1), u_z(1), div u(1))
+  for (int e = tid; e < N * NT; e += NB) {
+    const int c = e % NT, i = e / NT;
+    const int part = c & 1, mi = (c >> 1) % T, f = (c >> 1) / T;
+    const int kk = min(kk0 + mi, nk - 1);
+    const double2 u = a.Uj[f * fs + base + (long)i * nk + kk];
+    X[i * NT + c] -= cu * (part ? u.y : u.x);
+  }
+  __syncthreads();
   if (tid < T && kk0 + tid < nk) {
     const int mj = tid, kj = kk0 + tid;
     const double akj = d.alpha * (kj - (K - 1));
     auto xv = [&](int ff, int i) {
       const int c = (ff * T + mj) << 1;
-      return double2{X[i * st6 + c], X[i * st6 + c + 1]};
+      return double2{X[i * NT + c], X[i * NT + c + 1]};
     };
     const double2 g0 = xv(0, N - 1), g1 = xv(1, N - 1), g2 = xv(2, N - 1);
     const int lo = N - 9;
@@ -455,29 +515,60 @@ __global__ void __launch_bounds__(6 * T) k_solve(Dims d, SolveDev s, SolveArgs a
   }
   __syncthreads();
 
-  // ---- add basis responses, fixed-flux correction of (0,0), write out
-  if (kk0 + mi < nk) {
+  // ---- add basis responses
+  for (int e = tid; e < N * NT; e += NB) {
+    const int c = e % NT, i = e / NT;
+    const int part = c & 1, mi = (c >> 1) % T, f = (c >> 1) / T;
+    const int k = min(kk0 + mi, nk - 1) - (K - 1), ik = abs(k);
     const double* Bv = s.basis + ((long)(ik * M + m) * 6) * N;
     const double2 a0 = coef[mi * 4 + 0], ax = coef[mi * 4 + 1 + f];
     const double sk = k > 0 ? 1.0 : (k < 0 ? -1.0 : 0.0);
     const double c0 = f == 2 ? (part ? sk * a0.x : -sk * a0.y) : (part ? a0.y : a0.x);
     const double c1 = part ? ax.y : ax.x;
-    const double* b0 = Bv + f * N;
-    const double* b1 = Bv + (3 + f) * N;
-    for (int i = 0; i < N; ++i) Xc[i * st6] += c0 * b0[i] + c1 * b1[i];
-    if (k == 0 && m == 0 && f == 2 && part == 0) {
+    X[i * NT + c] += c0 * Bv[f * N + i] + c1 * Bv[(3 + f) * N + i];
+  }
+  __syncthreads();
+
+  // ---- fixed flux on (0,0): beta' so that 2 pi int u_z r dr = pi/2
+  const bool has_mean = (m == 0 && kk0 <= K - 1 && K - 1 < kk0 + T);
+  if (has_mean) {
+    const int cz = (2 * T + (K - 1 - kk0)) << 1;  // chain (u_z, mode k=0, re)
+    if (tid == 0) {
       double q = 0.0;
-      for (int i = 0; i < N; ++i) q += s.wq[i] * Xc[i * st6];
-      const double bp = (0.25 - q) / s.sumwG;  // 2 pi int u_z r dr = pi/2
-      for (int i = 0; i < N; ++i) Xc[i * st6] += bp * s.G[i];
+      for (int i = 0; i < N; ++i) q += s.wq[i] * X[i * NT + cz];
+      const double bp = (0.25 - q) / s.sumwG;
+      misc[0] = bp;
       *a.beta_p = bp;
     }
-    double* out = (double*)(a.Uout + f * fs + base + kk) + part;
-    for (int i = 0; i < N; ++i) out[(long)i * nk * 2] = Xc[i * st6];
+    __syncthreads();
+    const double bp = misc[0];
+    for (int i = tid; i < N; i += NB) X[i * NT + cz] += bp * s.G[i];
+    __syncthreads();
+  }
+
+  // ---- write out (coalesced over k)
+  for (int e = tid; e < N * NT; e += NB) {
+    const int c = e % NT, i = e / NT;
+    const int part = c & 1, mi = (c >> 1) % T, f = (c >> 1) / T;
+    if (kk0 + mi >= nk) continue;
+    double* out = (double*)(a.Uout + f * fs + base + (long)i * nk + kk0 + mi) + part;
+    *out = X[i * NT + c];
   }
 }
 
-static size_t solve_smem(int N, int T) { return (size_t)(5 * N * T + 4 * T) * 16 + (size_t)6 * N * T * 8; }
+static size_t solve_smem(int N, int T);
+
+// Largest tile that still gives every SM a block and fits 200 KB of shared memory.
+static int solve_tile(const Dims& d) {
+  const long modes = (long)d.nk * d.M;
+  for (int T : {16, 8})
+    if (modes / T >= 152 && solve_smem(d.N, T) <= 200 * 1024) return T;
+  return 4;
+}
+
+static size_t solve_smem(int N, int T) {
+  return (size_t)(5 * N * T + 4 * T) * 16 + (size_t)6 * N * T * 8 + (size_t)(2 * N * 9 + 2) * 8;
+}
 
 // Chunk sizes keep every transform block within ~96 KB of shared memory (two
 // blocks per SM), then raise each kernel's dynamic shared-memory limit.
@@ -502,7 +593,7 @@ bool prepare_kernel_attrs(const Dims& d) {
     return false;
   const size_t lim = (size_t)optin;
   if (zsynth_smem(d, d.mcz, vb) > lim || zanalysis_smem(d, d.mca, vb) > lim ||
-      product_smem(d, d.zc, vb) > lim || solve_smem(d.N, d.N <= 64 ? 16 : (d.N <= 128 ? 8 : 4)) > lim)
+      product_smem(d, d.zc, vb) > lim || solve_smem(d.N, solve_tile(d)) > lim)
     return false;
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   bool ok = cudaFuncSetAttribute(k_zsynth<double2>, a, optin) == cudaSuccess;
@@ -517,16 +608,11 @@ bool prepare_kernel_attrs(const Dims& d) {
 void launch_solve(const Dims& d, const DevSetup& s, const SolveArgs& a, double sumwG, int nJ,
                   cudaStream_t st) {
   SolveDev sd{s.d1, s.rinv, s.wq, s.hop, s.luH, s.luP, s.basis, s.ainv, s.G, sumwG, nJ};
-  if (d.N <= 64) {
-    dim3 g((d.nk + 15) / 16, d.M);
-    k_solve<16><<<g, 96, solve_smem(d.N, 16), st>>>(d, sd, a);
-  } else if (d.N <= 128) {
-    dim3 g((d.nk + 7) / 8, d.M);
-    k_solve<8><<<g, 48, solve_smem(d.N, 8), st>>>(d, sd, a);
-  } else {
-    dim3 g((d.nk + 3) / 4, d.M);
-    k_solve<4><<<g, 24, solve_smem(d.N, 4), st>>>(d, sd, a);
-  }
+  const int T = solve_tile(d);
+  dim3 g((d.nk + T - 1) / T, d.M);
+  if (T == 16) k_solve<16><<<g, 24 * 16, solve_smem(d.N, 16), st>>>(d, sd, a);
+  else if (T == 8) k_solve<8><<<g, 24 * 8, solve_smem(d.N, 8), st>>>(d, sd, a);
+  else k_solve<4><<<g, 24 * 4, solve_smem(d.N, 4), st>>>(d, sd, a);
 }
 
 // ------------------------------------------------------------------ diagnostics
