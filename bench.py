@@ -56,25 +56,23 @@ def config_dict(w, precision):
 
 # ------------------------------------------------------------------ algorithmic costs
 def kernel_costs(w):
-    """Algorithmic flops (FP64 path) and bytes per launch, per kernel.
+    """Algorithmic flops and bytes per launch, per kernel.
 
     FFT flops use 2.5 n log2 n per real 2-D transform of n = 9KM points,
-    split between z (log2 3K) and theta (log2 3M) parts; bytes are the
-    spectral/intermediate arrays each launch must read and write once."""
+    split between z (log2 3K) and theta (log2 3M) parts.  The solve counts,
+    per mode and radial row: div N_eff (48), d_r p (36), right-hand sides (30),
+    final update and influence correction (36), and 8 real banded
+    substitutions (2 nl + 2 nu + 1 each, nl/nu the row's band widths)."""
     N, K, M = w["N"], w["K"], w["M"]
     nz, nth, nk = 3 * K, 3 * M, 2 * K - 1
     n = nz * nth
     F = N * nk * M  # complex per spectral field
     P = N * nz * M  # complex per half-physical field
     lz, lt = math.log2(nz), math.log2(nth)
-    # banded solve per real RHS: forward nl_i, backward nu_i + 1 (multiply by 1/U_ii)
     lo = [min(max(i - 4, 0), N - 9) for i in range(N)]
-    fwd = sum(2 * (i - lo[i]) for i in range(N))
-    bwd = sum(2 * (min(i + 4, N - 1) - i) + 1 for i in range(N))
-    solve_flops_per_rhs = fwd + bwd
+    band = sum(2 * (i - lo[i]) + 2 * (min(i + 4, N - 1) - i) + 1 for i in range(N))
     modes = nk * M
-    solve = modes * (2 * (solve_flops_per_rhs + 2 * 9 * N + 10 * N)  # pressure: div N + solve
-                     + 6 * (solve_flops_per_rhs + 2 * 9 * N + 6 * N))  # velocity: grad p + rhs + solve
+    solve = modes * (N * (48 + 36 + 30 + 36) + 8 * band)
     return {
         "curl": {"flops": F * (2 * 9 * 4 + 30), "bytes": 16 * (3 * F + 6 * F)},
         "zsynth": {"flops": 6 * N * 2.5 * n * lz, "bytes": 16 * (6 * F + 6 * P)},
@@ -82,6 +80,14 @@ def kernel_costs(w):
         "zanalysis": {"flops": 3 * N * 2.5 * n * lz, "bytes": 16 * (3 * P + 3 * F)},
         "solve": {"flops": solve, "bytes": 16 * (3 * F * 3 + 3 * F)},
     }
+
+
+# which arithmetic bounds each kernel: FP64 for the solve and the curl (both
+# precisions), the transforms follow the precision
+def kernel_peak(name, precision):
+    if precision == 1 and name in ("zsynth", "product", "zanalysis"):
+        return FP32_PEAK_TFLOPS, "FP32 from unit counts (152 SMs x 128 lanes x 2 flops x 2.07 GHz)"
+    return FP64_PEAK_TFLOPS, "FP64 from unit counts (152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz)"
 
 
 def step_algorithmic_bytes(w, precision):
@@ -99,8 +105,11 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-# FP64 peak from unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz
+# Peaks from unit counts at the 2.07 GHz maximum SM clock: FP64 152 SMs x 2
+# DFMA/clk x 2 flops (FMA probe on this GPU: 1.20 TFLOP/s); FP32 152 SMs x 128
+# lanes x 2 flops (probe: 70 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 # ------------------------------------------------------------------ clocks
@@ -246,52 +255,62 @@ def run_gpu(args, w):
     stream = torch.cuda.current_stream()
     h = opf.opf_create(w["N"], w["K"], w["M"], w["m_p"], w["alpha"], w["Re"], w["dt"])
     opf.opf_set_stream(h, stream.cuda_stream)
-    if args.precision:
-        opf.opf_set_option(h, "precision", args.precision)
     # each replica runs its own seeded trajectory
     U0 = inputs.seeded_state(w["N"], w["K"], w["M"], w["m_p"], w["alpha"], w["amplitude"],
                              w["seed"] + rank, w["envelope"])
     opf.opf_set_state(h, U0)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    # warm-up (builds the CUDA graph)
-    for _ in range(args.warmup):
-        flush.zero_()
-        opf.opf_step(h, 1)
-    opf.opf_set_option(h, "timing", 1)
-    opf.opf_step(h, 1)  # capture the timed graph outside the timed region
-    opf.opf_kernel_times(h, reset=True)
+    def timed(precision):
+        """K steps at one precision from U0; per-step CUDA events, L2 flushed between."""
+        opf.opf_set_option(h, "precision", precision)
+        opf.opf_set_state(h, U0)
+        for _ in range(args.warmup):
+            flush.zero_()
+            opf.opf_step(h, 1)
+        opf.opf_set_state(h, U0)
+        opf.opf_set_option(h, "timing", 1)
+        opf.opf_step(h, 1)  # capture the timed graph outside the timed region
+        opf.opf_set_state(h, U0)
+        opf.opf_kernel_times(h, reset=True)
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.3)
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.time()
+        for i in range(args.steps):
+            flush.zero_()
+            ev0[i].record(stream)
+            opf.opf_step(h, 1)
+            ev1[i].record(stream)
+        torch.cuda.synchronize()
+        wall = time.time() - wall0
+        if world > 1:
+            dist.barrier()
+        clk = clocks.stop()
+        total = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+        kt = opf.opf_kernel_times(h, reset=True)
+        opf.opf_set_option(h, "timing", 0)
+        energy = opf.opf_energy(h)
+        if world > 1:
+            t = torch.tensor([total], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        return total, kt, clk, wall, energy
 
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    wall0 = time.time()
-    for i in range(args.steps):
-        flush.zero_()
-        ev0[i].record(stream)
-        opf.opf_step(h, 1)
-        ev1[i].record(stream)
-    torch.cuda.synchronize()
-    wall = time.time() - wall0
-    if world > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    total_ms = sum(step_ms)
-    ktimes = opf.opf_kernel_times(h, reset=True)
-    opf.opf_set_option(h, "timing", 0)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    res = {}
+    for prec in (0, 1):
+        res[prec] = timed(prec)
+    total_ms, ktimes, clk, wall, E = res[args.precision]
+    E64, E32 = res[0][4], res[1][4]
 
     # end-to-end through the public API with host buffers: per step, copy the
     # state in from pinned memory, advance one step, read E, I, D back.
+    opf.opf_set_option(h, "precision", args.precision)
     pinned = torch.from_numpy(U0.view(np.float64).copy()).pin_memory()
     e2e_steps = max(3, min(args.steps, 50))
     opf.opf_step(h, 1)
@@ -317,15 +336,20 @@ def run_gpu(args, w):
     value = args.steps * world / (total_ms / 1000.0)
     peaks, peak_kind = load_peaks()
     costs = kernel_costs(w)
-    # dominant kernel by device time over the timed region
-    dom = max(ktimes, key=lambda k: ktimes[k][0])
-    dom_ms = ktimes[dom][0] / max(1, ktimes[dom][1])
-    achieved = costs[dom]["flops"] / (dom_ms * 1e-3) / 1e12
-    roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "peak_source": "FP64 from unit counts (152 SMs x 2 DFMA/clk x 2.07 GHz)",
-            "launch_ms": dom_ms,
-            "share": {k: v[0] / sum(x[0] for x in ktimes.values()) for k, v in ktimes.items()}}
+
+    def roofline(kt, precision):
+        dom = max(kt, key=lambda k: kt[k][0])
+        dom_ms = kt[dom][0] / max(1, kt[dom][1])
+        pk, src = kernel_peak(dom, precision)
+        ach = costs[dom]["flops"] / (dom_ms * 1e-3) / 1e12
+        tot = sum(x[0] for x in kt.values())
+        return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                "frac": ach / pk, "traffic": None, "peak_source": src, "launch_ms": dom_ms,
+                "share": {k: v[0] / tot for k, v in kt.items()}}
+
+    roof = roofline(ktimes, args.precision)
+    fp64_value = args.steps * world / (res[0][0] / 1000.0)
+    mixed_value = args.steps * world / (res[1][0] / 1000.0)
     hbm_frac = step_algorithmic_bytes(w, args.precision) * value / world / (peaks["hbm_gbs"] * 1e9)
 
     cpu = None
@@ -347,6 +371,14 @@ def run_gpu(args, w):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64" if args.precision == 0 else "f32+f64",
+        "precision_compare": {
+            "fp64": {"value": fp64_value, "ms_per_step": res[0][0] / args.steps,
+                     "roofline": roofline(res[0][1], 0)},
+            "mixed": {"value": mixed_value, "ms_per_step": res[1][0] / args.steps,
+                      "roofline": roofline(res[1][1], 1)},
+            "mixed_over_fp64": mixed_value / fp64_value,
+            "mixed_energy_rel_err_vs_fp64_after_steps": float(abs(E32[0] - E64[0]) / E64[0]),
+        },
         "data": "synthetic",
         "config": config_dict(w, args.precision),
         "gdof_steps_per_s": value * dof(w) / 1e9,
@@ -372,7 +404,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--precision", type=int, default=1,
+                    help="headline precision: 1 = mixed (default), 0 = FP64; both are timed")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

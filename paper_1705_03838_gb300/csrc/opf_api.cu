@@ -42,6 +42,8 @@ struct opf_ctx {
   opf::FftPlan pz{}, pth{};
   double2 *U = nullptr, *U1 = nullptr, *Nj = nullptr, *Nq = nullptr, *W6 = nullptr;
   double2 *Z6 = nullptr, *ZN = nullptr, *abi = nullptr, *tmpU = nullptr;
+  float2 *W6f = nullptr, *Z6f = nullptr, *ZNf = nullptr;  // mixed-precision intermediates
+  double2* Nlin = nullptr;                                // FP64 linear terms (mixed)
   double *beta_p = nullptr, *partial = nullptr, *out3 = nullptr, *out2 = nullptr;
   int* flag = nullptr;
   int nblk_energy = 0;
@@ -139,6 +141,21 @@ void end(opf_ctx* h) {
 
 void enqueue_nonlinear(opf_ctx* h, const double2* U, double2* Nout) {
   const opf::Dims& d = h->d;
+  if (h->precision == 1) {
+    begin(h, 0);
+    opf::launch_curl_split32(d, h->ds, U, h->W6f, h->Nlin, h->stream);
+    end(h);
+    begin(h, 1);
+    opf::launch_zsynth32(d, h->ds, h->pz, h->W6f, h->Z6f, h->stream);
+    end(h);
+    begin(h, 2);
+    opf::launch_product32(d, h->ds, h->pth, h->Z6f, h->ZNf, h->stream);
+    end(h);
+    begin(h, 3);
+    opf::launch_zanalysis32(d, h->ds, h->pz, h->ZNf, h->Nlin, Nout, h->stream);
+    end(h);
+    return;
+  }
   begin(h, 0);
   opf::launch_curl(d, h->ds, U, h->W6, h->stream);
   end(h);
@@ -258,7 +275,8 @@ opf_t* opf_create(int N, int K, int M, int m_p, double alpha, double Re, double 
       dalloc(h, &h->Nq, 3 * F16) || dalloc(h, &h->W6, 6 * F16) || dalloc(h, &h->Z6, 6 * P16) ||
       dalloc(h, &h->ZN, 3 * P16) || dalloc(h, &h->abi, 3 * F16) || dalloc(h, &h->tmpU, 3 * F16) ||
       dalloc(h, &h->beta_p, 16) || dalloc(h, &h->out3, 32) || dalloc(h, &h->out2, 16) ||
-      dalloc(h, &h->flag, 16))
+      dalloc(h, &h->flag, 16) || dalloc(h, &h->W6f, 6 * F16 / 2) || dalloc(h, &h->Z6f, 6 * P16 / 2) ||
+      dalloc(h, &h->ZNf, 3 * P16 / 2) || dalloc(h, &h->Nlin, 3 * F16))
     return bail(0);
   h->nblk_energy = opf::energy_blocks(d);
   if (dalloc(h, &h->partial, (size_t)2 * h->nblk_energy * sizeof(double))) return bail(0);
@@ -420,8 +438,8 @@ int opf_set_option(opf_t* h, const char* key, double v) {
   if (check_handle(h)) return OPF_EINVAL;
   if (!key) return fail(OPF_EINVAL, "opf_set_option: NULL key");
   if (!strcmp(key, "precision")) {
-    if (v != 0.0) return fail(OPF_EINVAL, "precision: only 0 (FP64) is available");
-    h->precision = 0;
+    if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "precision: 0 (FP64) or 1 (mixed)");
+    h->precision = (int)v;
   } else if (!strcmp(key, "n_corr")) {
     if (!(v >= 1 && v <= 16 && v == std::floor(v))) return fail(OPF_EINVAL, "n_corr: 1..16");
     h->n_corr = (int)v;

@@ -89,6 +89,16 @@ void launch_product(const Dims& d, const DevSetup& s, const FftPlan& pth, const 
                     double2* ZN, cudaStream_t st);
 void launch_zanalysis(const Dims& d, const DevSetup& s, const FftPlan& pz, const double2* ZN,
                       double2* Nout, cudaStream_t st);
+// Mixed precision (FP32 transforms and product of the perturbation, FP64
+// terms linear in it): curl with base-flow split, then the FP32 transforms.
+void launch_curl_split32(const Dims& d, const DevSetup& s, const double2* U, float2* W6,
+                         double2* Nlin, cudaStream_t st);
+void launch_zsynth32(const Dims& d, const DevSetup& s, const FftPlan& pz, const float2* W6,
+                     float2* Z6, cudaStream_t st);
+void launch_product32(const Dims& d, const DevSetup& s, const FftPlan& pth, const float2* Z6,
+                      float2* ZN, cudaStream_t st);
+void launch_zanalysis32(const Dims& d, const DevSetup& s, const FftPlan& pz, const float2* ZN,
+                        const double2* Nlin, double2* Nout, cudaStream_t st);
 struct SolveArgs {
   const double2* Uj;
   const double2* Na;

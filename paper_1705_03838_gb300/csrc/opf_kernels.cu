@@ -69,10 +69,15 @@ void launch_internal_to_abi(const Dims& d, const double2* U, double2* abi, int, 
 }
 
 // ------------------------------------------------------------------ curl (A1)
-template <typename V>
+// SPLIT: the laminar base flow U = (1 - r^2) z, Omega = 2r theta is removed
+// in FP64 (W6 then holds u', w'), and the terms linear in the perturbation,
+// U x w' + u' x Omega (+ U x Omega on (0,0)), are evaluated here per mode in
+// FP64 -- they are diagonal in r -- and written to Nlin in +- form.
+template <typename V, bool SPLIT>
 __global__ void __launch_bounds__(256) k_curl(Dims d, const double* __restrict__ d1,
                                               const double* __restrict__ rinv,
-                                              const double2* __restrict__ U, V* __restrict__ W6) {
+                                              const double2* __restrict__ U, V* __restrict__ W6,
+                                              double2* __restrict__ Nlin) {
   using T = typename Scalar<V>::T;
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= d.F) return;
@@ -113,17 +118,39 @@ __global__ void __launch_bounds__(256) k_curl(Dims d, const double* __restrict__
   // w_z = d_r u_theta + u_theta / r - i m~ u_r / r
   const double wzx = dtx + ri * utx + mt * ri * ury, wzy = dty + ri * uty - mt * ri * urx;
   const long w = ((long)m * N + n) * nk + kk;
+  double uzx = c.x, uzy = c.y, wtx2 = wtx, wty2 = wty;
+  if constexpr (SPLIT) {
+    const double r = 1.0 / ri, Ub = 1.0 - r * r, Ob = 2.0 * r;
+    const bool mean = (m == 0 && kk == d.K - 1);
+    if (mean) {
+      uzx -= Ub;
+      wtx2 -= Ob;
+    }
+    // N_r = -U w'_t - Omega u'_z, N_t = U w'_r, N_z = Omega u'_r
+    double nrx = -Ub * wtx2 - Ob * uzx, nry = -Ub * wty2 - Ob * uzy;
+    if (mean) nrx -= Ub * Ob;
+    const double ntx = Ub * (-xi), nty = Ub * xr;
+    Nlin[w] = double2{nrx - nty, nry + ntx};
+    Nlin[fs + w] = double2{nrx + nty, nry - ntx};
+    Nlin[2 * fs + w] = double2{Ob * urx, Ob * ury};
+  }
   W6[0 * fs + w] = V{(T)urx, (T)ury};
   W6[1 * fs + w] = V{(T)utx, (T)uty};
-  W6[2 * fs + w] = V{(T)c.x, (T)c.y};
+  W6[2 * fs + w] = V{(T)uzx, (T)uzy};
   W6[3 * fs + w] = V{(T)(-xi), (T)xr};
-  W6[4 * fs + w] = V{(T)wtx, (T)wty};
+  W6[4 * fs + w] = V{(T)wtx2, (T)wty2};
   W6[5 * fs + w] = V{(T)wzx, (T)wzy};
 }
 
 void launch_curl(const Dims& d, const DevSetup& s, const double2* U, double2* W6, cudaStream_t st) {
   const int nb = (int)((d.F + 255) / 256);
-  k_curl<double2><<<nb, 256, 0, st>>>(d, s.d1, s.rinv, U, W6);
+  k_curl<double2, false><<<nb, 256, 0, st>>>(d, s.d1, s.rinv, U, W6, nullptr);
+}
+
+void launch_curl_split32(const Dims& d, const DevSetup& s, const double2* U, float2* W6,
+                         double2* Nlin, cudaStream_t st) {
+  const int nb = (int)((d.F + 255) / 256);
+  k_curl<float2, true><<<nb, 256, 0, st>>>(d, s.d1, s.rinv, U, W6, Nlin);
 }
 
 // ------------------------------------------------------------------ z synthesis (A2)
@@ -157,6 +184,12 @@ __global__ void __launch_bounds__(128) k_zsynth(Dims d, FftPlan pz, const V* __r
 }
 
 size_t zsynth_smem(const Dims& d, int mc, size_t vb) { return (2 * (size_t)mc * (d.nz + 1) + d.nz) * vb; }
+
+void launch_zsynth32(const Dims& d, const DevSetup& s, const FftPlan& pz, const float2* W6,
+                     float2* Z6, cudaStream_t st) {
+  dim3 g((d.M + d.mcz - 1) / d.mcz, d.N, 6);
+  k_zsynth<float2><<<g, 128, zsynth_smem(d, d.mcz, sizeof(float2)), st>>>(d, pz, s.tw_z32, W6, Z6);
+}
 
 void launch_zsynth(const Dims& d, const DevSetup& s, const FftPlan& pz, const double2* W6,
                    double2* Z6, cudaStream_t st) {
@@ -224,6 +257,12 @@ __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* _
 
 size_t product_smem(const Dims& d, int zc, size_t vb) { return (2 * 3 * (size_t)zc * d.nth + d.nth) * vb; }
 
+void launch_product32(const Dims& d, const DevSetup& s, const FftPlan& pth, const float2* Z6,
+                      float2* ZN, cudaStream_t st) {
+  dim3 g((d.nz + d.zc - 1) / d.zc, d.N);
+  k_product<float2><<<g, 128, product_smem(d, d.zc, sizeof(float2)), st>>>(d, pth, s.tw_th32, Z6, ZN);
+}
+
 void launch_product(const Dims& d, const DevSetup& s, const FftPlan& pth, const double2* Z6,
                     double2* ZN, cudaStream_t st) {
   dim3 g((d.nz + d.zc - 1) / d.zc, d.N);
@@ -233,7 +272,8 @@ void launch_product(const Dims& d, const DevSetup& s, const FftPlan& pth, const 
 // ------------------------------------------------------------------ z analysis (A4)
 template <typename V>
 __global__ void __launch_bounds__(128) k_zanalysis(Dims d, FftPlan pz, const V* __restrict__ twz,
-                                                   const V* __restrict__ ZN, double2* __restrict__ Nout) {
+                                                   const V* __restrict__ ZN, const double2* __restrict__ Nlin,
+                                                   double2* __restrict__ Nout) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nz = d.nz, ld = nz + 1, M = d.M, K = d.K, nk = d.nk;
   const int MC = d.mca;
@@ -264,8 +304,19 @@ __global__ void __launch_bounds__(128) k_zanalysis(Dims d, FftPlan pz, const V* 
     double2 nz2 = double2{sc * z_.x, sc * z_.y};
     if (k == 0 && m == 0) nz2.x += 4.0 / d.Re;  // base driving force (laminar balance)
     const long o = ((long)m * d.N + n) * nk + kk;
-    Nout[o] = double2{nrx - nty, nry + ntx};           // N+ = N_r + i N_theta
-    Nout[fs + o] = double2{nrx + nty, nry - ntx};      // N- = N_r - i N_theta
+    double2 np = double2{nrx - nty, nry + ntx};        // N+ = N_r + i N_theta
+    double2 nm = double2{nrx + nty, nry - ntx};        // N- = N_r - i N_theta
+    if (Nlin) {  // terms linear in the perturbation, evaluated in FP64
+      const double2 a = Nlin[o], b = Nlin[fs + o], c = Nlin[2 * fs + o];
+      np.x += a.x;
+      np.y += a.y;
+      nm.x += b.x;
+      nm.y += b.y;
+      nz2.x += c.x;
+      nz2.y += c.y;
+    }
+    Nout[o] = np;
+    Nout[fs + o] = nm;
     Nout[2 * fs + o] = nz2;
   }
 }
@@ -277,7 +328,15 @@ size_t zanalysis_smem(const Dims& d, int mc, size_t vb) {
 void launch_zanalysis(const Dims& d, const DevSetup& s, const FftPlan& pz, const double2* ZN,
                       double2* Nout, cudaStream_t st) {
   dim3 g((d.M + d.mca - 1) / d.mca, d.N);
-  k_zanalysis<double2><<<g, 128, zanalysis_smem(d, d.mca, sizeof(double2)), st>>>(d, pz, s.tw_z, ZN, Nout);
+  k_zanalysis<double2><<<g, 128, zanalysis_smem(d, d.mca, sizeof(double2)), st>>>(d, pz, s.tw_z, ZN, nullptr,
+                                                                                  Nout);
+}
+
+void launch_zanalysis32(const Dims& d, const DevSetup& s, const FftPlan& pz, const float2* ZN,
+                        const double2* Nlin, double2* Nout, cudaStream_t st) {
+  dim3 g((d.M + d.mca - 1) / d.mca, d.N);
+  k_zanalysis<float2><<<g, 128, zanalysis_smem(d, d.mca, sizeof(float2)), st>>>(d, pz, s.tw_z32, ZN, Nlin,
+                                                                                Nout);
 }
 
 // ------------------------------------------------------------------ linear solve (A5-A7)
@@ -599,6 +658,9 @@ bool prepare_kernel_attrs(const Dims& d) {
   bool ok = cudaFuncSetAttribute(k_zsynth<double2>, a, optin) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(k_zanalysis<double2>, a, optin) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(k_product<double2>, a, optin) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_zsynth<float2>, a, optin) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_zanalysis<float2>, a, optin) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_product<float2>, a, optin) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(k_solve<16>, a, optin) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(k_solve<8>, a, optin) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(k_solve<4>, a, optin) == cudaSuccess;
