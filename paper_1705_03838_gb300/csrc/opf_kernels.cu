@@ -355,53 +355,65 @@ struct SolveDev {
 };
 
 // Banded substitution on one real right-hand side held in shared memory at
-// x[i * st], i < N: forward with the unit lower factor, backward with the
-// upper factor (13-slot rows: 8 L, 1/U_ii, 4 U).  Warps issue in order, so
-// each row first issues the work that does not depend on the row just
-// finished (next-row factor prefetch, older band terms) and ends with the one
-// multiply-add on the previous row's value, which is kept in a register.
-__device__ __forceinline__ void band_solve(const double* __restrict__ L, double* x, int st, int N) {
-  double cur[kLuSlots], nxt[kLuSlots];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) cur[q] = L[q];
-  double prev = 0.0;
-  for (int i = 0; i < N; ++i) {
-    const int ip = min(i + 1, N - 1);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) nxt[q] = L[ip * kLuSlots + q];
-    const int q0 = 8 - (i - row_lo_d(i, N));
-    double b0 = x[i * st], b1 = 0.0;
-#pragma unroll
-    for (int q = 0; q < 7; q += 2) {
-      if (q >= q0) b0 -= cur[q] * x[(i - 8 + q) * st];
-      if (q + 1 < 7 && q + 1 >= q0) b1 -= cur[q + 1] * x[(i - 7 + q) * st];
+// x[i * st], i < N, by a group of 4 consecutive lanes (column-oriented):
+// lane t keeps the partial sum of row c+1+t (and of row c+5+t for the wall
+// rows, whose lower band reaches 8); once row c is final its value is
+// broadcast and each lane subtracts its row's multiple of it.  Factor rows
+// use 13 slots (8 L entries for columns i-8..i-1, 1/U_ii, 4 U entries for
+// columns i+1..i+4); slots outside a row's band hold zeros.  All 32 lanes
+// of the warp must call this together (8 right-hand sides per warp).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ void band_solve4(const double* __restrict__ L, double* x, int st, int N) {
+  const int t = threadIdx.x & 3;
+  const unsigned full = 0xffffffffu;
+  constexpr int kAhead = 8;  // factor rows are pulled into L1 this many steps ahead
+  for (int q = 0; q < kAhead; ++q)
+    if (q + t < N) prefetch_l1(L + (q + t) * kLuSlots);
+  // forward: y = L^{-1} b
+  double sa = t < N ? x[t * st] : 0.0;
+  double sb = 4 + t < N ? x[(4 + t) * st] : 0.0;
+  int r = 1 + t;  // row whose partial sum is in sa after the shift
+  double la = r < N ? L[r * kLuSlots + 7 - t] : 0.0;
+  for (int c = 0; c < N; ++c) {
+    const double y = __shfl_sync(full, sa, 0, 4);
+    if (t == 0) x[c * st] = y;
+    const double next_b = (t == 3 && c + 8 < N) ? x[(c + 8) * st] : 0.0;
+    double san = __shfl_down_sync(full, sa, 1, 4);
+    const double sb0 = __shfl_sync(full, sb, 0, 4);
+    double sbn = __shfl_down_sync(full, sb, 1, 4);
+    if (t == 3) {
+      san = sb0;
+      sbn = next_b;
     }
-    b0 += b1;
-    if (i > 0) b0 -= cur[7] * prev;
-    x[i * st] = b0;
-    prev = b0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) cur[q] = nxt[q];
+    sa = san - la * y;
+    if (c >= N - 9) {  // wall rows: band reaches 8 below the diagonal
+      const int r2 = c + 5 + t;
+      if (r2 < N) sbn -= L[r2 * kLuSlots + 3 - t] * y;
+    }
+    sb = sbn;
+    if (c + 1 + kAhead + t < N) prefetch_l1(L + (c + 1 + kAhead + t) * kLuSlots);
+    r = c + 2 + t;
+    la = r < N ? L[r * kLuSlots + 7 - t] : 0.0;
   }
-#pragma unroll
-  for (int q = 8; q < kLuSlots; ++q) cur[q] = L[(N - 1) * kLuSlots + q];
-  prev = 0.0;
-  for (int i = N - 1; i >= 0; --i) {
-    const int im = max(i - 1, 0);
-#pragma unroll
-    for (int q = 8; q < kLuSlots; ++q) nxt[q] = L[im * kLuSlots + q];
-    const int nu = min(i + 4, N - 1) - i;
-    double v0 = x[i * st], v1 = 0.0;
-    if (nu >= 2) v0 -= cur[10] * x[(i + 2) * st];
-    if (nu >= 3) v1 -= cur[11] * x[(i + 3) * st];
-    if (nu >= 4) v0 -= cur[12] * x[(i + 4) * st];
-    v0 += v1;
-    if (nu >= 1) v0 -= cur[9] * prev;
-    v0 *= cur[8];
-    x[i * st] = v0;
-    prev = v0;
-#pragma unroll
-    for (int q = 8; q < kLuSlots; ++q) cur[q] = nxt[q];
+  // backward: x = U^{-1} y
+  sa = N - 1 - t >= 0 ? x[(N - 1 - t) * st] : 0.0;
+  r = N - 2 - t;
+  double ua = r >= 0 ? L[r * kLuSlots + 9 + t] : 0.0;
+  double rinv = L[(N - 1) * kLuSlots + 8];
+  for (int c = N - 1; c >= 0; --c) {
+    const double xc = __shfl_sync(full, sa, 0, 4) * rinv;
+    if (t == 0) x[c * st] = xc;
+    const double next_y = (t == 3 && c - 4 >= 0) ? x[(c - 4) * st] : 0.0;
+    double san = __shfl_down_sync(full, sa, 1, 4);
+    if (t == 3) san = next_y;
+    sa = san - ua * xc;
+    if (c - 2 - kAhead - t >= 0) prefetch_l1(L + (c - 2 - kAhead - t) * kLuSlots);
+    r = c - 2 - t;
+    ua = r >= 0 ? L[r * kLuSlots + 9 + t] : 0.0;
+    rinv = c >= 1 ? L[(c - 1) * kLuSlots + 8] : 0.0;
   }
 }
 
@@ -413,8 +425,8 @@ template <int T>
 __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = d.N, nk = d.nk, M = d.M, K = d.K;
-  constexpr int NT = 6 * T;   // velocity chains
-  constexpr int NB = 24 * T;  // threads in the block (row-parallel phases)
+  constexpr int NT = 6 * T;   // velocity right-hand sides (chains)
+  constexpr int NB = 24 * T;  // threads: 4 lanes per velocity chain
   double2* NE = (double2*)smraw;        // [3][N][T]  N_eff
   double2* S = NE + 3 * N * T;          // [N][T]     N+ + N-, later d_r p
   double2* P = S + N * T;               // [N][T]     pressure
@@ -422,6 +434,8 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   double* X = (double*)(coef + 4 * T);  // [N][6T]    velocity chains
   double* W1 = X + N * NT;              // [2][N][9]  first-derivative stencils
   double* misc = W1 + 2 * N * 9;        // [2]        flux correction
+  double2* UJ = (double2*)(misc + 2);   // [3][N][T]  u_j
+  double* BS = (double*)(UJ + 3 * N * T);  // [T][6][N] influence basis of each mode's |k|
   const int m = blockIdx.y, kk0 = blockIdx.x * T, tid = threadIdx.x;
   const int mt = d.m_p * m, ps = mt & 1, pv = ps ^ 1;
   const double ci = 1.0 / (d.c * d.dt), cu = (1.0 - d.c) / d.c;
@@ -441,6 +455,12 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
       v.y += a.wb * w.y;
     }
     NE[(f * N + i) * T + mi] = v;
+    UJ[(f * N + i) * T + mi] = a.Uj[g];
+  }
+  for (int e = tid; e < 6 * N * T; e += NB) {
+    const int i = e % N, b = (e / N) % 6, mi = e / (6 * N);
+    const int ik = abs(min(kk0 + mi, nk - 1) - (K - 1));
+    BS[(mi * 6 + b) * N + i] = s.basis[((long)(ik * M + m) * 6 + b) * N + i];
   }
   __syncthreads();
   for (int e = tid; e < N * T; e += NB) {
@@ -476,11 +496,11 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   __syncthreads();
 
   // ---- pressure-Poisson solve (provisional dp/dr(1) = 0; (0,0): p(1) = 0)
-  if (tid < 2 * T) {
-    const int part = tid & 1, mi = tid >> 1;
+  if (tid < 8 * T) {  // 2T chains x 4 lanes
+    const int j = tid >> 2, part = j & 1, mi = j >> 1;
     const int k = min(kk0 + mi, nk - 1) - (K - 1), ik = abs(k);
     const int op = (ik == 0 && m == 0) ? K * M : ik * M + m;
-    band_solve(s.luP + (long)op * N * kLuSlots, (double*)P + 2 * mi + part, 2 * T, N);
+    band_solve4(s.luP + (long)op * N * kLuSlots, (double*)P + 2 * mi + part, 2 * T, N);
   }
   __syncthreads();
 
@@ -514,7 +534,7 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
       } else {
         gp = part == 0 ? -ak * pp.y : ak * pp.x;
       }
-      const double2 u = a.Uj[f * fs + base + (long)i * nk + kk];
+      const double2 u = UJ[(f * N + i) * T + mi];
       const double2 ne = NE[(f * N + i) * T + mi];
       b = ci * (part ? u.y : u.x) + (part ? ne.y : ne.x) - gp;
     }
@@ -523,12 +543,12 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   __syncthreads();
 
   // ---- implicit viscous solves (1/dt - cL) v = rhs, Dirichlet 0
-  if (tid < NT) {
-    const int part = tid & 1, mi = (tid >> 1) % T, f = (tid >> 1) / T;
-    (void)part;
+  {  // 6T chains x 4 lanes = all threads
+    const int c = tid >> 2;
+    const int mi = (c >> 1) % T, f = (c >> 1) / T;
     const int k = min(kk0 + mi, nk - 1) - (K - 1), ik = abs(k);
     const int op = ik * s.nJ + s.hop[3 * m + f];
-    band_solve(s.luH + (long)op * N * kLuSlots, X + tid, NT, N);
+    band_solve4(s.luH + (long)op * N * kLuSlots, X + c, NT, N);
   }
   __syncthreads();
 
@@ -536,8 +556,7 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   for (int e = tid; e < N * NT; e += NB) {
     const int c = e % NT, i = e / NT;
     const int part = c & 1, mi = (c >> 1) % T, f = (c >> 1) / T;
-    const int kk = min(kk0 + mi, nk - 1);
-    const double2 u = a.Uj[f * fs + base + (long)i * nk + kk];
+    const double2 u = UJ[(f * N + i) * T + mi];
     X[i * NT + c] -= cu * (part ? u.y : u.x);
   }
   __syncthreads();
@@ -578,8 +597,8 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   for (int e = tid; e < N * NT; e += NB) {
     const int c = e % NT, i = e / NT;
     const int part = c & 1, mi = (c >> 1) % T, f = (c >> 1) / T;
-    const int k = min(kk0 + mi, nk - 1) - (K - 1), ik = abs(k);
-    const double* Bv = s.basis + ((long)(ik * M + m) * 6) * N;
+    const int k = min(kk0 + mi, nk - 1) - (K - 1);
+    const double* Bv = BS + mi * 6 * N;
     const double2 a0 = coef[mi * 4 + 0], ax = coef[mi * 4 + 1 + f];
     const double sk = k > 0 ? 1.0 : (k < 0 ? -1.0 : 0.0);
     const double c0 = f == 2 ? (part ? sk * a0.x : -sk * a0.y) : (part ? a0.y : a0.x);
@@ -617,16 +636,19 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
 
 static size_t solve_smem(int N, int T);
 
-// Largest tile that still gives every SM a block and fits 200 KB of shared memory.
+// Tile of T modes: 4 keeps every warp of the sequential phases full (8
+// right-hand sides per warp) with the most blocks; larger tiles only when
+// there are many modes per SM.
 static int solve_tile(const Dims& d) {
   const long modes = (long)d.nk * d.M;
-  for (int T : {16, 8})
-    if (modes / T >= 152 && solve_smem(d.N, T) <= 200 * 1024) return T;
+  if (modes / 16 >= 8 * 152 && solve_smem(d.N, 16) <= 200 * 1024) return 16;
+  if (modes / 8 >= 4 * 152 && solve_smem(d.N, 8) <= 200 * 1024) return 8;
   return 4;
 }
 
 static size_t solve_smem(int N, int T) {
-  return (size_t)(5 * N * T + 4 * T) * 16 + (size_t)6 * N * T * 8 + (size_t)(2 * N * 9 + 2) * 8;
+  return (size_t)(5 * N * T + 4 * T) * 16 + (size_t)6 * N * T * 8 + (size_t)(2 * N * 9 + 2) * 8 +
+         (size_t)3 * N * T * 16 + (size_t)6 * N * T * 8;
 }
 
 // Chunk sizes keep every transform block within ~96 KB of shared memory (two
