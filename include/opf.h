@@ -121,6 +121,35 @@ int opf_set_stream(opf_t* h, void* stream);
 int opf_kernel_times(opf_t* h, int cap, int* count, const char** names,
                      double* total_ms, int* launches, int reset);
 
+/* ---- Ensembles: many independent trajectories stepped together -----------
+ * The paper runs one trajectory per job; this batches count trajectories,
+ * each with its own resolution and parameters, into one CUDA graph per step:
+ * trajectories with equal (N, K, M, m_p, alpha) share every kernel launch
+ * (one launch covers all of them), while Re and dt may differ per trajectory
+ * (each gets its own radial operators).  Arrays N..dt have count entries;
+ * trajectory i's state uses the layout above with its own (N, K, M).
+ * NULL on invalid arguments or allocation failure (opf_last_error). */
+typedef struct opf_ens opf_ens_t;
+opf_ens_t* opf_ens_create(int count, const int* N, const int* K, const int* M, const int* m_p,
+                          const double* alpha, const double* Re, const double* dt);
+void opf_ens_destroy(opf_ens_t* e);
+int opf_ens_count(opf_ens_t* e, int* count);
+/* State of trajectory i (host or device buffer, state layout, its own sizes). */
+int opf_ens_set_state(opf_ens_t* e, int i, const double* coeffs);
+int opf_ens_get_state(opf_ens_t* e, int i, double* coeffs);
+int opf_ens_set_state_device(opf_ens_t* e, int i, const double* d_coeffs);
+int opf_ens_get_state_device(opf_ens_t* e, int i, double* d_coeffs);
+/* Advance every trajectory n steps (same scheme as opf_step); synchronous. */
+int opf_ens_step(opf_ens_t* e, int n);
+/* E, I, D of trajectory i (as opf_energy) and its simulated time. */
+int opf_ens_energy(opf_ens_t* e, int i, double out[3]);
+int opf_ens_get_time(opf_ens_t* e, int i, double* t);
+/* Same options as opf_set_option, applied to all trajectories. */
+int opf_ens_set_option(opf_ens_t* e, const char* key, double value);
+int opf_ens_set_stream(opf_ens_t* e, void* stream);
+int opf_ens_kernel_times(opf_ens_t* e, int cap, int* count, const char** names,
+                         double* total_ms, int* launches, int reset);
+
 /* No counterpart in the paper: an allocation-free variant of opf_nonlinear
  * for callers that must not allocate device memory when they call (their
  * device memory is all owned by their own pool, cudaMalloc/cudaFree could

@@ -1,9 +1,17 @@
 // C ABI of libopf (declared in include/opf.h): handle life cycle, state
-// transfer, and the predictor-corrector orchestration of section 2.
+// transfer, and the predictor-corrector orchestration of section 2, for one
+// trajectory (opf_t) and for batched ensembles of trajectories (opf_ens_t).
+//
+// A Group holds B trajectories of one shape (N, K, M, m_p, alpha) in two
+// device arenas -- work buffers and setup arrays -- with fixed strides, so
+// every kernel launch covers all B trajectories (grid z).  A Runner records
+// one time step of a list of groups as a CUDA graph and replays it.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "opf_internal.h"
@@ -30,178 +38,12 @@ void set_last_error(const std::string& m) { g_err = m; }
 }  // namespace opf
 
 namespace {
-constexpr int kMaxSlots = 32;
+
+constexpr int kMaxSlots = 128;
 const char* kNames[] = {"curl", "zsynth", "product", "zanalysis", "solve"};
 constexpr int kNumNames = 5;
-}  // namespace
 
-struct opf_ctx {
-  opf::Setup hs;
-  opf::DevSetup ds;
-  opf::Dims d{};
-  opf::FftPlan pz{}, pth{};
-  double2 *U = nullptr, *U1 = nullptr, *Nj = nullptr, *Nq = nullptr, *W6 = nullptr;
-  double2 *Z6 = nullptr, *ZN = nullptr, *abi = nullptr, *tmpU = nullptr;
-  float2 *W6f = nullptr, *Z6f = nullptr, *ZNf = nullptr;  // mixed-precision intermediates
-  double2* Nlin = nullptr;                                // FP64 linear terms (mixed)
-  double *beta_p = nullptr, *partial = nullptr, *out3 = nullptr, *out2 = nullptr;
-  int* flag = nullptr;
-  int nblk_energy = 0;
-  cudaStream_t own = nullptr, stream = nullptr;
-  int precision = 0, n_corr = 1, use_graph = 1, timing = 0;
-  cudaGraphExec_t gexec = nullptr;
-  double time = 0.0;
-  int device = 0;
-  std::vector<void*> allocs;
-  // per-launch timing
-  cudaEvent_t ev[kMaxSlots][2];
-  int slot_name[kMaxSlots];
-  int nslots = 0, graph_nslots = 0;
-  bool events_made = false;
-  double tot_ms[kNumNames] = {0};
-  int tot_n[kNumNames] = {0};
-};
-
-namespace {
-
-template <typename P>
-int dalloc(opf_ctx* h, P** p, size_t bytes) {
-  void* q = nullptr;
-  cudaError_t e = cudaMalloc(&q, bytes);
-  if (e != cudaSuccess) return fail(OPF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-  h->allocs.push_back(q);
-  *p = (P*)q;
-  return OPF_OK;
-}
-
-template <typename T>
-int upload(opf_ctx* h, T** dst, const std::vector<T>& v) {
-  int rc = dalloc(h, dst, v.size() * sizeof(T) + 16);
-  if (rc) return rc;
-  CU(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
-  return OPF_OK;
-}
-
-int upload_setup(opf_ctx* h) {
-  const opf::Setup& s = h->hs;
-  int rc;
-  if ((rc = upload(h, &h->ds.rinv, s.rinv))) return rc;
-  if ((rc = upload(h, &h->ds.d1, s.d1))) return rc;
-  if ((rc = upload(h, &h->ds.wq, s.wq))) return rc;
-  if ((rc = upload(h, &h->ds.hop, s.hop))) return rc;
-  if ((rc = upload(h, &h->ds.luH, s.luH))) return rc;
-  if ((rc = upload(h, &h->ds.luP, s.luP))) return rc;
-  if ((rc = upload(h, &h->ds.basis, s.basis))) return rc;
-  double* ai = nullptr;
-  if ((rc = upload(h, &ai, s.ainv))) return rc;
-  h->ds.ainv = (double2*)ai;
-  if ((rc = upload(h, &h->ds.G, s.G))) return rc;
-  auto twiddles = [&](int n, double2** out, float2** out32) -> int {
-    std::vector<double2> t(n);
-    std::vector<float2> t32(n);
-    for (int i = 0; i < n; ++i) {
-      const long double a = 2.0L * 3.14159265358979323846264338327950288L * i / n;
-      t[i] = double2{(double)cosl(a), (double)sinl(a)};
-      t32[i] = float2{(float)t[i].x, (float)t[i].y};
-    }
-    int r2 = upload(h, out, t);
-    if (r2) return r2;
-    return upload(h, out32, t32);
-  };
-  if ((rc = twiddles(h->d.nz, &h->ds.tw_z, &h->ds.tw_z32))) return rc;
-  if ((rc = twiddles(h->d.nth, &h->ds.tw_th, &h->ds.tw_th32))) return rc;
-  return OPF_OK;
-}
-
-void free_all(opf_ctx* h) {
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  h->gexec = nullptr;
-  for (void* p : h->allocs) cudaFree(p);
-  h->allocs.clear();
-  if (h->events_made)
-    for (int i = 0; i < kMaxSlots; ++i) {
-      cudaEventDestroy(h->ev[i][0]);
-      cudaEventDestroy(h->ev[i][1]);
-    }
-  if (h->own) cudaStreamDestroy(h->own);
-}
-
-// ---- step orchestration
-void begin(opf_ctx* h, int name) {
-  if (!h->timing || h->nslots >= kMaxSlots) return;
-  h->slot_name[h->nslots] = name;
-  // external: inside stream capture this becomes an event-record node
-  cudaEventRecordWithFlags(h->ev[h->nslots][0], h->stream, cudaEventRecordExternal);
-}
-void end(opf_ctx* h) {
-  if (!h->timing || h->nslots >= kMaxSlots) return;
-  cudaEventRecordWithFlags(h->ev[h->nslots][1], h->stream, cudaEventRecordExternal);
-  ++h->nslots;
-}
-
-void enqueue_nonlinear(opf_ctx* h, const double2* U, double2* Nout) {
-  const opf::Dims& d = h->d;
-  if (h->precision == 1) {
-    begin(h, 0);
-    opf::launch_curl_split32(d, h->ds, U, h->W6f, h->Nlin, h->stream);
-    end(h);
-    begin(h, 1);
-    opf::launch_zsynth32(d, h->ds, h->pz, h->W6f, h->Z6f, h->stream);
-    end(h);
-    begin(h, 2);
-    opf::launch_product32(d, h->ds, h->pth, h->Z6f, h->ZNf, h->stream);
-    end(h);
-    begin(h, 3);
-    opf::launch_zanalysis32(d, h->ds, h->pz, h->ZNf, h->Nlin, Nout, h->stream);
-    end(h);
-    return;
-  }
-  begin(h, 0);
-  opf::launch_curl(d, h->ds, U, h->W6, h->stream);
-  end(h);
-  begin(h, 1);
-  opf::launch_zsynth(d, h->ds, h->pz, h->W6, h->Z6, h->stream);
-  end(h);
-  begin(h, 2);
-  opf::launch_product(d, h->ds, h->pth, h->Z6, h->ZN, h->stream);
-  end(h);
-  begin(h, 3);
-  opf::launch_zanalysis(d, h->ds, h->pz, h->ZN, Nout, h->stream);
-  end(h);
-}
-
-void enqueue_solve(opf_ctx* h, const double2* Na, const double2* Nb, double wa, double wb,
-                   double2* Uout) {
-  opf::SolveArgs a{h->U, Na, Nb, wa, wb, Uout, h->beta_p};
-  begin(h, 4);
-  opf::launch_solve(h->d, h->ds, a, h->hs.flux_G, h->hs.nJ, h->stream);
-  end(h);
-}
-
-// One predictor-corrector step (section 2): predictor with N_j, then n_corr
-// corrector passes with c N^q + (1 - c) N_j, each solved from u_j.
-void enqueue_step(opf_ctx* h) {
-  const double c = h->d.c;
-  enqueue_nonlinear(h, h->U, h->Nj);
-  enqueue_solve(h, h->Nj, nullptr, 1.0, 0.0, h->U1);
-  for (int q = 0; q < h->n_corr; ++q) {
-    enqueue_nonlinear(h, h->U1, h->Nq);
-    enqueue_solve(h, h->Nq, h->Nj, c, 1.0 - c, q == h->n_corr - 1 ? h->U : h->U1);
-  }
-}
-
-int harvest_timing(opf_ctx* h) {
-  if (!h->timing) return OPF_OK;
-  for (int i = 0; i < h->nslots; ++i) {
-    float ms = 0.f;
-    CU(cudaEventElapsedTime(&ms, h->ev[i][0], h->ev[i][1]));
-    h->tot_ms[h->slot_name[i]] += ms;
-    h->tot_n[h->slot_name[i]] += 1;
-  }
-  return OPF_OK;
-}
-
-int check_handle(opf_t* h) { return h ? OPF_OK : fail(OPF_EINVAL, "NULL handle"); }
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 bool smooth235(int n) {
   for (int p : {2, 3, 5})
@@ -209,37 +51,87 @@ bool smooth235(int n) {
   return n == 1;
 }
 
-}  // namespace
+// ------------------------------------------------------------------ Group
+struct Group {
+  opf::Dims d{};
+  opf::FftPlan pz{}, pth{};
+  int nJ = 0;
+  bool shared_setup = false;
+  std::vector<double> Re, dt, time;  // per trajectory
+  opf::DevSetup ds;                  // trajectory 0's setup arrays
+  char* parena = nullptr;
+  char* sarena = nullptr;
+  size_t pstride = 0, sstride = 0;
+  // trajectory 0's work buffers (trajectory b: + b * sstride bytes)
+  double2 *U = nullptr, *U1 = nullptr, *Nj = nullptr, *Nq = nullptr, *W6 = nullptr;
+  double2 *Z6 = nullptr, *ZN = nullptr, *abi = nullptr, *tmpU = nullptr, *Nlin = nullptr;
+  float2 *W6f = nullptr, *Z6f = nullptr, *ZNf = nullptr;
+  double *beta_p = nullptr, *partial = nullptr, *out3 = nullptr, *out2 = nullptr;
+  int* flag = nullptr;
+  int nblk_energy = 0;
 
-extern "C" {
+  template <typename P>
+  P* at(P* p, int b) const {
+    return (P*)((char*)p + (size_t)b * sstride);
+  }
+  opf::DevSetup setup_of(int b) const {
+    if (shared_setup || b == 0) return ds;
+    opf::DevSetup s = ds;
+    const size_t o = (size_t)b * pstride;
+    auto sh = [&](auto* p) { return (decltype(p))((char*)p + o); };
+    s.prm = sh(s.prm);
+    s.rinv = sh(s.rinv);
+    s.d1 = sh(s.d1);
+    s.wq = sh(s.wq);
+    s.hop = sh(s.hop);
+    s.luH = sh(s.luH);
+    s.luP = sh(s.luP);
+    s.basis = sh(s.basis);
+    s.ainv = sh(s.ainv);
+    s.G = sh(s.G);
+    s.tw_z = sh(s.tw_z);
+    s.tw_th = sh(s.tw_th);
+    s.tw_z32 = sh(s.tw_z32);
+    s.tw_th32 = sh(s.tw_th32);
+    return s;
+  }
+  // launch dimensions of trajectory b alone (pointers offset on the host)
+  opf::Dims single(int b) const {
+    opf::Dims e = d;
+    e.B = 1;
+    e.ss = 0;
+    e.ps = 0;
+    e.prm = setup_of(b).prm;
+    return e;
+  }
+};
 
-const char* opf_last_error(void) { return g_err.c_str(); }
+void group_free(Group* g) {
+  if (g->sarena) cudaFree(g->sarena);
+  if (g->parena) cudaFree(g->parena);
+  g->sarena = g->parena = nullptr;
+}
 
-opf_t* opf_create(int N, int K, int M, int m_p, double alpha, double Re, double dt) {
-  if (N < 9 || K < 1 || M < 1 || m_p < 1 || !(alpha > 0) || !(Re > 0) || !(dt > 0)) {
-    fail(OPF_EINVAL, "opf_create: need N>=9, K>=1, M>=1, m_p>=1, alpha>0, Re>0, dt>0");
-    return nullptr;
+struct Layout {
+  size_t off = 0;
+  size_t add(size_t bytes) {
+    const size_t o = off;
+    off = align256(off + bytes);
+    return o;
   }
-  if (!smooth235(3 * K) || !smooth235(3 * M)) {
-    fail(OPF_EINVAL, "opf_create: 3K and 3M must have no prime factor other than 2, 3, 5");
-    return nullptr;
-  }
-  opf_ctx* h = new opf_ctx();
-  h->hs.N = N;
-  h->hs.K = K;
-  h->hs.M = M;
-  h->hs.m_p = m_p;
-  h->hs.alpha = alpha;
-  h->hs.Re = Re;
-  h->hs.dt = dt;
-  h->hs.c = 0.5;
-  std::string err;
-  if (!opf::build_setup(&h->hs, &err)) {
-    fail(OPF_EINVAL, "opf_create: " + err);
-    delete h;
-    return nullptr;
-  }
-  opf::Dims& d = h->d;
+};
+
+// Build host setups, lay out and fill both arenas for B trajectories of one
+// shape with per-trajectory Re and dt (one shared setup when all are equal).
+int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, const double* Re,
+                const double* dt) {
+  if (N < 9 || K < 1 || M < 1 || m_p < 1 || !(alpha > 0) || B < 1)
+    return fail(OPF_EINVAL, "need N>=9, K>=1, M>=1, m_p>=1, alpha>0");
+  for (int b = 0; b < B; ++b)
+    if (!(Re[b] > 0) || !(dt[b] > 0)) return fail(OPF_EINVAL, "need Re>0, dt>0");
+  if (!smooth235(3 * K) || !smooth235(3 * M))
+    return fail(OPF_EINVAL, "3K and 3M must have no prime factor other than 2, 3, 5");
+  opf::Dims& d = g->d;
   d.N = N;
   d.K = K;
   d.M = M;
@@ -248,171 +140,510 @@ opf_t* opf_create(int N, int K, int M, int m_p, double alpha, double Re, double 
   d.nz = 3 * K;
   d.nth = 3 * M;
   d.alpha = alpha;
-  d.Re = Re;
-  d.dt = dt;
+  d.Re = Re[0];
+  d.dt = dt[0];
   d.c = 0.5;
   d.F = (long)M * N * d.nk;
+  d.B = B;
   opf::choose_chunks(&d);
-  if (!opf::make_plan(d.nz, &h->pz) || !opf::make_plan(d.nth, &h->pth)) {
-    fail(OPF_EINVAL, "opf_create: no FFT plan for 3K or 3M");
-    delete h;
-    return nullptr;
+  if (!opf::make_plan(d.nz, &g->pz) || !opf::make_plan(d.nth, &g->pth))
+    return fail(OPF_EINVAL, "no FFT plan for 3K or 3M");
+  g->Re.assign(Re, Re + B);
+  g->dt.assign(dt, dt + B);
+  g->time.assign(B, 0.0);
+  g->shared_setup = true;
+  for (int b = 1; b < B; ++b)
+    if (Re[b] != Re[0] || dt[b] != dt[0]) g->shared_setup = false;
+  const int nsetup = g->shared_setup ? 1 : B;
+
+  std::vector<opf::Setup> hs(nsetup);
+  for (int b = 0; b < nsetup; ++b) {
+    opf::Setup& s = hs[b];
+    s.N = N;
+    s.K = K;
+    s.M = M;
+    s.m_p = m_p;
+    s.alpha = alpha;
+    s.Re = Re[b];
+    s.dt = dt[b];
+    s.c = 0.5;
+    std::string err;
+    if (!opf::build_setup(&s, &err)) return fail(OPF_EINVAL, err);
   }
-  auto bail = [&](int) -> opf_t* {
-    std::string keep = g_err;
-    free_all(h);
+  g->nJ = hs[0].nJ;
+
+  // setup arena layout (identical sizes for every trajectory of the shape)
+  const opf::Setup& s0 = hs[0];
+  Layout pl;
+  const size_t o_prm = pl.add(opf::kPrmCount * sizeof(double));
+  const size_t o_rinv = pl.add(s0.rinv.size() * 8);
+  const size_t o_d1 = pl.add(s0.d1.size() * 8);
+  const size_t o_wq = pl.add(s0.wq.size() * 8);
+  const size_t o_hop = pl.add(s0.hop.size() * sizeof(int));
+  const size_t o_luH = pl.add(s0.luH.size() * 8);
+  const size_t o_luP = pl.add(s0.luP.size() * 8);
+  const size_t o_basis = pl.add(s0.basis.size() * 8);
+  const size_t o_ainv = pl.add(s0.ainv.size() * 8);
+  const size_t o_G = pl.add(s0.G.size() * 8);
+  const size_t o_twz = pl.add(d.nz * sizeof(double2));
+  const size_t o_twt = pl.add(d.nth * sizeof(double2));
+  const size_t o_twz32 = pl.add(d.nz * sizeof(float2));
+  const size_t o_twt32 = pl.add(d.nth * sizeof(float2));
+  g->pstride = pl.off;
+  if (cudaMalloc((void**)&g->parena, g->pstride * nsetup) != cudaSuccess)
+    return fail(OPF_ENOMEM, "cudaMalloc of setup arrays failed");
+  std::vector<char> host(g->pstride, 0);
+  auto put = [&](size_t o, const void* src, size_t bytes) { std::memcpy(host.data() + o, src, bytes); };
+  std::vector<double2> twz(d.nz), twt(d.nth);
+  std::vector<float2> twz32(d.nz), twt32(d.nth);
+  auto tw = [](int n, std::vector<double2>& t, std::vector<float2>& t32) {
+    for (int i = 0; i < n; ++i) {
+      const long double a = 2.0L * 3.14159265358979323846264338327950288L * i / n;
+      t[i] = double2{(double)cosl(a), (double)sinl(a)};
+      t32[i] = float2{(float)t[i].x, (float)t[i].y};
+    }
+  };
+  tw(d.nz, twz, twz32);
+  tw(d.nth, twt, twt32);
+  for (int b = 0; b < nsetup; ++b) {
+    const opf::Setup& s = hs[b];
+    double prm[opf::kPrmCount] = {0};
+    prm[opf::kPrmRe] = s.Re;
+    prm[opf::kPrmDt] = s.dt;
+    prm[opf::kPrmC] = s.c;
+    prm[opf::kPrmSumWG] = s.flux_G;
+    put(o_prm, prm, sizeof prm);
+    put(o_rinv, s.rinv.data(), s.rinv.size() * 8);
+    put(o_d1, s.d1.data(), s.d1.size() * 8);
+    put(o_wq, s.wq.data(), s.wq.size() * 8);
+    put(o_hop, s.hop.data(), s.hop.size() * sizeof(int));
+    put(o_luH, s.luH.data(), s.luH.size() * 8);
+    put(o_luP, s.luP.data(), s.luP.size() * 8);
+    put(o_basis, s.basis.data(), s.basis.size() * 8);
+    put(o_ainv, s.ainv.data(), s.ainv.size() * 8);
+    put(o_G, s.G.data(), s.G.size() * 8);
+    put(o_twz, twz.data(), d.nz * sizeof(double2));
+    put(o_twt, twt.data(), d.nth * sizeof(double2));
+    put(o_twz32, twz32.data(), d.nz * sizeof(float2));
+    put(o_twt32, twt32.data(), d.nth * sizeof(float2));
+    CU(cudaMemcpy(g->parena + (size_t)b * g->pstride, host.data(), g->pstride, cudaMemcpyHostToDevice));
+  }
+  char* P = g->parena;
+  g->ds.prm = (double*)(P + o_prm);
+  g->ds.rinv = (double*)(P + o_rinv);
+  g->ds.d1 = (double*)(P + o_d1);
+  g->ds.wq = (double*)(P + o_wq);
+  g->ds.hop = (int*)(P + o_hop);
+  g->ds.luH = (double*)(P + o_luH);
+  g->ds.luP = (double*)(P + o_luP);
+  g->ds.basis = (double*)(P + o_basis);
+  g->ds.ainv = (double2*)(P + o_ainv);
+  g->ds.G = (double*)(P + o_G);
+  g->ds.tw_z = (double2*)(P + o_twz);
+  g->ds.tw_th = (double2*)(P + o_twt);
+  g->ds.tw_z32 = (float2*)(P + o_twz32);
+  g->ds.tw_th32 = (float2*)(P + o_twt32);
+  d.ps = g->shared_setup ? 0 : (long)g->pstride;
+  d.prm = g->ds.prm;
+
+  // work arena: FP32 intermediates alias the FP64 ones (one precision per step)
+  const size_t F16 = (size_t)d.F * sizeof(double2);
+  const size_t P16 = (size_t)N * d.nz * M * sizeof(double2);
+  g->nblk_energy = opf::energy_blocks(d);
+  Layout sl;
+  const size_t o_U = sl.add(3 * F16), o_U1 = sl.add(3 * F16), o_Nj = sl.add(3 * F16);
+  const size_t o_Nq = sl.add(3 * F16), o_W6 = sl.add(6 * F16), o_Z6 = sl.add(6 * P16);
+  const size_t o_ZN = sl.add(3 * P16), o_abi = sl.add(3 * F16), o_tmp = sl.add(3 * F16);
+  const size_t o_Nlin = sl.add(3 * F16), o_beta = sl.add(16), o_out3 = sl.add(32);
+  const size_t o_out2 = sl.add(16), o_flag = sl.add(16);
+  const size_t o_part = sl.add((size_t)2 * g->nblk_energy * sizeof(double));
+  g->sstride = sl.off;
+  if (cudaMalloc((void**)&g->sarena, g->sstride * B) != cudaSuccess)
+    return fail(OPF_ENOMEM, "cudaMalloc of work buffers failed");
+  CU(cudaMemset(g->sarena, 0, g->sstride * B));
+  char* S = g->sarena;
+  g->U = (double2*)(S + o_U);
+  g->U1 = (double2*)(S + o_U1);
+  g->Nj = (double2*)(S + o_Nj);
+  g->Nq = (double2*)(S + o_Nq);
+  g->W6 = (double2*)(S + o_W6);
+  g->Z6 = (double2*)(S + o_Z6);
+  g->ZN = (double2*)(S + o_ZN);
+  g->W6f = (float2*)g->W6;
+  g->Z6f = (float2*)g->Z6;
+  g->ZNf = (float2*)g->ZN;
+  g->abi = (double2*)(S + o_abi);
+  g->tmpU = (double2*)(S + o_tmp);
+  g->Nlin = (double2*)(S + o_Nlin);
+  g->beta_p = (double*)(S + o_beta);
+  g->out3 = (double*)(S + o_out3);
+  g->out2 = (double*)(S + o_out2);
+  g->flag = (int*)(S + o_flag);
+  g->partial = (double*)(S + o_part);
+  d.ss = (long)g->sstride;
+  if (!opf::prepare_kernel_attrs(d))
+    return fail(OPF_EINVAL, "resolution needs more shared memory than a block has");
+  return OPF_OK;
+}
+
+// ------------------------------------------------------------------ Runner
+struct Runner {
+  std::vector<Group*> groups;
+  cudaStream_t own = nullptr, stream = nullptr;
+  int precision = 0, n_corr = 1, use_graph = 1, timing = 0;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t ev[kMaxSlots][2];
+  int slot_name[kMaxSlots];
+  int nslots = 0, graph_nslots = 0;
+  bool events_made = false;
+  double tot_ms[kNumNames] = {0};
+  int tot_n[kNumNames] = {0};
+
+  void begin(int name) {
+    if (!timing || nslots >= kMaxSlots) return;
+    slot_name[nslots] = name;
+    // external: inside stream capture this becomes an event-record node
+    cudaEventRecordWithFlags(ev[nslots][0], stream, cudaEventRecordExternal);
+  }
+  void end() {
+    if (!timing || nslots >= kMaxSlots) return;
+    cudaEventRecordWithFlags(ev[nslots][1], stream, cudaEventRecordExternal);
+    ++nslots;
+  }
+  void drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+  }
+};
+
+int runner_init(Runner* r) {
+  CU(cudaStreamCreateWithFlags(&r->own, cudaStreamNonBlocking));
+  r->stream = r->own;
+  for (int i = 0; i < kMaxSlots; ++i) {
+    CU(cudaEventCreate(&r->ev[i][0]));
+    CU(cudaEventCreate(&r->ev[i][1]));
+  }
+  r->events_made = true;
+  return OPF_OK;
+}
+
+void runner_free(Runner* r) {
+  r->drop_graph();
+  if (r->events_made)
+    for (int i = 0; i < kMaxSlots; ++i) {
+      cudaEventDestroy(r->ev[i][0]);
+      cudaEventDestroy(r->ev[i][1]);
+    }
+  r->events_made = false;
+  if (r->own) cudaStreamDestroy(r->own);
+  r->own = nullptr;
+}
+
+void enqueue_nonlinear(Runner* r, const Group& g, const double2* U, double2* Nout) {
+  const opf::Dims& d = g.d;
+  cudaStream_t st = r->stream;
+  if (r->precision == 1) {
+    r->begin(0);
+    opf::launch_curl_split32(d, g.ds, U, g.W6f, g.Nlin, st);
+    r->end();
+    r->begin(1);
+    opf::launch_zsynth32(d, g.ds, g.pz, g.W6f, g.Z6f, st);
+    r->end();
+    r->begin(2);
+    opf::launch_product32(d, g.ds, g.pth, g.Z6f, g.ZNf, st);
+    r->end();
+    r->begin(3);
+    opf::launch_zanalysis32(d, g.ds, g.pz, g.ZNf, g.Nlin, Nout, st);
+    r->end();
+    return;
+  }
+  r->begin(0);
+  opf::launch_curl(d, g.ds, U, g.W6, st);
+  r->end();
+  r->begin(1);
+  opf::launch_zsynth(d, g.ds, g.pz, g.W6, g.Z6, st);
+  r->end();
+  r->begin(2);
+  opf::launch_product(d, g.ds, g.pth, g.Z6, g.ZN, st);
+  r->end();
+  r->begin(3);
+  opf::launch_zanalysis(d, g.ds, g.pz, g.ZN, Nout, st);
+  r->end();
+}
+
+void enqueue_solve(Runner* r, const Group& g, const double2* Na, const double2* Nb, double wa,
+                   double wb, double2* Uout) {
+  opf::SolveArgs a{g.U, Na, Nb, wa, wb, Uout, g.beta_p};
+  r->begin(4);
+  opf::launch_solve(g.d, g.ds, a, g.nJ, r->stream);
+  r->end();
+}
+
+// One predictor-corrector step (section 2) of every trajectory of every
+// group: predictor with N_j, then n_corr corrector passes with
+// c N^q + (1 - c) N_j, each solved from u_j.
+void enqueue_step(Runner* r) {
+  for (Group* g : r->groups) {
+    const double c = g->d.c;
+    enqueue_nonlinear(r, *g, g->U, g->Nj);
+    enqueue_solve(r, *g, g->Nj, nullptr, 1.0, 0.0, g->U1);
+    for (int q = 0; q < r->n_corr; ++q) {
+      enqueue_nonlinear(r, *g, g->U1, g->Nq);
+      enqueue_solve(r, *g, g->Nq, g->Nj, c, 1.0 - c, q == r->n_corr - 1 ? g->U : g->U1);
+    }
+  }
+}
+
+int harvest_timing(Runner* r) {
+  if (!r->timing) return OPF_OK;
+  for (int i = 0; i < r->nslots; ++i) {
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, r->ev[i][0], r->ev[i][1]));
+    r->tot_ms[r->slot_name[i]] += ms;
+    r->tot_n[r->slot_name[i]] += 1;
+  }
+  return OPF_OK;
+}
+
+int runner_step(Runner* r, int n) {
+  if (n < 0) return fail(OPF_EINVAL, "step: n < 0");
+  for (int s = 0; s < n; ++s) {
+    r->nslots = 0;
+    if (r->use_graph) {
+      if (!r->gexec) {
+        cudaGraph_t gr;
+        CU(cudaStreamBeginCapture(r->stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_step(r);
+        cudaError_t e = cudaStreamEndCapture(r->stream, &gr);
+        if (e != cudaSuccess) return fail(OPF_ECUDA, std::string("stream capture: ") + cudaGetErrorString(e));
+        r->graph_nslots = r->nslots;
+        e = cudaGraphInstantiate(&r->gexec, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) {
+          r->gexec = nullptr;
+          return fail(OPF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        }
+      }
+      CU(cudaGraphLaunch(r->gexec, r->stream));
+      r->nslots = r->graph_nslots;  // event nodes captured with the graph
+    } else {
+      enqueue_step(r);
+    }
+    if (r->timing) {
+      CU(cudaStreamSynchronize(r->stream));
+      int rc = harvest_timing(r);
+      if (rc) return rc;
+    }
+  }
+  CU(cudaStreamSynchronize(r->stream));
+  CU(cudaGetLastError());
+  for (Group* g : r->groups)
+    for (int b = 0; b < g->d.B; ++b) g->time[b] += n * g->dt[b];
+  return OPF_OK;
+}
+
+int runner_option(Runner* r, const char* key, double v) {
+  if (!key) return fail(OPF_EINVAL, "set_option: NULL key");
+  if (!strcmp(key, "precision")) {
+    if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "precision: 0 (FP64) or 1 (mixed)");
+    r->precision = (int)v;
+  } else if (!strcmp(key, "n_corr")) {
+    if (!(v >= 1 && v <= 16 && v == std::floor(v))) return fail(OPF_EINVAL, "n_corr: 1..16");
+    r->n_corr = (int)v;
+  } else if (!strcmp(key, "graph")) {
+    if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "graph: 0 or 1");
+    r->use_graph = (int)v;
+  } else if (!strcmp(key, "timing")) {
+    if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "timing: 0 or 1");
+    r->timing = (int)v;
+  } else {
+    return fail(OPF_EINVAL, std::string("unknown option ") + key);
+  }
+  r->drop_graph();
+  return OPF_OK;
+}
+
+int runner_get_option(Runner* r, const char* key, double* v) {
+  if (!key || !v) return fail(OPF_EINVAL, "get_option: NULL argument");
+  if (!strcmp(key, "precision")) *v = r->precision;
+  else if (!strcmp(key, "n_corr")) *v = r->n_corr;
+  else if (!strcmp(key, "graph")) *v = r->use_graph;
+  else if (!strcmp(key, "timing")) *v = r->timing;
+  else return fail(OPF_EINVAL, std::string("unknown option ") + key);
+  return OPF_OK;
+}
+
+int runner_times(Runner* r, int cap, int* count, const char** names, double* total_ms, int* launches,
+                 int reset) {
+  if (!count) return fail(OPF_EINVAL, "NULL count");
+  int c = 0;
+  for (int i = 0; i < kNumNames && c < cap; ++i) {
+    if (names) names[c] = kNames[i];
+    if (total_ms) total_ms[c] = r->tot_ms[i];
+    if (launches) launches[c] = r->tot_n[i];
+    ++c;
+  }
+  *count = c;
+  if (reset)
+    for (int i = 0; i < kNumNames; ++i) {
+      r->tot_ms[i] = 0;
+      r->tot_n[i] = 0;
+    }
+  return OPF_OK;
+}
+
+// ---- per-trajectory state transfer and diagnostics
+int traj_set_state_device(Group* g, int b, const double* d_coeffs, cudaStream_t st) {
+  const opf::Dims d = g->single(b);
+  const size_t bytes = 3 * (size_t)d.F * sizeof(double2);
+  double2* abi = g->at(g->abi, b);
+  int* flag = g->at(g->flag, b);
+  CU(cudaMemcpyAsync(abi, d_coeffs, bytes, cudaMemcpyDeviceToDevice, st));
+  opf::launch_nan_check((const double*)abi, 6 * d.F, flag, st);
+  int h_flag = 0;
+  CU(cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (h_flag) return fail(OPF_ENAN, "set_state: non-finite coefficient; state unchanged");
+  opf::launch_abi_to_internal(d, abi, g->at(g->U, b), st);
+  CU(cudaMemsetAsync(g->at(g->beta_p, b), 0, sizeof(double), st));
+  CU(cudaStreamSynchronize(st));
+  CU(cudaGetLastError());
+  return OPF_OK;
+}
+
+int traj_set_state_host(Group* g, int b, const double* coeffs, cudaStream_t st) {
+  const size_t bytes = 3 * (size_t)g->d.F * sizeof(double2);
+  double2* tmp = g->at(g->tmpU, b);
+  CU(cudaMemcpyAsync(tmp, coeffs, bytes, cudaMemcpyHostToDevice, st));
+  return traj_set_state_device(g, b, (const double*)tmp, st);
+}
+
+int traj_get_state(Group* g, int b, double* out, bool host, cudaStream_t st) {
+  const opf::Dims d = g->single(b);
+  double2* abi = g->at(g->abi, b);
+  opf::launch_internal_to_abi(d, g->at(g->U, b), host ? abi : (double2*)out, 1, st);
+  if (host)
+    CU(cudaMemcpyAsync(out, abi, 3 * (size_t)d.F * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  CU(cudaGetLastError());
+  return OPF_OK;
+}
+
+int traj_energy(Group* g, int b, double out[3], cudaStream_t st) {
+  const opf::Dims d = g->single(b);
+  const opf::DevSetup s = g->setup_of(b);
+  double2* U = g->at(g->U, b);
+  double2* W6 = g->at(g->W6, b);
+  opf::launch_curl(d, s, U, W6, st);
+  opf::launch_energy(d, s, U, W6, g->at(g->beta_p, b), g->at(g->partial, b), g->nblk_energy,
+                     g->at(g->out3, b), st);
+  CU(cudaMemcpyAsync(out, g->at(g->out3, b), 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  CU(cudaGetLastError());
+  if (!std::isfinite(out[0]) || !std::isfinite(out[1]) || !std::isfinite(out[2]))
+    return fail(OPF_ENAN, "energy: non-finite state");
+  return OPF_OK;
+}
+
+int traj_beta(Group* g, int b, double* beta, cudaStream_t st) {
+  double bp = 0.0;
+  CU(cudaMemcpyAsync(&bp, g->at(g->beta_p, b), sizeof(double), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  *beta = bp * g->Re[b] / 4.0;
+  return OPF_OK;
+}
+
+}  // namespace
+
+// ====================================================================== handles
+struct opf_ctx {
+  Group g;
+  Runner run;
+};
+
+struct opf_ens {
+  std::vector<Group> groups;
+  std::vector<std::pair<int, int>> where;  // trajectory -> (group, index in group)
+  Runner run;
+};
+
+namespace {
+int check_handle(const void* h) { return h ? OPF_OK : fail(OPF_EINVAL, "NULL handle"); }
+}  // namespace
+
+extern "C" {
+
+const char* opf_last_error(void) { return g_err.c_str(); }
+
+opf_t* opf_create(int N, int K, int M, int m_p, double alpha, double Re, double dt) {
+  opf_ctx* h = new opf_ctx();
+  int rc = group_build(&h->g, N, K, M, m_p, alpha, 1, &Re, &dt);
+  if (rc == OPF_OK) rc = runner_init(&h->run);
+  if (rc == OPF_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) rc = fail(OPF_ECUDA, cudaGetErrorString(e));
+  }
+  if (rc != OPF_OK) {
+    std::string keep = "opf_create: " + g_err;
+    group_free(&h->g);
+    runner_free(&h->run);
     delete h;
     g_err = keep;
     return nullptr;
-  };
-  if (cudaGetDevice(&h->device) != cudaSuccess) {
-    fail(OPF_ECUDA, "opf_create: no CUDA device");
-    return bail(0);
   }
-  const size_t F16 = (size_t)d.F * sizeof(double2);
-  const size_t P16 = (size_t)N * d.nz * M * sizeof(double2);
-  if (dalloc(h, &h->U, 3 * F16) || dalloc(h, &h->U1, 3 * F16) || dalloc(h, &h->Nj, 3 * F16) ||
-      dalloc(h, &h->Nq, 3 * F16) || dalloc(h, &h->W6, 6 * F16) || dalloc(h, &h->Z6, 6 * P16) ||
-      dalloc(h, &h->ZN, 3 * P16) || dalloc(h, &h->abi, 3 * F16) || dalloc(h, &h->tmpU, 3 * F16) ||
-      dalloc(h, &h->beta_p, 16) || dalloc(h, &h->out3, 32) || dalloc(h, &h->out2, 16) ||
-      dalloc(h, &h->flag, 16) || dalloc(h, &h->W6f, 6 * F16 / 2) || dalloc(h, &h->Z6f, 6 * P16 / 2) ||
-      dalloc(h, &h->ZNf, 3 * P16 / 2) || dalloc(h, &h->Nlin, 3 * F16))
-    return bail(0);
-  h->nblk_energy = opf::energy_blocks(d);
-  if (dalloc(h, &h->partial, (size_t)2 * h->nblk_energy * sizeof(double))) return bail(0);
-  if (upload_setup(h)) return bail(0);
-  if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
-    fail(OPF_ECUDA, "opf_create: stream");
-    return bail(0);
-  }
-  h->stream = h->own;
-  if (!opf::prepare_kernel_attrs(d)) {
-    fail(OPF_EINVAL, "opf_create: resolution needs more shared memory than a block has");
-    return bail(0);
-  }
-  for (int i = 0; i < kMaxSlots; ++i) {
-    cudaEventCreate(&h->ev[i][0]);
-    cudaEventCreate(&h->ev[i][1]);
-  }
-  h->events_made = true;
-  cudaMemset(h->U, 0, 3 * F16);
-  cudaMemset(h->beta_p, 0, 16);
-  cudaError_t e = cudaDeviceSynchronize();
-  if (e != cudaSuccess) {
-    fail(OPF_ECUDA, std::string("opf_create: ") + cudaGetErrorString(e));
-    return bail(0);
-  }
+  h->run.groups = {&h->g};
   return h;
 }
 
 void opf_destroy(opf_t* h) {
   if (!h) return;
-  cudaStreamSynchronize(h->stream);
-  free_all(h);
+  cudaStreamSynchronize(h->run.stream);
+  runner_free(&h->run);
+  group_free(&h->g);
   delete h;
 }
 
 int opf_set_state_device(opf_t* h, const double* d_coeffs) {
   if (check_handle(h)) return OPF_EINVAL;
   if (!d_coeffs) return fail(OPF_EINVAL, "opf_set_state: NULL buffer");
-  const size_t bytes = 3 * (size_t)h->d.F * sizeof(double2);
-  CU(cudaMemcpyAsync(h->abi, d_coeffs, bytes, cudaMemcpyDeviceToDevice, h->stream));
-  opf::launch_nan_check((const double*)h->abi, 6 * h->d.F, h->flag, h->stream);
-  int flag = 0;
-  CU(cudaMemcpyAsync(&flag, h->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-  CU(cudaStreamSynchronize(h->stream));
-  if (flag) return fail(OPF_ENAN, "opf_set_state: non-finite coefficient; state unchanged");
-  opf::launch_abi_to_internal(h->d, h->abi, h->U, h->stream);
-  CU(cudaMemsetAsync(h->beta_p, 0, sizeof(double), h->stream));
-  CU(cudaStreamSynchronize(h->stream));
-  CU(cudaGetLastError());
-  return OPF_OK;
+  return traj_set_state_device(&h->g, 0, d_coeffs, h->run.stream);
 }
 
 int opf_set_state(opf_t* h, const double* coeffs) {
   if (check_handle(h)) return OPF_EINVAL;
   if (!coeffs) return fail(OPF_EINVAL, "opf_set_state: NULL buffer");
-  const size_t bytes = 3 * (size_t)h->d.F * sizeof(double2);
-  CU(cudaMemcpyAsync(h->tmpU, coeffs, bytes, cudaMemcpyHostToDevice, h->stream));
-  return opf_set_state_device(h, (const double*)h->tmpU);
+  return traj_set_state_host(&h->g, 0, coeffs, h->run.stream);
 }
 
 int opf_get_state_device(opf_t* h, double* d_coeffs) {
   if (check_handle(h)) return OPF_EINVAL;
   if (!d_coeffs) return fail(OPF_EINVAL, "opf_get_state: NULL buffer");
-  opf::launch_internal_to_abi(h->d, h->U, (double2*)d_coeffs, 1, h->stream);
-  CU(cudaStreamSynchronize(h->stream));
-  CU(cudaGetLastError());
-  return OPF_OK;
+  return traj_get_state(&h->g, 0, d_coeffs, false, h->run.stream);
 }
 
 int opf_get_state(opf_t* h, double* coeffs) {
   if (check_handle(h)) return OPF_EINVAL;
   if (!coeffs) return fail(OPF_EINVAL, "opf_get_state: NULL buffer");
-  opf::launch_internal_to_abi(h->d, h->U, h->abi, 1, h->stream);
-  CU(cudaMemcpyAsync(coeffs, h->abi, 3 * (size_t)h->d.F * sizeof(double2), cudaMemcpyDeviceToHost,
-                     h->stream));
-  CU(cudaStreamSynchronize(h->stream));
-  CU(cudaGetLastError());
-  return OPF_OK;
+  return traj_get_state(&h->g, 0, coeffs, true, h->run.stream);
 }
 
 int opf_step(opf_t* h, int n) {
   if (check_handle(h)) return OPF_EINVAL;
-  if (n < 0) return fail(OPF_EINVAL, "opf_step: n < 0");
-  for (int s = 0; s < n; ++s) {
-    h->nslots = 0;
-    if (h->use_graph) {
-      if (!h->gexec) {
-        cudaGraph_t g;
-        CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-        enqueue_step(h);
-        CU(cudaStreamEndCapture(h->stream, &g));
-        h->graph_nslots = h->nslots;
-        cudaError_t e = cudaGraphInstantiate(&h->gexec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-          h->gexec = nullptr;
-          return fail(OPF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
-        }
-      }
-      CU(cudaGraphLaunch(h->gexec, h->stream));
-      h->nslots = h->graph_nslots;  // event nodes captured with the graph
-    } else {
-      enqueue_step(h);
-    }
-    if (h->timing) {
-      CU(cudaStreamSynchronize(h->stream));
-      int rc = harvest_timing(h);
-      if (rc) return rc;
-    }
-  }
-  CU(cudaStreamSynchronize(h->stream));
-  CU(cudaGetLastError());
-  h->time += n * h->d.dt;
-  return OPF_OK;
+  return runner_step(&h->run, n);
 }
 
 int opf_energy(opf_t* h, double out[3]) {
   if (check_handle(h)) return OPF_EINVAL;
   if (!out) return fail(OPF_EINVAL, "opf_energy: NULL out");
-  opf::launch_curl(h->d, h->ds, h->U, h->W6, h->stream);
-  opf::launch_energy(h->d, h->ds, h->U, h->W6, h->beta_p, h->partial, h->nblk_energy, h->out3,
-                     h->stream);
-  CU(cudaMemcpyAsync(out, h->out3, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  CU(cudaStreamSynchronize(h->stream));
-  CU(cudaGetLastError());
-  if (!std::isfinite(out[0]) || !std::isfinite(out[1]) || !std::isfinite(out[2]))
-    return fail(OPF_ENAN, "opf_energy: non-finite state");
-  return OPF_OK;
+  return traj_energy(&h->g, 0, out, h->run.stream);
 }
 
 int opf_wall_residual(opf_t* h, double out[2]) {
   if (check_handle(h)) return OPF_EINVAL;
   if (!out) return fail(OPF_EINVAL, "opf_wall_residual: NULL out");
-  opf::launch_wall(h->d, h->ds, h->U, h->out2, h->stream);
-  CU(cudaMemcpyAsync(out, h->out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  CU(cudaStreamSynchronize(h->stream));
+  opf::launch_wall(h->g.single(0), h->g.ds, h->g.U, h->g.out2, h->run.stream);
+  CU(cudaMemcpyAsync(out, h->g.out2, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->run.stream));
+  CU(cudaStreamSynchronize(h->run.stream));
   CU(cudaGetLastError());
   return OPF_OK;
 }
@@ -420,107 +651,207 @@ int opf_wall_residual(opf_t* h, double out[2]) {
 int opf_nonlinear(opf_t* h, const double* coeffs, double* out) {
   if (check_handle(h)) return OPF_EINVAL;
   if (!coeffs || !out) return fail(OPF_EINVAL, "opf_nonlinear: NULL buffer");
-  const size_t bytes = 3 * (size_t)h->d.F * sizeof(double2);
-  CU(cudaMemcpyAsync(h->abi, coeffs, bytes, cudaMemcpyHostToDevice, h->stream));
-  opf::launch_abi_to_internal(h->d, h->abi, h->tmpU, h->stream);
-  const int timing = h->timing;
-  h->timing = 0;
-  enqueue_nonlinear(h, h->tmpU, h->Nq);
-  h->timing = timing;
-  opf::launch_internal_to_abi(h->d, h->Nq, h->abi, 1, h->stream);
-  CU(cudaMemcpyAsync(out, h->abi, bytes, cudaMemcpyDeviceToHost, h->stream));
-  CU(cudaStreamSynchronize(h->stream));
+  Group& g = h->g;
+  cudaStream_t st = h->run.stream;
+  const size_t bytes = 3 * (size_t)g.d.F * sizeof(double2);
+  CU(cudaMemcpyAsync(g.abi, coeffs, bytes, cudaMemcpyHostToDevice, st));
+  opf::launch_abi_to_internal(g.d, g.abi, g.tmpU, st);
+  const int timing = h->run.timing;
+  h->run.timing = 0;
+  enqueue_nonlinear(&h->run, g, g.tmpU, g.Nq);
+  h->run.timing = timing;
+  opf::launch_internal_to_abi(g.d, g.Nq, g.abi, 1, st);
+  CU(cudaMemcpyAsync(out, g.abi, bytes, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
   CU(cudaGetLastError());
   return OPF_OK;
 }
 
 int opf_set_option(opf_t* h, const char* key, double v) {
   if (check_handle(h)) return OPF_EINVAL;
-  if (!key) return fail(OPF_EINVAL, "opf_set_option: NULL key");
-  if (!strcmp(key, "precision")) {
-    if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "precision: 0 (FP64) or 1 (mixed)");
-    h->precision = (int)v;
-  } else if (!strcmp(key, "n_corr")) {
-    if (!(v >= 1 && v <= 16 && v == std::floor(v))) return fail(OPF_EINVAL, "n_corr: 1..16");
-    h->n_corr = (int)v;
-  } else if (!strcmp(key, "graph")) {
-    if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "graph: 0 or 1");
-    h->use_graph = (int)v;
-  } else if (!strcmp(key, "timing")) {
-    if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "timing: 0 or 1");
-    h->timing = (int)v;
-  } else {
-    return fail(OPF_EINVAL, std::string("unknown option ") + key);
-  }
-  if (h->gexec) {
-    cudaGraphExecDestroy(h->gexec);
-    h->gexec = nullptr;
-  }
-  return OPF_OK;
+  return runner_option(&h->run, key, v);
 }
 
 int opf_get_option(opf_t* h, const char* key, double* v) {
   if (check_handle(h)) return OPF_EINVAL;
-  if (!key || !v) return fail(OPF_EINVAL, "opf_get_option: NULL argument");
-  if (!strcmp(key, "precision")) *v = h->precision;
-  else if (!strcmp(key, "n_corr")) *v = h->n_corr;
-  else if (!strcmp(key, "graph")) *v = h->use_graph;
-  else if (!strcmp(key, "timing")) *v = h->timing;
-  else return fail(OPF_EINVAL, std::string("unknown option ") + key);
-  return OPF_OK;
+  return runner_get_option(&h->run, key, v);
 }
 
 int opf_get_dt(opf_t* h, double* dt) {
   if (check_handle(h)) return OPF_EINVAL;
   if (!dt) return fail(OPF_EINVAL, "NULL out");
-  *dt = h->d.dt;
+  *dt = h->g.dt[0];
   return OPF_OK;
 }
 
 int opf_get_time(opf_t* h, double* t) {
   if (check_handle(h)) return OPF_EINVAL;
   if (!t) return fail(OPF_EINVAL, "NULL out");
-  *t = h->time;
+  *t = h->g.time[0];
   return OPF_OK;
 }
 
 int opf_get_beta(opf_t* h, double* beta) {
   if (check_handle(h)) return OPF_EINVAL;
   if (!beta) return fail(OPF_EINVAL, "NULL out");
-  double bp = 0.0;
-  CU(cudaMemcpyAsync(&bp, h->beta_p, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  CU(cudaStreamSynchronize(h->stream));
-  *beta = bp * h->d.Re / 4.0;
-  return OPF_OK;
+  return traj_beta(&h->g, 0, beta, h->run.stream);
 }
 
 int opf_set_stream(opf_t* h, void* stream) {
   if (check_handle(h)) return OPF_EINVAL;
-  CU(cudaStreamSynchronize(h->stream));
-  h->stream = stream ? (cudaStream_t)stream : h->own;
+  CU(cudaStreamSynchronize(h->run.stream));
+  h->run.stream = stream ? (cudaStream_t)stream : h->run.own;
   return OPF_OK;
 }
 
 int opf_kernel_times(opf_t* h, int cap, int* count, const char** names, double* total_ms,
                      int* launches, int reset) {
   if (check_handle(h)) return OPF_EINVAL;
-  if (!count) return fail(OPF_EINVAL, "NULL count");
-  int c = 0;
-  for (int i = 0; i < kNumNames && c < cap; ++i) {
-    if (names) names[c] = kNames[i];
-    if (total_ms) total_ms[c] = h->tot_ms[i];
-    if (launches) launches[c] = h->tot_n[i];
-    ++c;
+  return runner_times(&h->run, cap, count, names, total_ms, launches, reset);
+}
+
+// ---------------------------------------------------------------- ensembles
+opf_ens_t* opf_ens_create(int count, const int* N, const int* K, const int* M, const int* m_p,
+                          const double* alpha, const double* Re, const double* dt) {
+  if (count < 1 || !N || !K || !M || !m_p || !alpha || !Re || !dt) {
+    fail(OPF_EINVAL, "opf_ens_create: need count >= 1 and non-NULL arrays");
+    return nullptr;
   }
-  *count = c;
-  if (reset)
-    for (int i = 0; i < kNumNames; ++i) {
-      h->tot_ms[i] = 0;
-      h->tot_n[i] = 0;
+  // group trajectories by shape, keeping their order inside each group
+  std::map<std::tuple<int, int, int, int, double>, std::vector<int>> by_shape;
+  std::vector<std::tuple<int, int, int, int, double>> order;
+  for (int i = 0; i < count; ++i) {
+    auto key = std::make_tuple(N[i], K[i], M[i], m_p[i], alpha[i]);
+    if (!by_shape.count(key)) order.push_back(key);
+    by_shape[key].push_back(i);
+  }
+  opf_ens* e = new opf_ens();
+  e->groups.resize(order.size());
+  e->where.assign(count, {0, 0});
+  int rc = OPF_OK;
+  for (size_t gi = 0; gi < order.size() && rc == OPF_OK; ++gi) {
+    const auto& idx = by_shape[order[gi]];
+    std::vector<double> re, tt;
+    for (int i : idx) {
+      re.push_back(Re[i]);
+      tt.push_back(dt[i]);
     }
+    const auto& k = order[gi];
+    rc = group_build(&e->groups[gi], std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
+                     std::get<4>(k), (int)idx.size(), re.data(), tt.data());
+    for (size_t b = 0; b < idx.size(); ++b) e->where[idx[b]] = {(int)gi, (int)b};
+  }
+  if (rc == OPF_OK) rc = runner_init(&e->run);
+  if (rc != OPF_OK) {
+    std::string keep = "opf_ens_create: " + g_err;
+    for (Group& g : e->groups) group_free(&g);
+    runner_free(&e->run);
+    delete e;
+    g_err = keep;
+    return nullptr;
+  }
+  for (Group& g : e->groups) e->run.groups.push_back(&g);
+  return e;
+}
+
+void opf_ens_destroy(opf_ens_t* e) {
+  if (!e) return;
+  cudaStreamSynchronize(e->run.stream);
+  runner_free(&e->run);
+  for (Group& g : e->groups) group_free(&g);
+  delete e;
+}
+
+namespace {
+int ens_traj(opf_ens_t* e, int i, Group** g, int* b) {
+  if (!e) return fail(OPF_EINVAL, "NULL ensemble");
+  if (i < 0 || i >= (int)e->where.size()) return fail(OPF_EINVAL, "trajectory index out of range");
+  *g = &e->groups[e->where[i].first];
+  *b = e->where[i].second;
+  return OPF_OK;
+}
+}  // namespace
+
+int opf_ens_count(opf_ens_t* e, int* count) {
+  if (check_handle(e) || !count) return fail(OPF_EINVAL, "NULL argument");
+  *count = (int)e->where.size();
   return OPF_OK;
 }
 
+int opf_ens_set_state(opf_ens_t* e, int i, const double* coeffs) {
+  Group* g;
+  int b;
+  if (ens_traj(e, i, &g, &b)) return OPF_EINVAL;
+  if (!coeffs) return fail(OPF_EINVAL, "opf_ens_set_state: NULL buffer");
+  return traj_set_state_host(g, b, coeffs, e->run.stream);
+}
+
+int opf_ens_get_state(opf_ens_t* e, int i, double* coeffs) {
+  Group* g;
+  int b;
+  if (ens_traj(e, i, &g, &b)) return OPF_EINVAL;
+  if (!coeffs) return fail(OPF_EINVAL, "opf_ens_get_state: NULL buffer");
+  return traj_get_state(g, b, coeffs, true, e->run.stream);
+}
+
+int opf_ens_set_state_device(opf_ens_t* e, int i, const double* d_coeffs) {
+  Group* g;
+  int b;
+  if (ens_traj(e, i, &g, &b)) return OPF_EINVAL;
+  if (!d_coeffs) return fail(OPF_EINVAL, "opf_ens_set_state_device: NULL buffer");
+  return traj_set_state_device(g, b, d_coeffs, e->run.stream);
+}
+
+int opf_ens_get_state_device(opf_ens_t* e, int i, double* d_coeffs) {
+  Group* g;
+  int b;
+  if (ens_traj(e, i, &g, &b)) return OPF_EINVAL;
+  if (!d_coeffs) return fail(OPF_EINVAL, "opf_ens_get_state_device: NULL buffer");
+  return traj_get_state(g, b, d_coeffs, false, e->run.stream);
+}
+
+int opf_ens_step(opf_ens_t* e, int n) {
+  if (check_handle(e)) return OPF_EINVAL;
+  return runner_step(&e->run, n);
+}
+
+int opf_ens_energy(opf_ens_t* e, int i, double out[3]) {
+  Group* g;
+  int b;
+  if (ens_traj(e, i, &g, &b)) return OPF_EINVAL;
+  if (!out) return fail(OPF_EINVAL, "opf_ens_energy: NULL out");
+  return traj_energy(g, b, out, e->run.stream);
+}
+
+int opf_ens_get_time(opf_ens_t* e, int i, double* t) {
+  Group* g;
+  int b;
+  if (ens_traj(e, i, &g, &b)) return OPF_EINVAL;
+  if (!t) return fail(OPF_EINVAL, "NULL out");
+  *t = g->time[b];
+  return OPF_OK;
+}
+
+int opf_ens_set_option(opf_ens_t* e, const char* key, double v) {
+  if (check_handle(e)) return OPF_EINVAL;
+  return runner_option(&e->run, key, v);
+}
+
+int opf_ens_set_stream(opf_ens_t* e, void* stream) {
+  if (check_handle(e)) return OPF_EINVAL;
+  CU(cudaStreamSynchronize(e->run.stream));
+  e->run.stream = stream ? (cudaStream_t)stream : e->run.own;
+  e->run.drop_graph();
+  return OPF_OK;
+}
+
+int opf_ens_kernel_times(opf_ens_t* e, int cap, int* count, const char** names, double* total_ms,
+                         int* launches, int reset) {
+  if (check_handle(e)) return OPF_EINVAL;
+  return runner_times(&e->run, cap, count, names, total_ms, launches, reset);
+}
+
+// ---------------------------------------------------------------- host-only
 int opf_setup_query(int N, int K, int M, int m_p, double alpha, double Re, double dt,
                     const char* what, double* out, long cap, long* len) {
   if (N < 9 || K < 1 || M < 1 || m_p < 1 || !(alpha > 0) || !(Re > 0) || !(dt > 0) || !what || !len)

@@ -48,7 +48,11 @@ struct Setup {
 bool build_setup(Setup* s, std::string* err);
 
 // --------------------------------------------------------------- device side
+// Per-trajectory scalars at the head of each trajectory's setup arrays.
+constexpr int kPrmRe = 0, kPrmDt = 1, kPrmC = 2, kPrmSumWG = 3, kPrmCount = 8;
+
 struct DevSetup {
+  double* prm = nullptr;  // [kPrmCount] Re, dt, c, sum(wq G)
   double* rinv = nullptr;
   double* d1 = nullptr;
   double* wq = nullptr;
@@ -68,10 +72,16 @@ struct DevSetup {
 // Physical-in-z intermediates are stored [field][n][z][m] (m fastest).
 struct Dims {
   int N, K, M, m_p, nk, nz, nth;
-  double alpha, Re, dt, c;
+  double alpha, Re, dt, c;  // host copies (trajectory 0); kernels read DevSetup::prm
   long F;         // complex values per spectral field = M * N * nk
   int mcz, mca;   // m columns per block: z synthesis, z analysis
   int zc;         // z rows per block in the theta/product kernel
+  // batching: B trajectories of this shape per launch (grid z); trajectory b's
+  // work buffers start b*ss bytes after trajectory 0's, its setup arrays b*ps
+  // bytes after (ps = 0: one shared setup)
+  int B = 1;
+  long ss = 0, ps = 0;
+  const double* prm = nullptr;  // trajectory 0's DevSetup::prm
 };
 
 void choose_chunks(Dims* d);
@@ -107,8 +117,7 @@ struct SolveArgs {
   double2* Uout;
   double* beta_p;  // device scalar: beta' of this solve (written by the (0,0) mode)
 };
-void launch_solve(const Dims& d, const DevSetup& s, const SolveArgs& a, double sumwG, int nJ,
-                  cudaStream_t st);
+void launch_solve(const Dims& d, const DevSetup& s, const SolveArgs& a, int nJ, cudaStream_t st);
 void launch_energy(const Dims& d, const DevSetup& s, const double2* U, const double2* W6,
                    const double* beta_p, double* partial, int nblk, double* out3, cudaStream_t st);
 int energy_blocks(const Dims& d);

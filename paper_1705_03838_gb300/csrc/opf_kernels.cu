@@ -18,6 +18,13 @@ namespace opf {
 
 __device__ __forceinline__ int row_lo_d(int i, int N) { return min(max(i - 4, 0), N - 9); }
 
+// Batched launches: trajectory b = blockIdx.z; its buffers sit `stride` bytes
+// after trajectory b-1's (stride 0: shared).  Null stays null.
+template <typename P>
+__device__ __forceinline__ P* bofs(P* p, long stride) {
+  return p ? (P*)((char*)p + (long)blockIdx.z * stride) : p;
+}
+
 // ------------------------------------------------------------------ ABI <-> internal
 // abi: [3][M][nk][N] (u_r, u_theta, u_z); internal: [3][M][N][nk] (u+, u-, u_z).
 __global__ void k_abi_to_internal(Dims d, const double2* __restrict__ abi, double2* __restrict__ U) {
@@ -81,6 +88,11 @@ __global__ void __launch_bounds__(256) k_curl(Dims d, const double* __restrict__
   using T = typename Scalar<V>::T;
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= d.F) return;
+  d1 = bofs(d1, d.ps);
+  rinv = bofs(rinv, d.ps);
+  U = bofs(U, d.ss);
+  W6 = bofs(W6, d.ss);
+  Nlin = bofs(Nlin, d.ss);
   const int kk = idx % d.nk;
   const long t = idx / d.nk;
   const int n = t % d.N;
@@ -143,14 +155,14 @@ __global__ void __launch_bounds__(256) k_curl(Dims d, const double* __restrict__
 }
 
 void launch_curl(const Dims& d, const DevSetup& s, const double2* U, double2* W6, cudaStream_t st) {
-  const int nb = (int)((d.F + 255) / 256);
-  k_curl<double2, false><<<nb, 256, 0, st>>>(d, s.d1, s.rinv, U, W6, nullptr);
+  dim3 g((unsigned)((d.F + 255) / 256), 1, d.B);
+  k_curl<double2, false><<<g, 256, 0, st>>>(d, s.d1, s.rinv, U, W6, nullptr);
 }
 
 void launch_curl_split32(const Dims& d, const DevSetup& s, const double2* U, float2* W6,
                          double2* Nlin, cudaStream_t st) {
-  const int nb = (int)((d.F + 255) / 256);
-  k_curl<float2, true><<<nb, 256, 0, st>>>(d, s.d1, s.rinv, U, W6, Nlin);
+  dim3 g((unsigned)((d.F + 255) / 256), 1, d.B);
+  k_curl<float2, true><<<g, 256, 0, st>>>(d, s.d1, s.rinv, U, W6, Nlin);
 }
 
 // ------------------------------------------------------------------ z synthesis (A2)
@@ -163,8 +175,11 @@ __global__ void __launch_bounds__(128) k_zsynth(Dims d, FftPlan pz, const V* __r
   V* A = (V*)smraw;
   V* B = A + MC * ld;
   V* tw = B + MC * ld;
-  const int m0 = blockIdx.x * MC, n = blockIdx.y, f = blockIdx.z;
+  const int m0 = blockIdx.x * MC, n = blockIdx.y / 6, f = blockIdx.y % 6;
   const int K = d.K;
+  twz = bofs(twz, d.ps);
+  W6 = bofs(W6, d.ss);
+  Z6 = bofs(Z6, d.ss);
   for (int e = threadIdx.x; e < nz; e += blockDim.x) tw[e] = twz[e];
   const long fs = d.F;
   for (int e = threadIdx.x; e < MC * nz; e += blockDim.x) {
@@ -187,13 +202,13 @@ size_t zsynth_smem(const Dims& d, int mc, size_t vb) { return (2 * (size_t)mc * 
 
 void launch_zsynth32(const Dims& d, const DevSetup& s, const FftPlan& pz, const float2* W6,
                      float2* Z6, cudaStream_t st) {
-  dim3 g((d.M + d.mcz - 1) / d.mcz, d.N, 6);
+  dim3 g((d.M + d.mcz - 1) / d.mcz, d.N * 6, d.B);
   k_zsynth<float2><<<g, 128, zsynth_smem(d, d.mcz, sizeof(float2)), st>>>(d, pz, s.tw_z32, W6, Z6);
 }
 
 void launch_zsynth(const Dims& d, const DevSetup& s, const FftPlan& pz, const double2* W6,
                    double2* Z6, cudaStream_t st) {
-  dim3 g((d.M + d.mcz - 1) / d.mcz, d.N, 6);
+  dim3 g((d.M + d.mcz - 1) / d.mcz, d.N * 6, d.B);
   k_zsynth<double2><<<g, 128, zsynth_smem(d, d.mcz, sizeof(double2)), st>>>(d, pz, s.tw_z, W6, Z6);
 }
 
@@ -211,6 +226,9 @@ __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* _
   V* tw = B + 3 * ZC * ld;
   const int z0 = blockIdx.x * ZC, n = blockIdx.y, nz = d.nz;
   const int zc = min(ZC, nz - z0);
+  twth = bofs(twth, d.ps);
+  Z6 = bofs(Z6, d.ss);
+  ZN = bofs(ZN, d.ss);
   for (int e = threadIdx.x; e < nth; e += blockDim.x) tw[e] = twth[e];
   const long fstride = (long)d.N * nz * M;
   // spectra of the pairs (u_r,u_t), (u_z,w_r), (w_t,w_z):  Z = A + i B
@@ -259,13 +277,13 @@ size_t product_smem(const Dims& d, int zc, size_t vb) { return (2 * 3 * (size_t)
 
 void launch_product32(const Dims& d, const DevSetup& s, const FftPlan& pth, const float2* Z6,
                       float2* ZN, cudaStream_t st) {
-  dim3 g((d.nz + d.zc - 1) / d.zc, d.N);
+  dim3 g((d.nz + d.zc - 1) / d.zc, d.N, d.B);
   k_product<float2><<<g, 128, product_smem(d, d.zc, sizeof(float2)), st>>>(d, pth, s.tw_th32, Z6, ZN);
 }
 
 void launch_product(const Dims& d, const DevSetup& s, const FftPlan& pth, const double2* Z6,
                     double2* ZN, cudaStream_t st) {
-  dim3 g((d.nz + d.zc - 1) / d.zc, d.N);
+  dim3 g((d.nz + d.zc - 1) / d.zc, d.N, d.B);
   k_product<double2><<<g, 128, product_smem(d, d.zc, sizeof(double2)), st>>>(d, pth, s.tw_th, Z6, ZN);
 }
 
@@ -282,6 +300,11 @@ __global__ void __launch_bounds__(128) k_zanalysis(Dims d, FftPlan pz, const V* 
   V* tw = B + 3 * MC * ld;
   const int m0 = blockIdx.x * MC, n = blockIdx.y;
   const int mcn = min(MC, M - m0);
+  twz = bofs(twz, d.ps);
+  ZN = bofs(ZN, d.ss);
+  Nlin = bofs(Nlin, d.ss);
+  Nout = bofs(Nout, d.ss);
+  const double Re = bofs(d.prm, d.ps)[kPrmRe];
   for (int e = threadIdx.x; e < nz; e += blockDim.x) tw[e] = twz[e];
   const long fstride = (long)d.N * nz * M;
   for (int e = threadIdx.x; e < 3 * MC * nz; e += blockDim.x) {
@@ -302,7 +325,7 @@ __global__ void __launch_bounds__(128) k_zanalysis(Dims d, FftPlan pz, const V* 
     const V z_ = res[(2 * MC + mc) * ld + zp];
     const double nrx = sc * r_.x, nry = sc * r_.y, ntx = sc * t_.x, nty = sc * t_.y;
     double2 nz2 = double2{sc * z_.x, sc * z_.y};
-    if (k == 0 && m == 0) nz2.x += 4.0 / d.Re;  // base driving force (laminar balance)
+    if (k == 0 && m == 0) nz2.x += 4.0 / Re;  // base driving force (laminar balance)
     const long o = ((long)m * d.N + n) * nk + kk;
     double2 np = double2{nrx - nty, nry + ntx};        // N+ = N_r + i N_theta
     double2 nm = double2{nrx + nty, nry - ntx};        // N- = N_r - i N_theta
@@ -327,14 +350,14 @@ size_t zanalysis_smem(const Dims& d, int mc, size_t vb) {
 
 void launch_zanalysis(const Dims& d, const DevSetup& s, const FftPlan& pz, const double2* ZN,
                       double2* Nout, cudaStream_t st) {
-  dim3 g((d.M + d.mca - 1) / d.mca, d.N);
+  dim3 g((d.M + d.mca - 1) / d.mca, d.N, d.B);
   k_zanalysis<double2><<<g, 128, zanalysis_smem(d, d.mca, sizeof(double2)), st>>>(d, pz, s.tw_z, ZN, nullptr,
                                                                                   Nout);
 }
 
 void launch_zanalysis32(const Dims& d, const DevSetup& s, const FftPlan& pz, const float2* ZN,
                         const double2* Nlin, double2* Nout, cudaStream_t st) {
-  dim3 g((d.M + d.mca - 1) / d.mca, d.N);
+  dim3 g((d.M + d.mca - 1) / d.mca, d.N, d.B);
   k_zanalysis<float2><<<g, 128, zanalysis_smem(d, d.mca, sizeof(float2)), st>>>(d, pz, s.tw_z32, ZN, Nlin,
                                                                                 Nout);
 }
@@ -350,7 +373,7 @@ struct SolveDev {
   const double* basis;
   const double2* ainv;
   const double* G;
-  double sumwG;
+  const double* prm;
   int nJ;
 };
 
@@ -438,7 +461,23 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   double* BS = (double*)(UJ + 3 * N * T);  // [T][6][N] influence basis of each mode's |k|
   const int m = blockIdx.y, kk0 = blockIdx.x * T, tid = threadIdx.x;
   const int mt = d.m_p * m, ps = mt & 1, pv = ps ^ 1;
-  const double ci = 1.0 / (d.c * d.dt), cu = (1.0 - d.c) / d.c;
+  s.d1 = bofs(s.d1, d.ps);
+  s.rinv = bofs(s.rinv, d.ps);
+  s.wq = bofs(s.wq, d.ps);
+  s.hop = bofs(s.hop, d.ps);
+  s.luH = bofs(s.luH, d.ps);
+  s.luP = bofs(s.luP, d.ps);
+  s.basis = bofs(s.basis, d.ps);
+  s.ainv = bofs(s.ainv, d.ps);
+  s.G = bofs(s.G, d.ps);
+  s.prm = bofs(s.prm, d.ps);
+  a.Uj = bofs(a.Uj, d.ss);
+  a.Na = bofs(a.Na, d.ss);
+  a.Nb = bofs(a.Nb, d.ss);
+  a.Uout = bofs(a.Uout, d.ss);
+  a.beta_p = bofs(a.beta_p, d.ss);
+  const double cc = s.prm[kPrmC], dtb = s.prm[kPrmDt];
+  const double ci = 1.0 / (cc * dtb), cu = (1.0 - cc) / cc;
   const long fs = d.F;
   const long base = (long)m * N * nk;
 
@@ -614,7 +653,7 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
     if (tid == 0) {
       double q = 0.0;
       for (int i = 0; i < N; ++i) q += s.wq[i] * X[i * NT + cz];
-      const double bp = (0.25 - q) / s.sumwG;
+      const double bp = (0.25 - q) / s.prm[kPrmSumWG];
       misc[0] = bp;
       *a.beta_p = bp;
     }
@@ -640,7 +679,7 @@ static size_t solve_smem(int N, int T);
 // right-hand sides per warp) with the most blocks; larger tiles only when
 // there are many modes per SM.
 static int solve_tile(const Dims& d) {
-  const long modes = (long)d.nk * d.M;
+  const long modes = (long)d.nk * d.M * d.B;
   if (modes / 16 >= 8 * 152 && solve_smem(d.N, 16) <= 200 * 1024) return 16;
   if (modes / 8 >= 4 * 152 && solve_smem(d.N, 8) <= 200 * 1024) return 8;
   return 4;
@@ -689,11 +728,10 @@ bool prepare_kernel_attrs(const Dims& d) {
   return ok;
 }
 
-void launch_solve(const Dims& d, const DevSetup& s, const SolveArgs& a, double sumwG, int nJ,
-                  cudaStream_t st) {
-  SolveDev sd{s.d1, s.rinv, s.wq, s.hop, s.luH, s.luP, s.basis, s.ainv, s.G, sumwG, nJ};
+void launch_solve(const Dims& d, const DevSetup& s, const SolveArgs& a, int nJ, cudaStream_t st) {
+  SolveDev sd{s.d1, s.rinv, s.wq, s.hop, s.luH, s.luP, s.basis, s.ainv, s.G, s.prm, nJ};
   const int T = solve_tile(d);
-  dim3 g((d.nk + T - 1) / T, d.M);
+  dim3 g((d.nk + T - 1) / T, d.M, d.B);
   if (T == 16) k_solve<16><<<g, 24 * 16, solve_smem(d.N, 16), st>>>(d, sd, a);
   else if (T == 8) k_solve<8><<<g, 24 * 8, solve_smem(d.N, 8), st>>>(d, sd, a);
   else k_solve<4><<<g, 24 * 4, solve_smem(d.N, 4), st>>>(d, sd, a);
@@ -736,7 +774,7 @@ __global__ void __launch_bounds__(256) k_energy(Dims d, const double* __restrict
 
 __global__ void k_energy_final(Dims d, const double* __restrict__ partial, int nblk,
                                const double* __restrict__ wq, const double2* __restrict__ U,
-                               const double* beta_p, double* out3) {
+                               const double* beta_p, const double* prm, double* out3) {
   __shared__ double su[256], sw[256];
   double a = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
@@ -757,7 +795,7 @@ __global__ void k_energy_final(Dims d, const double* __restrict__ partial, int n
     double flux = 0.0;
     const double2* uz = U + 2 * d.F + (d.K - 1);  // (k,m) = (0,0), u_z
     for (int n = 0; n < d.N; ++n) flux += wq[n] * uz[(long)n * d.nk].x;
-    const double beta = *beta_p * d.Re / 4.0;
+    const double beta = *beta_p * prm[kPrmRe] / 4.0;
     out3[0] = 6.0 * su[0];
     out3[1] = 4.0 * (1.0 + beta) * flux;
     out3[2] = sw[0];
@@ -769,7 +807,7 @@ int energy_blocks(const Dims& d) { return (int)((d.F + 255) / 256); }
 void launch_energy(const Dims& d, const DevSetup& s, const double2* U, const double2* W6,
                    const double* beta_p, double* partial, int nblk, double* out3, cudaStream_t st) {
   k_energy<<<nblk, 256, 0, st>>>(d, s.wq, W6, partial);
-  k_energy_final<<<1, 256, 0, st>>>(d, partial, nblk, s.wq, U, beta_p, out3);
+  k_energy_final<<<1, 256, 0, st>>>(d, partial, nblk, s.wq, U, beta_p, s.prm, out3);
 }
 
 // Boundary vector g of section 2 over all modes: max |u(1)| and max |div u(1)|.

@@ -47,9 +47,10 @@ bool smooth235(int n) {
 // Radial points, 9-point first-derivative stencils for both axis parities
 // (Fornberg's recursion, same points and folding as the handle's setup) and
 // the z / theta twiddle tables, computed on the device into the scratch.
-__global__ void k_noalloc_consts(int N, int nz, int nth, double* d1, double* rinv, double2* twz,
-                                 double2* twth) {
+__global__ void k_noalloc_consts(int N, int nz, int nth, double Re, double* prm, double* d1,
+                                 double* rinv, double2* twz, double2* twth) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < opf::kPrmCount) prm[t] = t == opf::kPrmRe ? Re : 0.0;
   if (t < nz) {
     double s, c;
     sincospi(2.0 * t / nz, &s, &c);
@@ -138,7 +139,8 @@ extern "C" int opf_nonlinear_noalloc(int N, int K, int M, int m_p, double alpha,
   // scratch layout: constants | U (3F) | W6 (6F) | Z6 (6P) | ZN (3P) | N (3F)
   const size_t F16 = (size_t)d.F * sizeof(double2);
   const size_t P16 = (size_t)N * d.nz * M * sizeof(double2);
-  const size_t o_d1 = 0;
+  const size_t o_prm = 0;
+  const size_t o_d1 = align256(o_prm + opf::kPrmCount * sizeof(double));
   const size_t o_rinv = align256(o_d1 + 2 * (size_t)N * 9 * sizeof(double));
   const size_t o_twz = align256(o_rinv + N * sizeof(double));
   const size_t o_twth = align256(o_twz + d.nz * sizeof(double2));
@@ -168,6 +170,8 @@ extern "C" int opf_nonlinear_noalloc(int N, int K, int M, int m_p, double alpha,
     return fail(OPF_EINVAL, "opf_nonlinear_noalloc: resolution needs more shared memory than a block has");
   unsigned char* base = (unsigned char*)g_scratch_addr[dev];
   opf::DevSetup s{};
+  s.prm = (double*)(base + o_prm);
+  d.prm = s.prm;
   s.d1 = (double*)(base + o_d1);
   s.rinv = (double*)(base + o_rinv);
   s.tw_z = (double2*)(base + o_twz);
@@ -180,7 +184,8 @@ extern "C" int opf_nonlinear_noalloc(int N, int K, int M, int m_p, double alpha,
   cudaStream_t st = (cudaStream_t)stream;
 
   const int nc = std::max(N, std::max(d.nz, d.nth));
-  k_noalloc_consts<<<(nc + 127) / 128, 128, 0, st>>>(N, d.nz, d.nth, s.d1, s.rinv, s.tw_z, s.tw_th);
+  k_noalloc_consts<<<(nc + 127) / 128, 128, 0, st>>>(N, d.nz, d.nth, Re, s.prm, s.d1, s.rinv, s.tw_z,
+                                                      s.tw_th);
   opf::launch_abi_to_internal(d, (const double2*)d_state, U, st);
   opf::launch_curl(d, s, U, W6, st);
   opf::launch_zsynth(d, s, pz, W6, Z6, st);

@@ -62,6 +62,29 @@ def lib():
         L.opf_kernel_times.restype = i
         L.opf_kernel_times.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(cp), _dp,
                                        ctypes.POINTER(i), i]
+        L.opf_ens_create.restype = vp
+        ip = ctypes.POINTER(ctypes.c_int)
+        L.opf_ens_create.argtypes = [i, ip, ip, ip, ip, _dp, _dp, _dp]
+        L.opf_ens_destroy.restype = None
+        L.opf_ens_destroy.argtypes = [vp]
+        L.opf_ens_count.restype = i
+        L.opf_ens_count.argtypes = [vp, ip]
+        for name in ("opf_ens_set_state", "opf_ens_get_state", "opf_ens_set_state_device",
+                     "opf_ens_get_state_device"):
+            getattr(L, name).restype = i
+            getattr(L, name).argtypes = [vp, i, vp]
+        L.opf_ens_step.restype = i
+        L.opf_ens_step.argtypes = [vp, i]
+        L.opf_ens_energy.restype = i
+        L.opf_ens_energy.argtypes = [vp, i, _dp]
+        L.opf_ens_get_time.restype = i
+        L.opf_ens_get_time.argtypes = [vp, i, _dp]
+        L.opf_ens_set_option.restype = i
+        L.opf_ens_set_option.argtypes = [vp, cp, d]
+        L.opf_ens_set_stream.restype = i
+        L.opf_ens_set_stream.argtypes = [vp, vp]
+        L.opf_ens_kernel_times.restype = i
+        L.opf_ens_kernel_times.argtypes = [vp, i, ip, ctypes.POINTER(cp), _dp, ip, i]
         L.opf_nonlinear_noalloc.restype = i
         L.opf_nonlinear_noalloc.argtypes = [i, i, i, i, d, d, vp, vp, vp]
         L.opf_setup_query.restype = i
@@ -203,6 +226,83 @@ def opf_kernel_times(h, reset=False):
     ms = (ctypes.c_double * cap)()
     n = (ctypes.c_int * cap)()
     _check(lib().opf_kernel_times(h.ptr, cap, ctypes.byref(count), names, ms, n, int(reset)))
+    return {names[i].decode(): (ms[i], n[i]) for i in range(count.value)}
+
+
+class EnsHandle:
+    """Owns an opf_ens_t*; per-trajectory state shapes for marshalling."""
+
+    def __init__(self, ptr, shapes):
+        self.ptr, self.shapes = ptr, shapes
+
+    def __del__(self):
+        try:
+            opf_ens_destroy(self)
+        except Exception:
+            pass
+
+
+def opf_ens_create(N, K, M, m_p, alpha, Re, dt):
+    """Sequences of equal length (one entry per trajectory)."""
+    n = len(N)
+    ci = lambda v: (ctypes.c_int * n)(*[int(x) for x in v])
+    cd = lambda v: (ctypes.c_double * n)(*[float(x) for x in v])
+    ptr = lib().opf_ens_create(n, ci(N), ci(K), ci(M), ci(m_p), cd(alpha), cd(Re), cd(dt))
+    if not ptr:
+        raise OpfError(OPF_EINVAL, lib().opf_last_error().decode())
+    return EnsHandle(ptr, [(3, M[j], 2 * K[j] - 1, N[j]) for j in range(n)])
+
+
+def opf_ens_destroy(e):
+    if e.ptr:
+        lib().opf_ens_destroy(e.ptr)
+        e.ptr = None
+
+
+def opf_ens_set_state(e, i, state):
+    a = np.ascontiguousarray(state, dtype=np.complex128)
+    if a.shape != e.shapes[i]:
+        raise ValueError(f"state {i} must have shape {e.shapes[i]}")
+    _check(lib().opf_ens_set_state(e.ptr, int(i), a.ctypes.data))
+
+
+def opf_ens_get_state(e, i):
+    out = np.empty(e.shapes[i], dtype=np.complex128)
+    _check(lib().opf_ens_get_state(e.ptr, int(i), out.ctypes.data))
+    return out
+
+
+def opf_ens_step(e, n=1):
+    _check(lib().opf_ens_step(e.ptr, int(n)))
+
+
+def opf_ens_energy(e, i):
+    out = (ctypes.c_double * 3)()
+    _check(lib().opf_ens_energy(e.ptr, int(i), out))
+    return np.array(out[:])
+
+
+def opf_ens_get_time(e, i):
+    v = ctypes.c_double()
+    _check(lib().opf_ens_get_time(e.ptr, int(i), ctypes.byref(v)))
+    return v.value
+
+
+def opf_ens_set_option(e, key, value):
+    _check(lib().opf_ens_set_option(e.ptr, key.encode(), float(value)))
+
+
+def opf_ens_set_stream(e, stream_handle):
+    _check(lib().opf_ens_set_stream(e.ptr, ctypes.c_void_p(stream_handle)))
+
+
+def opf_ens_kernel_times(e, reset=False):
+    cap = 16
+    count = ctypes.c_int()
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_double * cap)()
+    n = (ctypes.c_int * cap)()
+    _check(lib().opf_ens_kernel_times(e.ptr, cap, ctypes.byref(count), names, ms, n, int(reset)))
     return {names[i].decode(): (ms[i], n[i]) for i in range(count.value)}
 
 

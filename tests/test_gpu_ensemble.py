@@ -1,0 +1,99 @@
+"""Batched ensembles: trajectories stepped together in shared launches must
+equal the same trajectories stepped alone (identical arithmetic per
+trajectory -> bit-for-bit), for uneven shapes and per-trajectory Re/dt."""
+import numpy as np
+import pytest
+
+from oracle.opf_oracle import Oracle, Params
+from paper_1705_03838_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def opf():
+    from paper_1705_03838_gb300 import build, opf as _opf
+
+    build.build()
+    _opf.lib()
+    return _opf
+
+
+def run_single(opf, N, K, M, m_p, alpha, Re, dt, U0, n, precision):
+    h = opf.opf_create(N, K, M, m_p, alpha, Re, dt)
+    opf.opf_set_option(h, "precision", precision)
+    opf.opf_set_state(h, U0)
+    opf.opf_step(h, n)
+    return opf.opf_get_state(h), opf.opf_energy(h)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_uneven_ensemble_equals_single_runs(opf, precision):
+    specs = [  # (N, K, M, m_p, alpha, Re, dt)
+        (16, 4, 4, 1, 1.25, 900.0, 0.01),
+        (12, 3, 6, 2, 1.25, 1200.0, 0.01),
+        (16, 4, 4, 1, 1.25, 1500.0, 0.005),
+        (20, 5, 3, 1, 0.8, 700.0, 0.01),
+        (16, 4, 4, 1, 1.25, 900.0, 0.01),
+        (12, 3, 6, 2, 1.25, 2000.0, 0.02),
+    ]
+    cols = list(zip(*specs))
+    e = opf.opf_ens_create(*cols)
+    opf.opf_ens_set_option(e, "precision", precision)
+    states = []
+    for i, (N, K, M, m_p, alpha, Re, dt) in enumerate(specs):
+        U0 = inputs.seeded_state(N, K, M, m_p, alpha, 0.05, 500 + i)
+        states.append(U0)
+        opf.opf_ens_set_state(e, i, U0)
+    opf.opf_ens_step(e, 4)
+    for i, sp in enumerate(specs):
+        U, E = run_single(opf, *sp, states[i], 4, precision)
+        assert np.array_equal(opf.opf_ens_get_state(e, i), U)
+        assert np.array_equal(opf.opf_ens_energy(e, i), E)
+        assert abs(opf.opf_ens_get_time(e, i) - 4 * sp[6]) < 1e-15
+
+
+def test_shared_setup_batch_matches_oracle(opf):
+    """A batch with one shared setup (equal Re and dt), checked per member
+    against the oracle."""
+    N, K, M, m_p, alpha, Re, dt = 16, 4, 4, 1, 1.25, 800.0, 0.01
+    e = opf.opf_ens_create([N] * 3, [K] * 3, [M] * 3, [m_p] * 3, [alpha] * 3, [Re] * 3, [dt] * 3)
+    o = Oracle(Params(N, K, M, m_p, alpha, Re, dt))
+    U0s = [inputs.seeded_state(N, K, M, m_p, alpha, a, 900 + i) for i, a in enumerate((1e-3, 1e-2, 0.1))]
+    for i, U0 in enumerate(U0s):
+        opf.opf_ens_set_state(e, i, U0)
+    opf.opf_ens_step(e, 3)
+    for i, U0 in enumerate(U0s):
+        ref = o.step(U0, 3)
+        U = opf.opf_ens_get_state(e, i)
+        assert np.linalg.norm(U - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def test_ensemble_workload_shapes(opf):
+    """The batched-ensemble workload's three resolutions (N=32/48/64,
+    |k|<16/24/32, m<16/24/32), a few members each, mixed precision, against
+    single runs of the same members."""
+    shapes = [(32, 16, 16)] * 3 + [(48, 24, 24)] * 3 + [(64, 32, 32)] * 2
+    Re = [1800.0 + 800.0 * u for u in inputs.uniforms(1705038383, len(shapes))]
+    N, K, M = zip(*shapes)
+    n = len(shapes)
+    e = opf.opf_ens_create(N, K, M, [1] * n, [1.25] * n, Re, [0.01] * n)
+    opf.opf_ens_set_option(e, "precision", 1)
+    U0s = []
+    for i, (Ni, Ki, Mi) in enumerate(shapes):
+        U0 = inputs.seeded_state(Ni, Ki, Mi, 1, 1.25, 1e-2, 1705038383 + i)
+        U0s.append(U0)
+        opf.opf_ens_set_state(e, i, U0)
+    opf.opf_ens_step(e, 2)
+    for i in (0, 4, 7):
+        Ni, Ki, Mi = shapes[i]
+        U, _ = run_single(opf, Ni, Ki, Mi, 1, 1.25, Re[i], 0.01, U0s[i], 2, 1)
+        assert np.array_equal(opf.opf_ens_get_state(e, i), U)
+
+
+def test_ensemble_rejects_bad_input(opf):
+    with pytest.raises(opf.OpfError):
+        opf.opf_ens_create([8], [4], [4], [1], [1.25], [100.0], [0.01])
+    e = opf.opf_ens_create([12], [3], [3], [1], [1.25], [100.0], [0.01])
+    with pytest.raises(opf.OpfError):
+        opf.opf_ens_energy(e, 5)
