@@ -233,6 +233,100 @@ def run_reference(args, w):
 
 
 # ------------------------------------------------------------------ GPU arm
+ENSEMBLE_SHAPES = [(32, 16, 16)] * 96 + [(48, 24, 24)] * 96 + [(64, 32, 32)] * 64
+
+
+def run_ensemble(args):
+    """Batched-ensemble workload: 256 trajectories of uneven resolution
+    (96 x N=32 |k|<16 m<16, 96 x N=48 |k|<24 m<24, 64 x N=64 |k|<32 m<32),
+    Re uniform in [1800, 2600], perturbation amplitude log-uniform in
+    [1e-3, 1e-1], mixed precision, all stepped in one CUDA graph per step.
+    The working set (~10 GB) exceeds L2, so no flush is needed."""
+    import torch
+
+    from paper_1705_03838_gb300 import build as _build, inputs, opf
+
+    torch.cuda.set_device(0)
+    _build.build()
+    n = len(ENSEMBLE_SHAPES)
+    seed = 1705038383
+    U = inputs.uniforms(seed, 2 * n)
+    Re = [1800.0 + 800.0 * U[2 * i] for i in range(n)]
+    amp = [10.0 ** (-3.0 + 2.0 * U[2 * i + 1]) for i in range(n)]
+    Ns, Ks, Ms = zip(*ENSEMBLE_SHAPES)
+    alpha, dt = 1.25, 0.005
+    t0 = time.time()
+    e = opf.opf_ens_create(Ns, Ks, Ms, [1] * n, [alpha] * n, Re, [dt] * n)
+    setup_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+    opf.opf_ens_set_stream(e, stream.cuda_stream)
+    opf.opf_ens_set_option(e, "precision", args.precision)
+    t0 = time.time()
+    for i, (N, K, M) in enumerate(ENSEMBLE_SHAPES):
+        opf.opf_ens_set_state(e, i, inputs.seeded_state(N, K, M, 1, alpha, amp[i], seed + i))
+    inputs_s = time.time() - t0
+    if args.autotune:
+        opf.opf_ens_set_option(e, "autotune", 1)
+    opf.opf_ens_step(e, args.warmup)
+    opf.opf_ens_set_option(e, "timing", 1)
+    opf.opf_ens_step(e, 1)
+    opf.opf_ens_kernel_times(e, reset=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    opf.opf_ens_step(e, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    kt = opf.opf_ens_kernel_times(e, reset=True)
+    E = [opf.opf_ens_energy(e, i) for i in (0, 96, 192)]
+    steps_per_s = args.steps / (total_ms / 1000.0)
+    dofs = sum(3 * N * (2 * K - 1) * (2 * M - 1) for N, K, M in ENSEMBLE_SHAPES)
+    Fsum = sum(N * (2 * K - 1) * M for N, K, M in ENSEMBLE_SHAPES)
+    peaks, peak_kind = load_peaks()
+    algo_bytes = (528 if args.precision == 0 else 432) * Fsum
+    flops = {}
+    for (N, K, M), cnt in ((ENSEMBLE_SHAPES[0], 96), (ENSEMBLE_SHAPES[96], 96), (ENSEMBLE_SHAPES[192], 64)):
+        c = kernel_costs({"N": N, "K": K, "M": M})
+        for k, v in c.items():
+            flops[k] = flops.get(k, 0.0) + cnt * v["flops"]
+    dom = max(kt, key=lambda k: kt[k][0])
+    dom_ms = kt[dom][0] / max(1, kt[dom][1]) * 3  # three shape groups per kernel slot
+    pk, src = kernel_peak(dom, args.precision)
+    ach = flops[dom] / (dom_ms * 1e-3) / 1e12
+    tot = sum(x[0] for x in kt.values())
+    line = {
+        "metric": "ensemble trajectory-steps/s (256 uneven trajectories, one graph per step)",
+        "value": steps_per_s * n,
+        "unit": "trajectory-steps/s",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "dtype": "f64" if args.precision == 0 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "ensemble: 96x(N32,|k|<16,m<16) + 96x(N48,|k|<24,m<24) + 64x(N64,|k|<32,m<32), "
+                               "Re U[1800,2600], amp logU[1e-3,1e-1], dt=0.005",
+                   "l2": "working set > L2 (no flush needed)",
+                   "autotune": bool(args.autotune)},
+        "gdof_steps_per_s": steps_per_s * dofs / 1e9,
+        "hbm_roofline_frac": algo_bytes * steps_per_s / (peaks["hbm_gbs"] * 1e9),
+        "roofline": {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                     "frac": ach / pk, "traffic": None, "peak_source": src,
+                     "share": {k: v[0] / tot for k, v in kt.items()}},
+        "setup_s": setup_s,
+        "inputs_s": inputs_s,
+        "clocks": clk,
+        "energy_EID_members_0_96_192": [[float(x) for x in v] for v in E],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args, w):
     import numpy as np
     import torch
@@ -408,12 +502,17 @@ def main():
                     help="headline precision: 1 = mixed (default), 0 = FP64; both are timed")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="medium", choices=["medium", "ensemble"],
+                    help="medium: the default single-run line; ensemble: the batched workload")
+    ap.add_argument("--autotune", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     w = workload_params()
     if args.impl == "reference":
         run_reference(args, w)
+    elif args.workload == "ensemble":
+        run_ensemble(args)
     else:
         run_gpu(args, w)
 

@@ -101,6 +101,12 @@ int opf_nonlinear(opf_t* h, const double* coeffs, double* out);
  *                product, FP64 radial solves and boundary correction)
  *   "n_corr":    corrector iterations per step (default 1)
  *   "graph":     1 = replay the step as a CUDA graph (default), 0 = plain launches
+ *   "timing":    1 = record per-kernel device times (opf_kernel_times)
+ *   "autotune":  1 = on the next step, time the launch shapes of each kernel
+ *                (columns/rows per block of the transforms, modes per block of
+ *                the solve) on the current state and keep the fastest; reads
+ *                back as 2 once done.  Read-only keys "tile", "mcz", "mca", "zc"
+ *                report the shapes in use.
  * Unknown keys or out-of-range values: OPF_EINVAL. */
 int opf_set_option(opf_t* h, const char* key, double value);
 int opf_get_option(opf_t* h, const char* key, double* value);

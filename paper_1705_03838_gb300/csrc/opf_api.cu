@@ -6,10 +6,13 @@
 // device arenas -- work buffers and setup arrays -- with fixed strides, so
 // every kernel launch covers all B trajectories (grid z).  A Runner records
 // one time step of a list of groups as a CUDA graph and replays it.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <thread>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -156,8 +159,11 @@ int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, con
     if (Re[b] != Re[0] || dt[b] != dt[0]) g->shared_setup = false;
   const int nsetup = g->shared_setup ? 1 : B;
 
+  // host setups, built on all host cores when trajectories differ
   std::vector<opf::Setup> hs(nsetup);
-  for (int b = 0; b < nsetup; ++b) {
+  std::vector<std::string> errs(nsetup);
+  std::vector<char> ok(nsetup, 0);
+  auto build_one = [&](int b) {
     opf::Setup& s = hs[b];
     s.N = N;
     s.K = K;
@@ -167,9 +173,22 @@ int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, con
     s.Re = Re[b];
     s.dt = dt[b];
     s.c = 0.5;
-    std::string err;
-    if (!opf::build_setup(&s, &err)) return fail(OPF_EINVAL, err);
+    ok[b] = opf::build_setup(&s, &errs[b]) ? 1 : 0;
+  };
+  const int nthreads = std::max(1, std::min<int>(nsetup, (int)std::thread::hardware_concurrency()));
+  if (nthreads == 1) {
+    for (int b = 0; b < nsetup; ++b) build_one(b);
+  } else {
+    std::vector<std::thread> pool;
+    std::atomic<int> next{0};
+    for (int t = 0; t < nthreads; ++t)
+      pool.emplace_back([&] {
+        for (int b = next++; b < nsetup; b = next++) build_one(b);
+      });
+    for (auto& th : pool) th.join();
   }
+  for (int b = 0; b < nsetup; ++b)
+    if (!ok[b]) return fail(OPF_EINVAL, errs[b]);
   g->nJ = hs[0].nJ;
 
   // setup arena layout (identical sizes for every trajectory of the shape)
@@ -291,6 +310,7 @@ struct Runner {
   std::vector<Group*> groups;
   cudaStream_t own = nullptr, stream = nullptr;
   int precision = 0, n_corr = 1, use_graph = 1, timing = 0;
+  int autotune = 0;  // 1: time launch shapes on the next step, keep the fastest
   cudaGraphExec_t gexec = nullptr;
   cudaEvent_t ev[kMaxSlots][2];
   int slot_name[kMaxSlots];
@@ -405,8 +425,96 @@ int harvest_timing(Runner* r) {
   return OPF_OK;
 }
 
+// ---- autotuner: per group, time each transform kernel and the solve over
+// the launch shapes whose shared memory fits, on the group's current state
+// (every timed kernel is idempotent: it rewrites only scratch buffers).
+template <typename F>
+float time_launch(Runner* r, F launch) {
+  launch();
+  cudaEventRecord(r->ev[0][0], r->stream);
+  for (int rep = 0; rep < 3; ++rep) launch();
+  cudaEventRecord(r->ev[0][1], r->stream);
+  cudaEventSynchronize(r->ev[0][1]);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, r->ev[0][0], r->ev[0][1]);
+  return ms / 3.f;
+}
+
+int tune_group(Runner* r, Group* g) {
+  opf::Dims& d = g->d;
+  int dev = 0, optin = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t vb = r->precision == 1 ? sizeof(float2) : sizeof(double2);
+  const bool mixed = r->precision == 1;
+  cudaStream_t st = r->stream;
+  // valid inputs for every stage: one nonlinear evaluation of the state
+  enqueue_nonlinear(r, *g, g->U, g->Nj);
+  const int cand[5] = {1, 2, 4, 8, 16};
+  float best = 1e30f;
+  int pick = d.mcz;
+  for (int c : cand) {
+    if (c > d.M || opf::zsynth_smem(d, c, vb) > (size_t)optin) continue;
+    d.mcz = c;
+    const float t = time_launch(r, [&] {
+      if (mixed) opf::launch_zsynth32(d, g->ds, g->pz, g->W6f, g->Z6f, st);
+      else opf::launch_zsynth(d, g->ds, g->pz, g->W6, g->Z6, st);
+    });
+    if (t < best) best = t, pick = c;
+  }
+  d.mcz = pick;
+  best = 1e30f;
+  pick = d.zc;
+  for (int c : cand) {
+    if (c > d.nz || opf::product_smem(d, c, vb) > (size_t)optin) continue;
+    d.zc = c;
+    const float t = time_launch(r, [&] {
+      if (mixed) opf::launch_product32(d, g->ds, g->pth, g->Z6f, g->ZNf, st);
+      else opf::launch_product(d, g->ds, g->pth, g->Z6, g->ZN, st);
+    });
+    if (t < best) best = t, pick = c;
+  }
+  d.zc = pick;
+  best = 1e30f;
+  pick = d.mca;
+  for (int c : cand) {
+    if (c > d.M || opf::zanalysis_smem(d, c, vb) > (size_t)optin) continue;
+    d.mca = c;
+    const float t = time_launch(r, [&] {
+      if (mixed) opf::launch_zanalysis32(d, g->ds, g->pz, g->ZNf, g->Nlin, g->Nq, st);
+      else opf::launch_zanalysis(d, g->ds, g->pz, g->ZN, g->Nq, st);
+    });
+    if (t < best) best = t, pick = c;
+  }
+  d.mca = pick;
+  best = 1e30f;
+  pick = 0;
+  for (int T : {4, 8, 16}) {
+    if (opf::solve_smem_bytes(d.N, T) > (size_t)optin) continue;
+    d.tile = T;
+    opf::SolveArgs a{g->U, g->Nj, nullptr, 1.0, 0.0, g->U1, g->beta_p};
+    const float t = time_launch(r, [&] { opf::launch_solve(d, g->ds, a, g->nJ, st); });
+    if (t < best) best = t, pick = T;
+  }
+  d.tile = pick;
+  CU(cudaStreamSynchronize(st));
+  CU(cudaGetLastError());
+  return OPF_OK;
+}
+
 int runner_step(Runner* r, int n) {
   if (n < 0) return fail(OPF_EINVAL, "step: n < 0");
+  if (r->autotune == 1) {
+    const int timing = r->timing;
+    r->timing = 0;
+    for (Group* g : r->groups) {
+      int rc = tune_group(r, g);
+      if (rc) return rc;
+    }
+    r->timing = timing;
+    r->autotune = 2;  // tuned
+    r->drop_graph();
+  }
   for (int s = 0; s < n; ++s) {
     r->nslots = 0;
     if (r->use_graph) {
@@ -456,6 +564,9 @@ int runner_option(Runner* r, const char* key, double v) {
   } else if (!strcmp(key, "timing")) {
     if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "timing: 0 or 1");
     r->timing = (int)v;
+  } else if (!strcmp(key, "autotune")) {
+    if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "autotune: 0 or 1");
+    r->autotune = (int)v;
   } else {
     return fail(OPF_EINVAL, std::string("unknown option ") + key);
   }
@@ -469,6 +580,11 @@ int runner_get_option(Runner* r, const char* key, double* v) {
   else if (!strcmp(key, "n_corr")) *v = r->n_corr;
   else if (!strcmp(key, "graph")) *v = r->use_graph;
   else if (!strcmp(key, "timing")) *v = r->timing;
+  else if (!strcmp(key, "autotune")) *v = r->autotune;
+  else if (!strcmp(key, "tile")) *v = r->groups.empty() ? 0 : r->groups[0]->d.tile;
+  else if (!strcmp(key, "mcz")) *v = r->groups.empty() ? 0 : r->groups[0]->d.mcz;
+  else if (!strcmp(key, "mca")) *v = r->groups.empty() ? 0 : r->groups[0]->d.mca;
+  else if (!strcmp(key, "zc")) *v = r->groups.empty() ? 0 : r->groups[0]->d.zc;
   else return fail(OPF_EINVAL, std::string("unknown option ") + key);
   return OPF_OK;
 }

@@ -76,6 +76,7 @@ struct Dims {
   long F;         // complex values per spectral field = M * N * nk
   int mcz, mca;   // m columns per block: z synthesis, z analysis
   int zc;         // z rows per block in the theta/product kernel
+  int tile = 0;   // modes per block in the solve (0: heuristic)
   // batching: B trajectories of this shape per launch (grid z); trajectory b's
   // work buffers start b*ss bytes after trajectory 0's, its setup arrays b*ps
   // bytes after (ps = 0: one shared setup)
@@ -86,6 +87,11 @@ struct Dims {
 
 void choose_chunks(Dims* d);
 bool prepare_kernel_attrs(const Dims& d);
+// Shared memory a launch shape needs (autotuner candidates must fit).
+size_t zsynth_smem(const Dims& d, int mc, size_t vb);
+size_t zanalysis_smem(const Dims& d, int mc, size_t vb);
+size_t product_smem(const Dims& d, int zc, size_t vb);
+size_t solve_smem_bytes(int N, int T);
 void set_last_error(const std::string& m);  // text returned by opf_last_error()
 
 // Launch wrappers (kernels live in opf_kernels.cu).

@@ -679,11 +679,14 @@ static size_t solve_smem(int N, int T);
 // right-hand sides per warp) with the most blocks; larger tiles only when
 // there are many modes per SM.
 static int solve_tile(const Dims& d) {
+  if (d.tile == 4 || d.tile == 8 || d.tile == 16) return d.tile;
   const long modes = (long)d.nk * d.M * d.B;
   if (modes / 16 >= 8 * 152 && solve_smem(d.N, 16) <= 200 * 1024) return 16;
   if (modes / 8 >= 4 * 152 && solve_smem(d.N, 8) <= 200 * 1024) return 8;
   return 4;
 }
+
+size_t solve_smem_bytes(int N, int T) { return solve_smem(N, T); }
 
 static size_t solve_smem(int N, int T) {
   return (size_t)(5 * N * T + 4 * T) * 16 + (size_t)6 * N * T * 8 + (size_t)(2 * N * 9 + 2) * 8 +

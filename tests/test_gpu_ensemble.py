@@ -97,3 +97,24 @@ def test_ensemble_rejects_bad_input(opf):
     e = opf.opf_ens_create([12], [3], [3], [1], [1.25], [100.0], [0.01])
     with pytest.raises(opf.OpfError):
         opf.opf_ens_energy(e, 5)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotuned_shapes_give_identical_results(opf, precision):
+    """Launch shapes change only how work is split across blocks, never the
+    arithmetic of a mode: the autotuned run equals the default one exactly."""
+    w = inputs.WORKLOADS["medium"]
+    args = (w["N"], w["K"], w["M"], w["m_p"], w["alpha"], w["Re"], w["dt"])
+    U0 = inputs.workload_state("medium")
+    out = []
+    for tune in (0, 1):
+        h = opf.opf_create(*args)
+        opf.opf_set_option(h, "precision", precision)
+        opf.opf_set_option(h, "autotune", tune)
+        opf.opf_set_state(h, U0)
+        opf.opf_step(h, 3)
+        out.append(opf.opf_get_state(h))
+        if tune:
+            assert opf.opf_get_option(h, "autotune") == 2
+            assert opf.opf_get_option(h, "tile") in (4, 8, 16)
+    assert np.array_equal(out[0], out[1])
