@@ -327,6 +327,82 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+def run_large(args):
+    """Large turbulent-start run, mixed precision: Re=5300, alpha=0.4
+    (L = 5 pi R), N=128, |k|<128, m<128, m_p=1, broadband perturbation of
+    amplitude 0.3, CFL-controlled dt <= 0.002 (C = 0.5).  Reports steps/s,
+    the dt range, the device footprint, and the energy difference from the
+    FP64 path over the same dt sequence (first 50 steps)."""
+    import torch
+
+    from paper_1705_03838_gb300 import build as _build, inputs, opf
+
+    torch.cuda.set_device(0)
+    _build.build()
+    w = inputs.WORKLOADS["large"]
+    args_h = (w["N"], w["K"], w["M"], w["m_p"], w["alpha"], w["Re"], w["dt"])
+    free0, total = torch.cuda.mem_get_info()
+    h = opf.opf_create(*args_h)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    stream = torch.cuda.current_stream()
+    opf.opf_set_stream(h, stream.cuda_stream)
+    U0 = inputs.workload_state("large")
+    res = {}
+    # FP64 first with CFL control, recording its dt sequence; the mixed run
+    # replays the same sequence for its first 50 steps (same time levels),
+    # then keeps CFL control on for the timed remainder
+    opf.opf_set_option(h, "precision", 0)
+    opf.opf_set_state(h, U0)
+    opf.opf_set_option(h, "cfl", 0.5)
+    opf.opf_set_option(h, "dt_max", w["dt"])
+    dts64 = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for i in range(50):
+        dts64.append(opf.opf_get_dt(h))
+        opf.opf_step(h, 1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    res[0] = {"ms_per_step": ev0.elapsed_time(ev1) / 50, "E": opf.opf_energy(h)}
+    opf.opf_set_option(h, "cfl", 0.0)
+    opf.opf_set_option(h, "precision", 1)
+    opf.opf_set_state(h, U0)
+    for d in dts64:
+        opf.opf_set_option(h, "dt", d)
+        opf.opf_step(h, 1)
+    E50 = opf.opf_energy(h)
+    opf.opf_set_option(h, "cfl", 0.5)
+    dts = []
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for i in range(args.steps):
+        opf.opf_step(h, 1)
+        dts.append(opf.opf_get_dt(h))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    res[1] = {"ms_per_step": ev0.elapsed_time(ev1) / args.steps, "steps": args.steps,
+              "dt_min": min(dts), "dt_max": max(dts), "E": E50}
+    dof = 3 * w["N"] * (2 * w["K"] - 1) * (2 * w["M"] - 1)
+    line = {
+        "metric": "large run timesteps/s (CFL-controlled dt, includes per-step dt control)",
+        "value": 1000.0 / res[1]["ms_per_step"],
+        "unit": "timesteps/s",
+        "n_gpus": 1,
+        "steps": res[1]["steps"],
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "large: N=128 |k|<128 m<128 m_p=1 Re=5300 alpha=0.4 amp=0.3, CFL C=0.5, dt<=0.002"},
+        "gdof_steps_per_s": dof * 1000.0 / res[1]["ms_per_step"] / 1e9,
+        "fp64_timesteps_per_s": 1000.0 / res[0]["ms_per_step"],
+        "dt_range_mixed": [res[1]["dt_min"], res[1]["dt_max"]],
+        "device_footprint_gb": (free0 - free1) / 1e9,
+        "energy_rel_diff_mixed_vs_fp64_after_50_steps": float(abs(res[1]["E"][0] - res[0]["E"][0]) / res[0]["E"][0]),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args, w):
     import numpy as np
     import torch
@@ -502,7 +578,7 @@ def main():
                     help="headline precision: 1 = mixed (default), 0 = FP64; both are timed")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="medium", choices=["medium", "ensemble"],
+    ap.add_argument("--workload", default="medium", choices=["medium", "ensemble", "large"],
                     help="medium: the default single-run line; ensemble: the batched workload")
     ap.add_argument("--autotune", type=int, default=0)
     args = ap.parse_args()
@@ -513,6 +589,8 @@ def main():
         run_reference(args, w)
     elif args.workload == "ensemble":
         run_ensemble(args)
+    elif args.workload == "large":
+        run_large(args)
     else:
         run_gpu(args, w)
 

@@ -107,6 +107,15 @@ int opf_nonlinear(opf_t* h, const double* coeffs, double* out);
  *                the solve) on the current state and keep the fastest; reads
  *                back as 2 once done.  Read-only keys "tile", "mcz", "mca", "zc"
  *                report the shapes in use.
+ *   "cfl":       C > 0 switches on automatic time-step control (section 2):
+ *                after every step dt = min(dt_max, C / max(|u_r|/dr,
+ *                |u_theta|/(r dtheta), |u_z|/dz)) over the 3K x 3M grid, applied
+ *                when dt must drop or could rise by more than 10 %; the
+ *                dt-dependent operators are then refactored.  0 = off (default).
+ *                Single-trajectory handles only.
+ *   "dt_max":    upper bound of the controlled dt (default: the initial dt).
+ *   "dt":        set the time step now (refactors the dt-dependent operators).
+ *   "cfl_number" (read only): max |u| dt / spacing seen in the last step.
  * Unknown keys or out-of-range values: OPF_EINVAL. */
 int opf_set_option(opf_t* h, const char* key, double value);
 int opf_get_option(opf_t* h, const char* key, double* value);

@@ -70,8 +70,12 @@ struct Group {
   double2 *Z6 = nullptr, *ZN = nullptr, *abi = nullptr, *tmpU = nullptr, *Nlin = nullptr;
   float2 *W6f = nullptr, *Z6f = nullptr, *ZNf = nullptr;
   double *beta_p = nullptr, *partial = nullptr, *out3 = nullptr, *out2 = nullptr;
+  double* cfl = nullptr;  // per trajectory: max |u|/spacing over the grid
   int* flag = nullptr;
   int nblk_energy = 0;
+  // setup-arena offsets (same for every trajectory), for in-place rebuilds
+  size_t o_prm = 0, o_rinv = 0, o_d1 = 0, o_wq = 0, o_hop = 0, o_luH = 0, o_luP = 0;
+  size_t o_basis = 0, o_ainv = 0, o_G = 0, o_twz = 0, o_twt = 0, o_twz32 = 0, o_twt32 = 0;
 
   template <typename P>
   P* at(P* p, int b) const {
@@ -124,41 +128,17 @@ struct Layout {
   }
 };
 
-// Build host setups, lay out and fill both arenas for B trajectories of one
-// shape with per-trajectory Re and dt (one shared setup when all are equal).
-int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, const double* Re,
-                const double* dt) {
-  if (N < 9 || K < 1 || M < 1 || m_p < 1 || !(alpha > 0) || B < 1)
-    return fail(OPF_EINVAL, "need N>=9, K>=1, M>=1, m_p>=1, alpha>0");
-  for (int b = 0; b < B; ++b)
-    if (!(Re[b] > 0) || !(dt[b] > 0)) return fail(OPF_EINVAL, "need Re>0, dt>0");
-  if (!smooth235(3 * K) || !smooth235(3 * M))
-    return fail(OPF_EINVAL, "3K and 3M must have no prime factor other than 2, 3, 5");
+// Build the host setups (radial operators, LU factors, influence data) of
+// every trajectory for its current Re and dt and upload them into the setup
+// arena; first = true also lays the arena out and allocates it.  Rebuilding
+// keeps every device address, so captured graphs stay valid.
+int group_fill_setups(Group* g, bool first) {
   opf::Dims& d = g->d;
-  d.N = N;
-  d.K = K;
-  d.M = M;
-  d.m_p = m_p;
-  d.nk = 2 * K - 1;
-  d.nz = 3 * K;
-  d.nth = 3 * M;
-  d.alpha = alpha;
-  d.Re = Re[0];
-  d.dt = dt[0];
-  d.c = 0.5;
-  d.F = (long)M * N * d.nk;
-  d.B = B;
-  opf::choose_chunks(&d);
-  if (!opf::make_plan(d.nz, &g->pz) || !opf::make_plan(d.nth, &g->pth))
-    return fail(OPF_EINVAL, "no FFT plan for 3K or 3M");
-  g->Re.assign(Re, Re + B);
-  g->dt.assign(dt, dt + B);
-  g->time.assign(B, 0.0);
-  g->shared_setup = true;
-  for (int b = 1; b < B; ++b)
-    if (Re[b] != Re[0] || dt[b] != dt[0]) g->shared_setup = false;
+  const int N = d.N, K = d.K, M = d.M, m_p = d.m_p, B = d.B;
+  const double alpha = d.alpha;
+  const double* Re = g->Re.data();
+  const double* dt = g->dt.data();
   const int nsetup = g->shared_setup ? 1 : B;
-
   // host setups, built on all host cores when trajectories differ
   std::vector<opf::Setup> hs(nsetup);
   std::vector<std::string> errs(nsetup);
@@ -194,23 +174,25 @@ int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, con
   // setup arena layout (identical sizes for every trajectory of the shape)
   const opf::Setup& s0 = hs[0];
   Layout pl;
-  const size_t o_prm = pl.add(opf::kPrmCount * sizeof(double));
-  const size_t o_rinv = pl.add(s0.rinv.size() * 8);
-  const size_t o_d1 = pl.add(s0.d1.size() * 8);
-  const size_t o_wq = pl.add(s0.wq.size() * 8);
-  const size_t o_hop = pl.add(s0.hop.size() * sizeof(int));
-  const size_t o_luH = pl.add(s0.luH.size() * 8);
-  const size_t o_luP = pl.add(s0.luP.size() * 8);
-  const size_t o_basis = pl.add(s0.basis.size() * 8);
-  const size_t o_ainv = pl.add(s0.ainv.size() * 8);
-  const size_t o_G = pl.add(s0.G.size() * 8);
-  const size_t o_twz = pl.add(d.nz * sizeof(double2));
-  const size_t o_twt = pl.add(d.nth * sizeof(double2));
-  const size_t o_twz32 = pl.add(d.nz * sizeof(float2));
-  const size_t o_twt32 = pl.add(d.nth * sizeof(float2));
-  g->pstride = pl.off;
-  if (cudaMalloc((void**)&g->parena, g->pstride * nsetup) != cudaSuccess)
-    return fail(OPF_ENOMEM, "cudaMalloc of setup arrays failed");
+  g->o_prm = pl.add(opf::kPrmCount * sizeof(double));
+  g->o_rinv = pl.add(s0.rinv.size() * 8);
+  g->o_d1 = pl.add(s0.d1.size() * 8);
+  g->o_wq = pl.add(s0.wq.size() * 8);
+  g->o_hop = pl.add(s0.hop.size() * sizeof(int));
+  g->o_luH = pl.add(s0.luH.size() * 8);
+  g->o_luP = pl.add(s0.luP.size() * 8);
+  g->o_basis = pl.add(s0.basis.size() * 8);
+  g->o_ainv = pl.add(s0.ainv.size() * 8);
+  g->o_G = pl.add(s0.G.size() * 8);
+  g->o_twz = pl.add(d.nz * sizeof(double2));
+  g->o_twt = pl.add(d.nth * sizeof(double2));
+  g->o_twz32 = pl.add(d.nz * sizeof(float2));
+  g->o_twt32 = pl.add(d.nth * sizeof(float2));
+  if (first) {
+    g->pstride = pl.off;
+    if (cudaMalloc((void**)&g->parena, g->pstride * nsetup) != cudaSuccess)
+      return fail(OPF_ENOMEM, "cudaMalloc of setup arrays failed");
+  }
   std::vector<char> host(g->pstride, 0);
   auto put = [&](size_t o, const void* src, size_t bytes) { std::memcpy(host.data() + o, src, bytes); };
   std::vector<double2> twz(d.nz), twt(d.nth);
@@ -231,37 +213,76 @@ int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, con
     prm[opf::kPrmDt] = s.dt;
     prm[opf::kPrmC] = s.c;
     prm[opf::kPrmSumWG] = s.flux_G;
-    put(o_prm, prm, sizeof prm);
-    put(o_rinv, s.rinv.data(), s.rinv.size() * 8);
-    put(o_d1, s.d1.data(), s.d1.size() * 8);
-    put(o_wq, s.wq.data(), s.wq.size() * 8);
-    put(o_hop, s.hop.data(), s.hop.size() * sizeof(int));
-    put(o_luH, s.luH.data(), s.luH.size() * 8);
-    put(o_luP, s.luP.data(), s.luP.size() * 8);
-    put(o_basis, s.basis.data(), s.basis.size() * 8);
-    put(o_ainv, s.ainv.data(), s.ainv.size() * 8);
-    put(o_G, s.G.data(), s.G.size() * 8);
-    put(o_twz, twz.data(), d.nz * sizeof(double2));
-    put(o_twt, twt.data(), d.nth * sizeof(double2));
-    put(o_twz32, twz32.data(), d.nz * sizeof(float2));
-    put(o_twt32, twt32.data(), d.nth * sizeof(float2));
+    put(g->o_prm, prm, sizeof prm);
+    put(g->o_rinv, s.rinv.data(), s.rinv.size() * 8);
+    put(g->o_d1, s.d1.data(), s.d1.size() * 8);
+    put(g->o_wq, s.wq.data(), s.wq.size() * 8);
+    put(g->o_hop, s.hop.data(), s.hop.size() * sizeof(int));
+    put(g->o_luH, s.luH.data(), s.luH.size() * 8);
+    put(g->o_luP, s.luP.data(), s.luP.size() * 8);
+    put(g->o_basis, s.basis.data(), s.basis.size() * 8);
+    put(g->o_ainv, s.ainv.data(), s.ainv.size() * 8);
+    put(g->o_G, s.G.data(), s.G.size() * 8);
+    put(g->o_twz, twz.data(), d.nz * sizeof(double2));
+    put(g->o_twt, twt.data(), d.nth * sizeof(double2));
+    put(g->o_twz32, twz32.data(), d.nz * sizeof(float2));
+    put(g->o_twt32, twt32.data(), d.nth * sizeof(float2));
     CU(cudaMemcpy(g->parena + (size_t)b * g->pstride, host.data(), g->pstride, cudaMemcpyHostToDevice));
   }
+  return OPF_OK;
+}
+
+// Build host setups, lay out and fill both arenas for B trajectories of one
+// shape with per-trajectory Re and dt (one shared setup when all are equal).
+int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, const double* Re,
+                const double* dt) {
+  if (N < 9 || K < 1 || M < 1 || m_p < 1 || !(alpha > 0) || B < 1)
+    return fail(OPF_EINVAL, "need N>=9, K>=1, M>=1, m_p>=1, alpha>0");
+  for (int b = 0; b < B; ++b)
+    if (!(Re[b] > 0) || !(dt[b] > 0)) return fail(OPF_EINVAL, "need Re>0, dt>0");
+  if (!smooth235(3 * K) || !smooth235(3 * M))
+    return fail(OPF_EINVAL, "3K and 3M must have no prime factor other than 2, 3, 5");
+  opf::Dims& d = g->d;
+  d.N = N;
+  d.K = K;
+  d.M = M;
+  d.m_p = m_p;
+  d.nk = 2 * K - 1;
+  d.nz = 3 * K;
+  d.nth = 3 * M;
+  d.alpha = alpha;
+  d.Re = Re[0];
+  d.dt = dt[0];
+  d.c = 0.5;
+  d.F = (long)M * N * d.nk;
+  d.B = B;
+  opf::choose_chunks(&d);
+  if (!opf::make_plan(d.nz, &g->pz) || !opf::make_plan(d.nth, &g->pth))
+    return fail(OPF_EINVAL, "no FFT plan for 3K or 3M");
+  g->Re.assign(Re, Re + B);
+  g->dt.assign(dt, dt + B);
+  g->time.assign(B, 0.0);
+  g->shared_setup = true;
+  for (int b = 1; b < B; ++b)
+    if (Re[b] != Re[0] || dt[b] != dt[0]) g->shared_setup = false;
+  g->nJ = 0;
+  int rc = group_fill_setups(g, true);
+  if (rc) return rc;
   char* P = g->parena;
-  g->ds.prm = (double*)(P + o_prm);
-  g->ds.rinv = (double*)(P + o_rinv);
-  g->ds.d1 = (double*)(P + o_d1);
-  g->ds.wq = (double*)(P + o_wq);
-  g->ds.hop = (int*)(P + o_hop);
-  g->ds.luH = (double*)(P + o_luH);
-  g->ds.luP = (double*)(P + o_luP);
-  g->ds.basis = (double*)(P + o_basis);
-  g->ds.ainv = (double2*)(P + o_ainv);
-  g->ds.G = (double*)(P + o_G);
-  g->ds.tw_z = (double2*)(P + o_twz);
-  g->ds.tw_th = (double2*)(P + o_twt);
-  g->ds.tw_z32 = (float2*)(P + o_twz32);
-  g->ds.tw_th32 = (float2*)(P + o_twt32);
+  g->ds.prm = (double*)(P + g->o_prm);
+  g->ds.rinv = (double*)(P + g->o_rinv);
+  g->ds.d1 = (double*)(P + g->o_d1);
+  g->ds.wq = (double*)(P + g->o_wq);
+  g->ds.hop = (int*)(P + g->o_hop);
+  g->ds.luH = (double*)(P + g->o_luH);
+  g->ds.luP = (double*)(P + g->o_luP);
+  g->ds.basis = (double*)(P + g->o_basis);
+  g->ds.ainv = (double2*)(P + g->o_ainv);
+  g->ds.G = (double*)(P + g->o_G);
+  g->ds.tw_z = (double2*)(P + g->o_twz);
+  g->ds.tw_th = (double2*)(P + g->o_twt);
+  g->ds.tw_z32 = (float2*)(P + g->o_twz32);
+  g->ds.tw_th32 = (float2*)(P + g->o_twt32);
   d.ps = g->shared_setup ? 0 : (long)g->pstride;
   d.prm = g->ds.prm;
 
@@ -274,7 +295,7 @@ int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, con
   const size_t o_Nq = sl.add(3 * F16), o_W6 = sl.add(6 * F16), o_Z6 = sl.add(6 * P16);
   const size_t o_ZN = sl.add(3 * P16), o_abi = sl.add(3 * F16), o_tmp = sl.add(3 * F16);
   const size_t o_Nlin = sl.add(3 * F16), o_beta = sl.add(16), o_out3 = sl.add(32);
-  const size_t o_out2 = sl.add(16), o_flag = sl.add(16);
+  const size_t o_out2 = sl.add(16), o_flag = sl.add(16), o_cfl = sl.add(16);
   const size_t o_part = sl.add((size_t)2 * g->nblk_energy * sizeof(double));
   g->sstride = sl.off;
   if (cudaMalloc((void**)&g->sarena, g->sstride * B) != cudaSuccess)
@@ -298,6 +319,7 @@ int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, con
   g->out3 = (double*)(S + o_out3);
   g->out2 = (double*)(S + o_out2);
   g->flag = (int*)(S + o_flag);
+  g->cfl = (double*)(S + o_cfl);
   g->partial = (double*)(S + o_part);
   d.ss = (long)g->sstride;
   if (!opf::prepare_kernel_attrs(d))
@@ -311,6 +333,8 @@ struct Runner {
   cudaStream_t own = nullptr, stream = nullptr;
   int precision = 0, n_corr = 1, use_graph = 1, timing = 0;
   int autotune = 0;  // 1: time launch shapes on the next step, keep the fastest
+  double cfl_C = 0.0;   // > 0: CFL-controlled time step (single trajectory)
+  double dt_max = 0.0;  // upper bound of the controlled time step
   cudaGraphExec_t gexec = nullptr;
   cudaEvent_t ev[kMaxSlots][2];
   int slot_name[kMaxSlots];
@@ -405,6 +429,7 @@ void enqueue_solve(Runner* r, const Group& g, const double2* Na, const double2* 
 void enqueue_step(Runner* r) {
   for (Group* g : r->groups) {
     const double c = g->d.c;
+    if (g->d.cfl) cudaMemsetAsync(g->cfl, 0, sizeof(double), r->stream);
     enqueue_nonlinear(r, *g, g->U, g->Nj);
     enqueue_solve(r, *g, g->Nj, nullptr, 1.0, 0.0, g->U1);
     for (int q = 0; q < r->n_corr; ++q) {
@@ -502,6 +527,28 @@ int tune_group(Runner* r, Group* g) {
   return OPF_OK;
 }
 
+// CFL control (single trajectory): dt = min(dt_max, C / max(|u|/spacing)),
+// changed only when it must drop or could rise by more than 10 %; the
+// dt-dependent operators are then rebuilt in place.
+int cfl_update(Runner* r) {
+  for (Group* g : r->groups) {
+    if (!g->d.cfl || g->d.B != 1) continue;
+    double c = 0.0;
+    CU(cudaMemcpyAsync(&c, g->cfl, sizeof(double), cudaMemcpyDeviceToHost, r->stream));
+    CU(cudaStreamSynchronize(r->stream));
+    if (!(c > 0.0) || !std::isfinite(c)) continue;
+    const double target = std::min(r->dt_max, r->cfl_C / c);
+    const double cur = g->dt[0];
+    if (target < cur || target > 1.1 * cur) {
+      g->dt[0] = target;
+      g->d.dt = target;
+      int rc = group_fill_setups(g, false);
+      if (rc) return rc;
+    }
+  }
+  return OPF_OK;
+}
+
 int runner_step(Runner* r, int n) {
   if (n < 0) return fail(OPF_EINVAL, "step: n < 0");
   if (r->autotune == 1) {
@@ -542,11 +589,15 @@ int runner_step(Runner* r, int n) {
       int rc = harvest_timing(r);
       if (rc) return rc;
     }
+    for (Group* g : r->groups)
+      for (int b = 0; b < g->d.B; ++b) g->time[b] += g->dt[b];
+    if (r->cfl_C > 0.0) {
+      int rc = cfl_update(r);
+      if (rc) return rc;
+    }
   }
   CU(cudaStreamSynchronize(r->stream));
   CU(cudaGetLastError());
-  for (Group* g : r->groups)
-    for (int b = 0; b < g->d.B; ++b) g->time[b] += n * g->dt[b];
   return OPF_OK;
 }
 
@@ -785,11 +836,49 @@ int opf_nonlinear(opf_t* h, const double* coeffs, double* out) {
 
 int opf_set_option(opf_t* h, const char* key, double v) {
   if (check_handle(h)) return OPF_EINVAL;
+  if (key && !strcmp(key, "cfl")) {  // CFL number C; 0 switches control off
+    if (!(v >= 0.0 && v <= 10.0)) return fail(OPF_EINVAL, "cfl: 0 (off) .. 10");
+    h->run.cfl_C = v;
+    if (h->run.dt_max <= 0.0) h->run.dt_max = h->g.dt[0];
+    h->g.d.cfl = v > 0.0 ? h->g.cfl : nullptr;
+    h->g.d.rinv_cfl = h->g.ds.rinv;
+    h->run.drop_graph();
+    return OPF_OK;
+  }
+  if (key && !strcmp(key, "dt_max")) {
+    if (!(v > 0.0)) return fail(OPF_EINVAL, "dt_max: > 0");
+    h->run.dt_max = v;
+    return OPF_OK;
+  }
+  if (key && !strcmp(key, "dt")) {  // set the time step; dt-dependent operators are refactored
+    if (!(v > 0.0) || !std::isfinite(v)) return fail(OPF_EINVAL, "dt: > 0");
+    if (v != h->g.dt[0]) {
+      CU(cudaStreamSynchronize(h->run.stream));
+      h->g.dt[0] = v;
+      h->g.d.dt = v;
+      return group_fill_setups(&h->g, false);
+    }
+    return OPF_OK;
+  }
   return runner_option(&h->run, key, v);
 }
 
 int opf_get_option(opf_t* h, const char* key, double* v) {
   if (check_handle(h)) return OPF_EINVAL;
+  if (key && v && !strcmp(key, "cfl")) {
+    *v = h->run.cfl_C;
+    return OPF_OK;
+  }
+  if (key && v && !strcmp(key, "dt_max")) {
+    *v = h->run.dt_max > 0.0 ? h->run.dt_max : h->g.dt[0];
+    return OPF_OK;
+  }
+  if (key && v && !strcmp(key, "cfl_number")) {  // max |u| dt / spacing of the last step
+    double c = 0.0;
+    CU(cudaMemcpy(&c, h->g.cfl, sizeof(double), cudaMemcpyDeviceToHost));
+    *v = c * h->g.dt[0];
+    return OPF_OK;
+  }
   return runner_get_option(&h->run, key, v);
 }
 

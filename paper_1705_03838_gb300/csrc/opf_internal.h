@@ -83,6 +83,11 @@ struct Dims {
   int B = 1;
   long ss = 0, ps = 0;
   const double* prm = nullptr;  // trajectory 0's DevSetup::prm
+  // CFL reduction in the product kernel (null: off): per-trajectory maximum of
+  // |u_r|/dr, |u_t|/(r dtheta), |u_z|/dz written at cfl (+ b*ss), radial
+  // points from rinv_cfl (+ b*ps)
+  double* cfl = nullptr;
+  const double* rinv_cfl = nullptr;
 };
 
 void choose_chunks(Dims* d);

@@ -250,12 +250,36 @@ __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* _
   __syncthreads();
   V* res = block_fft(A, B, 3 * zc, ld, pth, tw, +1);
   V* C = (res == A) ? B : A;
+  // CFL number of this radial plane (optional): max over the grid of
+  // |u_r|/dr, |u_t|/(r dtheta), |u_z|/dz for the TOTAL velocity (the FP32
+  // path carries the perturbation only, so the laminar 1 - r^2 is added back)
+  double* cfl = bofs(d.cfl, d.ss);
+  double rn = 0.0, inv_dr = 0.0, inv_rdt = 0.0, inv_dz = 0.0, Ubase = 0.0;
+  if (cfl) {
+    const double* rinv = bofs(d.rinv_cfl, d.ps);
+    rn = 1.0 / rinv[n];
+    const double rm = n > 0 ? 1.0 / rinv[n - 1] : -rn;
+    const double rp = n < d.N - 1 ? 1.0 / rinv[n + 1] : 1.0 + (1.0 - rm);
+    inv_dr = 1.0 / fmin(rn - rm, rp - rn);
+    inv_rdt = d.m_p * nth / (6.283185307179586 * rn);
+    inv_dz = d.alpha * nz / 6.283185307179586;
+    if constexpr (sizeof(T) == 4) Ubase = 1.0 - rn * rn;
+  }
+  double cmax = 0.0;
   for (int e = threadIdx.x; e < zc * nth; e += blockDim.x) {
     const int q = e % nth, zr = e / nth;
     const V x0 = res[(zr * 3 + 0) * ld + q], x1 = res[(zr * 3 + 1) * ld + q], x2 = res[(zr * 3 + 2) * ld + q];
     const T ur = x0.x, ut = x0.y, uz = x1.x, wr = x1.y, wt = x2.x, wz = x2.y;
     C[(zr * 2 + 0) * ld + q] = V{ut * wz - uz * wt, uz * wr - ur * wz};
     C[(zr * 2 + 1) * ld + q] = V{ur * wt - ut * wr, (T)0};
+    if (cfl)
+      cmax = fmax(cmax, fmax(fabs((double)ur) * inv_dr,
+                             fmax(fabs((double)ut) * inv_rdt, fabs((double)uz + Ubase) * inv_dz)));
+  }
+  if (cfl) {  // block max, then one atomic per block (non-negative doubles order as integers)
+    for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    if ((threadIdx.x & 31) == 0 && cmax > 0.0)
+      atomicMax((unsigned long long*)cfl, (unsigned long long)__double_as_longlong(cmax));
   }
   __syncthreads();
   V* D = (C == A) ? B : A;
