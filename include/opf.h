@@ -165,6 +165,52 @@ int opf_ens_set_stream(opf_ens_t* e, void* stream);
 int opf_ens_kernel_times(opf_ens_t* e, int cap, int* count, const char** names,
                          double* total_ms, int* launches, int reset);
 
+/* ---- Newton-Krylov-trust-region solver (paper section 2: Newton utility
+ * with a combined Krylov / trust-region "hookstep" method, Viswanath 2007) --
+ * opf_nk_core solves F(x) = 0 for count independent problems of size n in
+ * lockstep: GMRES (modified Gram-Schmidt, FP64) builds a Krylov basis from
+ * Jacobian-vector products, the hookstep minimises the linearised residual
+ * inside a trust region via the SVD of the small Hessenberg matrix, and a
+ * trial is accepted when it achieves >= 1 % of the predicted reduction.
+ * Callbacks see a subset of the problems: idx[j] is the problem index of
+ * x[j]; commit = 1 marks points that become the base of the following
+ * Jacobian-vector products.  Return non-zero from a callback to abort.
+ * x: [count][n] in/out; scale: per problem (|F| <= tol * scale stops it);
+ * res_out: final |F| / scale; iters_out: accepted Newton steps. */
+typedef int (*opf_nk_residual)(void* ctx, int count, const int* idx, double* const* x,
+                               double* const* f, int commit);
+typedef int (*opf_nk_jv)(void* ctx, int count, const int* idx, double* const* x,
+                         double* const* v, double* const* jv);
+typedef struct {
+  int max_newton;    /* Newton iterations */
+  int max_krylov;    /* Krylov dimension per Newton iteration */
+  int max_hook;      /* trust-region trials per Newton iteration */
+  double tol;        /* |F| <= tol * scale stops a problem */
+  double gmres_tol;  /* GMRES relative residual target */
+  double delta0;     /* initial trust radius (<= 0: 0.1 |x|) */
+  /* used by opf_nk_solve only: */
+  double dt;         /* target time step; steps per period n = ceil(T / dt) */
+  double eps;        /* relative size of the finite-difference perturbation */
+  int fix_T;         /* 1: period T fixed (no time phase condition) */
+  int fix_s;         /* 1: axial shift s fixed (no axial phase condition) */
+  int precision;     /* time integrations: 0 FP64, 1 mixed */
+} opf_nk_opts;
+int opf_nk_core(int n, int count, double* x, const double* scale, opf_nk_residual F,
+                opf_nk_jv JV, void* ctx, const opf_nk_opts* opts, double* res_out,
+                int* iters_out);
+
+/* Periodic orbits / relative periodic orbits / travelling waves of the pipe
+ * flow: solve sigma_s Phi_T(u) = u, Phi_T the time-T map of opf_step (n steps
+ * of dt = T/n) and sigma_s the axial shift by s, for count initial guesses in
+ * lockstep (every Krylov step integrates all guesses in one batched launch
+ * sequence).  Unknowns: the state's independent coefficients, T and s (unless
+ * fixed), with phase conditions <du/dt, du'> = 0 and <du/dz, du'> = 0 closing
+ * the system.  states: [count] host states (state layout) in/out; T, s:
+ * [count] in/out; residual: [count] final |F| / |u|; iters: [count]. */
+int opf_nk_solve(int N, int K, int M, int m_p, double alpha, double Re, int count,
+                 double* states, double* T, double* s, const opf_nk_opts* opts,
+                 double* residual, int* iters);
+
 /* No counterpart in the paper: an allocation-free variant of opf_nonlinear
  * for callers that must not allocate device memory when they call (their
  * device memory is all owned by their own pool, cudaMalloc/cudaFree could

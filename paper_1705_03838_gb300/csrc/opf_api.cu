@@ -235,7 +235,7 @@ int group_fill_setups(Group* g, bool first) {
 // Build host setups, lay out and fill both arenas for B trajectories of one
 // shape with per-trajectory Re and dt (one shared setup when all are equal).
 int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, const double* Re,
-                const double* dt) {
+                const double* dt, bool separate_setups = false) {
   if (N < 9 || K < 1 || M < 1 || m_p < 1 || !(alpha > 0) || B < 1)
     return fail(OPF_EINVAL, "need N>=9, K>=1, M>=1, m_p>=1, alpha>0");
   for (int b = 0; b < B; ++b)
@@ -262,7 +262,7 @@ int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, con
   g->Re.assign(Re, Re + B);
   g->dt.assign(dt, dt + B);
   g->time.assign(B, 0.0);
-  g->shared_setup = true;
+  g->shared_setup = !separate_setups;
   for (int b = 1; b < B; ++b)
     if (Re[b] != Re[0] || dt[b] != dt[0]) g->shared_setup = false;
   g->nJ = 0;
@@ -1088,3 +1088,291 @@ int opf_setup_query(int N, int K, int M, int m_p, double alpha, double Re, doubl
 }
 
 }  // extern "C"
+
+// ====================================================================== Newton-Krylov front end
+namespace {
+
+// Independent real coefficients of a state (state layout [3][M][nk][N]):
+// m >= 1 all k (re, im); m = 0: k > 0 (re, im) and k = 0 (re only).
+struct NkPack {
+  int N, K, M, nk;
+  long ndof;
+  NkPack(int N_, int K_, int M_) : N(N_), K(K_), M(M_), nk(2 * K_ - 1) {
+    ndof = 3L * N * ((long)(M - 1) * nk * 2 + (K - 1) * 2 + 1);
+  }
+  void pack(const double* st, double* x) const {  // st: interleaved complex
+    long o = 0;
+    for (int c = 0; c < 3; ++c)
+      for (int m = 0; m < M; ++m)
+        for (int kk = 0; kk < nk; ++kk) {
+          const int k = kk - (K - 1);
+          if (m == 0 && k < 0) continue;
+          for (int n = 0; n < N; ++n) {
+            const double* z = st + 2 * ((((long)c * M + m) * nk + kk) * N + n);
+            x[o++] = z[0];
+            if (!(m == 0 && k == 0)) x[o++] = z[1];
+          }
+        }
+  }
+  void unpack(const double* x, double* st) const {
+    long o = 0;
+    for (int c = 0; c < 3; ++c)
+      for (int m = 0; m < M; ++m)
+        for (int kk = 0; kk < nk; ++kk) {
+          const int k = kk - (K - 1);
+          if (m == 0 && k < 0) continue;
+          for (int n = 0; n < N; ++n) {
+            double* z = st + 2 * ((((long)c * M + m) * nk + kk) * N + n);
+            z[0] = x[o++];
+            z[1] = (m == 0 && k == 0) ? 0.0 : x[o++];
+            if (m == 0 && k > 0) {  // conjugate partner
+              double* w = st + 2 * ((((long)c * M + m) * nk + (nk - 1 - kk)) * N + n);
+              w[0] = z[0];
+              w[1] = -z[1];
+            }
+          }
+        }
+  }
+};
+
+struct NkCtx {
+  Group g;
+  Runner run;
+  int N, K, M, m_p;
+  double alpha;
+  int count, nsteps;
+  long ndof, n;  // n = ndof + free (T, s)
+  opf_nk_opts o;
+  std::vector<double> T, s;           // per problem: period, shift of the base point
+  std::vector<std::vector<double>> phi, dphi_dt, dphi_ds, du_dt, du_dz, ubase;  // packed, base data
+  std::vector<double> st;             // scratch state (interleaved complex, one trajectory)
+  NkPack pk;
+  NkCtx(int N_, int K_, int M_) : pk(N_, K_, M_) {}
+};
+
+// multiply each axial mode k of a state by e^{i alpha k s} (shift by s) and,
+// if dz, by i alpha k (axial derivative)
+void shift_state(const NkCtx& c, double* st, double s, bool dz) {
+  const int nk = 2 * c.K - 1;
+  for (int f = 0; f < 3; ++f)
+    for (int m = 0; m < c.M; ++m)
+      for (int kk = 0; kk < nk; ++kk) {
+        const double ak = c.alpha * (kk - (c.K - 1));
+        const double cr = std::cos(ak * s), ci = std::sin(ak * s);
+        for (int n = 0; n < c.N; ++n) {
+          double* z = &st[2 * ((((long)f * c.M + m) * nk + kk) * c.N + n)];
+          double re = z[0] * cr - z[1] * ci, im = z[0] * ci + z[1] * cr;
+          if (dz) {
+            const double r2 = -ak * im, i2 = ak * re;
+            re = r2;
+            im = i2;
+          }
+          z[0] = re;
+          z[1] = im;
+        }
+      }
+}
+
+// dt per problem from its period; operators refactored when any changed
+int nk_set_periods(NkCtx* c, const int* idx, int cnt, const double* Ts) {
+  bool changed = false;
+  for (int j = 0; j < cnt; ++j) {
+    const double dt = Ts[j] / c->nsteps;
+    if (dt != c->g.dt[idx[j]]) {
+      c->g.dt[idx[j]] = dt;
+      changed = true;
+    }
+  }
+  if (changed) return group_fill_setups(&c->g, false);
+  return OPF_OK;
+}
+
+// integrate the given states (problem idx[j] uses trajectory idx[j]) for `steps`
+// steps; states in/out as interleaved complex host arrays
+int nk_integrate(NkCtx* c, int cnt, const int* idx, std::vector<std::vector<double>>& states, int steps) {
+  for (int j = 0; j < cnt; ++j) {
+    int rc = traj_set_state_host(&c->g, idx[j], states[j].data(), c->run.stream);
+    if (rc) return rc;
+  }
+  int rc = runner_step(&c->run, steps);
+  if (rc) return rc;
+  for (int j = 0; j < cnt; ++j) {
+    rc = traj_get_state(&c->g, idx[j], states[j].data(), true, c->run.stream);
+    if (rc) return rc;
+  }
+  return OPF_OK;
+}
+
+long nk_state_len(const NkCtx* c) { return 2L * 3 * c->M * (2 * c->K - 1) * c->N; }
+
+int nk_residual(void* vctx, int cnt, const int* idx, double* const* x, double* const* f, int commit) {
+  NkCtx* c = (NkCtx*)vctx;
+  const long L = nk_state_len(c);
+  std::vector<std::vector<double>> u(cnt, std::vector<double>(L));
+  std::vector<double> Ts(cnt), ss(cnt);
+  for (int j = 0; j < cnt; ++j) {
+    c->pk.unpack(x[j], u[j].data());
+    long o = c->ndof;
+    Ts[j] = c->o.fix_T ? c->T[idx[j]] : x[j][o++];
+    ss[j] = c->o.fix_s ? c->s[idx[j]] : x[j][o++];
+    if (!(Ts[j] > 0)) return fail(OPF_EINVAL, "nk: non-positive period");
+  }
+  int rc = nk_set_periods(c, idx, cnt, Ts.data());
+  if (rc) return rc;
+  std::vector<std::vector<double>> v = u;
+  rc = nk_integrate(c, cnt, idx, v, c->nsteps);
+  if (rc) return rc;
+  for (int j = 0; j < cnt; ++j) {
+    std::vector<double> w = v[j];
+    shift_state(*c, w.data(), ss[j], false);
+    c->pk.pack(w.data(), f[j]);
+    for (long t = 0; t < c->ndof; ++t) f[j][t] -= x[j][t];
+    for (long t = c->ndof; t < c->n; ++t) f[j][t] = 0.0;
+  }
+  if (!commit) return OPF_OK;
+  // base data for the Jacobian-vector products at these points
+  std::vector<std::vector<double>> v1 = v, u1 = u;
+  rc = nk_integrate(c, cnt, idx, v1, 1);  // one more step from Phi_T(u)
+  if (rc) return rc;
+  rc = nk_integrate(c, cnt, idx, u1, 1);  // one step from u
+  if (rc) return rc;
+  for (int j = 0; j < cnt; ++j) {
+    const int i = idx[j];
+    const double dt = c->g.dt[i];
+    c->T[i] = Ts[j];
+    c->s[i] = ss[j];
+    std::vector<double> w = v[j];
+    shift_state(*c, w.data(), ss[j], false);
+    c->phi[i].resize(c->ndof);
+    c->pk.pack(w.data(), c->phi[i].data());
+    std::vector<double> a = v1[j];
+    for (long t = 0; t < L; ++t) a[t] = (a[t] - v[j][t]) / dt;
+    shift_state(*c, a.data(), ss[j], false);
+    c->dphi_dt[i].resize(c->ndof);
+    c->pk.pack(a.data(), c->dphi_dt[i].data());
+    std::vector<double> b = v[j];
+    shift_state(*c, b.data(), ss[j], true);
+    c->dphi_ds[i].resize(c->ndof);
+    c->pk.pack(b.data(), c->dphi_ds[i].data());
+    std::vector<double> e = u1[j];
+    for (long t = 0; t < L; ++t) e[t] = (e[t] - u[j][t]) / dt;
+    c->du_dt[i].resize(c->ndof);
+    c->pk.pack(e.data(), c->du_dt[i].data());
+    std::vector<double> zz = u[j];
+    shift_state(*c, zz.data(), 0.0, true);
+    c->du_dz[i].resize(c->ndof);
+    c->pk.pack(zz.data(), c->du_dz[i].data());
+    c->ubase[i].assign(x[j], x[j] + c->ndof);
+  }
+  return OPF_OK;
+}
+
+int nk_jv(void* vctx, int cnt, const int* idx, double* const* x, double* const* v, double* const* jv) {
+  NkCtx* c = (NkCtx*)vctx;
+  const long L = nk_state_len(c);
+  std::vector<std::vector<double>> up(cnt, std::vector<double>(L));
+  std::vector<double> eps(cnt);
+  std::vector<double> tmp(c->ndof);
+  for (int j = 0; j < cnt; ++j) {
+    double xn = 0.0, vn = 0.0;
+    for (long t = 0; t < c->ndof; ++t) {
+      xn += x[j][t] * x[j][t];
+      vn += v[j][t] * v[j][t];
+    }
+    eps[j] = vn > 0 ? c->o.eps * std::sqrt(xn / vn) : 1.0;
+    for (long t = 0; t < c->ndof; ++t) tmp[t] = x[j][t] + eps[j] * v[j][t];
+    c->pk.unpack(tmp.data(), up[j].data());
+  }
+  int rc = nk_integrate(c, cnt, idx, up, c->nsteps);
+  if (rc) return rc;
+  for (int j = 0; j < cnt; ++j) {
+    const int i = idx[j];
+    shift_state(*c, up[j].data(), c->s[i], false);
+    c->pk.pack(up[j].data(), jv[j]);
+    const double dT = c->o.fix_T ? 0.0 : v[j][c->ndof];
+    const double ds = c->o.fix_s ? 0.0 : v[j][c->ndof + (c->o.fix_T ? 0 : 1)];
+    double pt = 0.0, pz = 0.0;
+    for (long t = 0; t < c->ndof; ++t) {
+      jv[j][t] = (jv[j][t] - c->phi[i][t]) / eps[j] - v[j][t] + dT * c->dphi_dt[i][t] + ds * c->dphi_ds[i][t];
+      pt += c->du_dt[i][t] * v[j][t];
+      pz += c->du_dz[i][t] * v[j][t];
+    }
+    long o = c->ndof;
+    if (!c->o.fix_T) jv[j][o++] = pt;
+    if (!c->o.fix_s) jv[j][o++] = pz;
+  }
+  return OPF_OK;
+}
+
+}  // namespace
+
+extern "C" int opf_nk_solve(int N, int K, int M, int m_p, double alpha, double Re, int count,
+                            double* states, double* T, double* s, const opf_nk_opts* o,
+                            double* residual, int* iters) {
+  if (count < 1 || !states || !T || !s || !o || !(o->dt > 0) || !(o->eps > 0))
+    return fail(OPF_EINVAL, "opf_nk_solve: bad arguments");
+  NkCtx* c = new NkCtx(N, K, M);
+  c->N = N;
+  c->K = K;
+  c->M = M;
+  c->m_p = m_p;
+  c->alpha = alpha;
+  c->count = count;
+  c->o = *o;
+  double Tmax = 0.0;
+  for (int i = 0; i < count; ++i) Tmax = std::max(Tmax, T[i]);
+  c->nsteps = std::max(1, (int)std::ceil(Tmax / o->dt - 1e-9));
+  std::vector<double> Re_v(count, Re), dt_v(count);
+  for (int i = 0; i < count; ++i) dt_v[i] = T[i] / c->nsteps;
+  // periods may diverge during the solve: every problem gets its own setup
+  int rc = group_build(&c->g, N, K, M, m_p, alpha, count, Re_v.data(), dt_v.data(), true);
+  if (rc == OPF_OK) rc = runner_init(&c->run);
+  if (rc != OPF_OK) {
+    group_free(&c->g);
+    runner_free(&c->run);
+    delete c;
+    return rc;
+  }
+  c->run.groups = {&c->g};
+  c->run.precision = o->precision;
+  c->ndof = c->pk.ndof;
+  c->n = c->ndof + (o->fix_T ? 0 : 1) + (o->fix_s ? 0 : 1);
+  c->T.assign(T, T + count);
+  c->s.assign(s, s + count);
+  c->phi.resize(count);
+  c->dphi_dt.resize(count);
+  c->dphi_ds.resize(count);
+  c->du_dt.resize(count);
+  c->du_dz.resize(count);
+  c->ubase.resize(count);
+  const long L = nk_state_len(c);
+  std::vector<double> x((size_t)count * c->n), scale(count);
+  for (int i = 0; i < count; ++i) {
+    double* xi = &x[(size_t)i * c->n];
+    c->pk.pack(states + (size_t)i * L, xi);
+    long q = c->ndof;
+    if (!o->fix_T) xi[q++] = T[i];
+    if (!o->fix_s) xi[q++] = s[i];
+    double nn = 0.0;
+    for (long t = 0; t < c->ndof; ++t) nn += xi[t] * xi[t];
+    scale[i] = std::sqrt(nn);
+  }
+  std::vector<double> res(count, 0.0);
+  std::vector<int> it(count, 0);
+  rc = opf_nk_core((int)c->n, count, x.data(), scale.data(), nk_residual, nk_jv, c, o, res.data(), it.data());
+  if (rc == OPF_OK) {
+    for (int i = 0; i < count; ++i) {
+      const double* xi = &x[(size_t)i * c->n];
+      c->pk.unpack(xi, states + (size_t)i * L);
+      long q = c->ndof;
+      if (!o->fix_T) T[i] = xi[q++];
+      if (!o->fix_s) s[i] = xi[q++];
+      if (residual) residual[i] = res[i];
+      if (iters) iters[i] = it[i];
+    }
+  }
+  runner_free(&c->run);
+  group_free(&c->g);
+  delete c;
+  return rc;
+}

@@ -18,6 +18,28 @@ _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 
 
+_pdp = ctypes.POINTER(ctypes.POINTER(ctypes.c_double))
+NK_RESIDUAL = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                               _pdp, _pdp, ctypes.c_int)
+NK_JV = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                         _pdp, _pdp, _pdp)
+
+
+class NkOpts(ctypes.Structure):
+    _fields_ = [("max_newton", ctypes.c_int), ("max_krylov", ctypes.c_int), ("max_hook", ctypes.c_int),
+                ("tol", ctypes.c_double), ("gmres_tol", ctypes.c_double), ("delta0", ctypes.c_double),
+                ("dt", ctypes.c_double), ("eps", ctypes.c_double), ("fix_T", ctypes.c_int),
+                ("fix_s", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+def nk_opts(**kw):
+    o = NkOpts(max_newton=30, max_krylov=60, max_hook=12, tol=1e-10, gmres_tol=1e-3, delta0=0.0,
+               dt=0.01, eps=1e-7, fix_T=0, fix_s=0, precision=0)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
 class OpfError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"opf error {code}: {msg}")
@@ -85,6 +107,12 @@ def lib():
         L.opf_ens_set_stream.argtypes = [vp, vp]
         L.opf_ens_kernel_times.restype = i
         L.opf_ens_kernel_times.argtypes = [vp, i, ip, ctypes.POINTER(cp), _dp, ip, i]
+        L.opf_nk_core.restype = i
+        L.opf_nk_core.argtypes = [i, i, _dp, _dp, NK_RESIDUAL, NK_JV, vp, ctypes.POINTER(NkOpts),
+                                  _dp, ctypes.POINTER(i)]
+        L.opf_nk_solve.restype = i
+        L.opf_nk_solve.argtypes = [i, i, i, i, d, d, i, vp, _dp, _dp, ctypes.POINTER(NkOpts), _dp,
+                                   ctypes.POINTER(i)]
         L.opf_nonlinear_noalloc.restype = i
         L.opf_nonlinear_noalloc.argtypes = [i, i, i, i, d, d, vp, vp, vp]
         L.opf_setup_query.restype = i
@@ -304,6 +332,61 @@ def opf_ens_kernel_times(e, reset=False):
     n = (ctypes.c_int * cap)()
     _check(lib().opf_ens_kernel_times(e.ptr, cap, ctypes.byref(count), names, ms, n, int(reset)))
     return {names[i].decode(): (ms[i], n[i]) for i in range(count.value)}
+
+
+def opf_nk_core(x0, F, JV, scale=None, **opts):
+    """Newton-Krylov-hookstep on count problems: x0 (count, n) float64;
+    F(idx, xs) -> list of residual arrays; JV(idx, xs, vs) -> list of arrays
+    (idx: problem indices of this batch).  Returns (x, residual, iters)."""
+    x = np.ascontiguousarray(x0, dtype=np.float64).copy()
+    count, n = x.shape
+    sc = np.ones(count) if scale is None else np.ascontiguousarray(scale, dtype=np.float64)
+
+    def view(ptrs, cnt):
+        return [np.ctypeslib.as_array(ptrs[j], shape=(n,)) for j in range(cnt)]
+
+    def f_cb(ctx, cnt, idx, xp, fp, commit):
+        try:
+            ids = [idx[j] for j in range(cnt)]
+            out = F(ids, [a.copy() for a in view(xp, cnt)])
+            for dst, src in zip(view(fp, cnt), out):
+                dst[:] = src
+            return 0
+        except Exception:
+            return -1
+
+    def jv_cb(ctx, cnt, idx, xp, vp, jp):
+        try:
+            ids = [idx[j] for j in range(cnt)]
+            out = JV(ids, [a.copy() for a in view(xp, cnt)], [a.copy() for a in view(vp, cnt)])
+            for dst, src in zip(view(jp, cnt), out):
+                dst[:] = src
+            return 0
+        except Exception:
+            return -1
+
+    fcb, jcb = NK_RESIDUAL(f_cb), NK_JV(jv_cb)
+    res = np.zeros(count)
+    it = (ctypes.c_int * count)()
+    o = nk_opts(**opts)
+    _check(lib().opf_nk_core(n, count, x.ctypes.data_as(_dp), sc.ctypes.data_as(_dp), fcb, jcb, None,
+                             ctypes.byref(o), res.ctypes.data_as(_dp), it))
+    return x, res, np.array(it[:])
+
+
+def opf_nk_solve(N, K, M, m_p, alpha, Re, states, T, s, **opts):
+    """Periodic-orbit / travelling-wave search for a list of guesses; returns
+    (states, T, s, relative residuals, Newton iterations)."""
+    count = len(states)
+    st = np.ascontiguousarray(np.stack(states), dtype=np.complex128)
+    Ta = np.ascontiguousarray(T, dtype=np.float64).copy()
+    sa = np.ascontiguousarray(s, dtype=np.float64).copy()
+    res = np.zeros(count)
+    it = (ctypes.c_int * count)()
+    o = nk_opts(**opts)
+    _check(lib().opf_nk_solve(N, K, M, m_p, alpha, Re, count, st.ctypes.data, Ta.ctypes.data_as(_dp),
+                              sa.ctypes.data_as(_dp), ctypes.byref(o), res.ctypes.data_as(_dp), it))
+    return list(st), Ta, sa, res, np.array(it[:])
 
 
 def opf_setup_query(N, K, M, m_p, alpha, Re, dt, what):
