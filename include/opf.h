@@ -211,6 +211,29 @@ int opf_nk_solve(int N, int K, int M, int m_p, double alpha, double Re, int coun
                  double* states, double* T, double* s, const opf_nk_opts* opts,
                  double* residual, int* iters);
 
+/* ---- Proposal network for Newton-Krylov initial guesses (no counterpart in
+ * the paper; the learned-proposal part of this implementation) ---------------
+ * A 1-D convolution net over the L radial points of the lowest Fourier modes:
+ *   h1 = gelu(conv3(x)), h2 = gelu(conv3(h1)), y = conv3(h2)  ([B][L][cin])
+ *   z = Wh mean_l(h2) + bh                                    ([B][nout])
+ * conv3: width 3 along r, zero padding.  BF16 operands, FP32 accumulation
+ * (tensor-core GEMMs), FP32 master weights, Adam.  Loss:
+ * mean((y - ty)^2) + lambda mean((z - tz)^2).  All array arguments of the
+ * forward/gradient/train calls are DEVICE pointers to float32; parameters
+ * are exchanged in the order W1 [H][3 cin], b1, W2 [H][3H], b2, W3 [cin][3H],
+ * b3, Wh [nout][H], bh (W[o][j*C + c] weights input channel c at offset j-1). */
+typedef struct opf_net opf_net_t;
+opf_net_t* opf_net_create(int cin, int hidden, int L, int nout, unsigned long long seed);
+void opf_net_destroy(opf_net_t* n);
+int opf_net_param_count(opf_net_t* n, long* total, long* sizes8);
+int opf_net_get_params(opf_net_t* n, float* host, int grads); /* grads=1: last gradients */
+int opf_net_set_params(opf_net_t* n, const float* host);
+int opf_net_forward(opf_net_t* n, const float* d_x, int B, float* d_y, float* d_z);
+int opf_net_gradients(opf_net_t* n, const float* d_x, const float* d_ty, const float* d_tz, int B,
+                      float lambda, double* loss);
+int opf_net_train_step(opf_net_t* n, const float* d_x, const float* d_ty, const float* d_tz, int B,
+                       float lambda, float lr, double* loss);
+
 /* No counterpart in the paper: an allocation-free variant of opf_nonlinear
  * for callers that must not allocate device memory when they call (their
  * device memory is all owned by their own pool, cudaMalloc/cudaFree could

@@ -113,6 +113,22 @@ def lib():
         L.opf_nk_solve.restype = i
         L.opf_nk_solve.argtypes = [i, i, i, i, d, d, i, vp, _dp, _dp, ctypes.POINTER(NkOpts), _dp,
                                    ctypes.POINTER(i)]
+        L.opf_net_create.restype = vp
+        L.opf_net_create.argtypes = [i, i, i, i, ctypes.c_ulonglong]
+        L.opf_net_destroy.restype = None
+        L.opf_net_destroy.argtypes = [vp]
+        L.opf_net_param_count.restype = i
+        L.opf_net_param_count.argtypes = [vp, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long)]
+        L.opf_net_get_params.restype = i
+        L.opf_net_get_params.argtypes = [vp, vp, i]
+        L.opf_net_set_params.restype = i
+        L.opf_net_set_params.argtypes = [vp, vp]
+        L.opf_net_forward.restype = i
+        L.opf_net_forward.argtypes = [vp, vp, i, vp, vp]
+        L.opf_net_gradients.restype = i
+        L.opf_net_gradients.argtypes = [vp, vp, vp, vp, i, ctypes.c_float, _dp]
+        L.opf_net_train_step.restype = i
+        L.opf_net_train_step.argtypes = [vp, vp, vp, vp, i, ctypes.c_float, ctypes.c_float, _dp]
         L.opf_nonlinear_noalloc.restype = i
         L.opf_nonlinear_noalloc.argtypes = [i, i, i, i, d, d, vp, vp, vp]
         L.opf_setup_query.restype = i
@@ -387,6 +403,69 @@ def opf_nk_solve(N, K, M, m_p, alpha, Re, states, T, s, **opts):
     _check(lib().opf_nk_solve(N, K, M, m_p, alpha, Re, count, st.ctypes.data, Ta.ctypes.data_as(_dp),
                               sa.ctypes.data_as(_dp), ctypes.byref(o), res.ctypes.data_as(_dp), it))
     return list(st), Ta, sa, res, np.array(it[:])
+
+
+class NetHandle:
+    def __init__(self, ptr, cin, hidden, L, nout):
+        self.ptr, self.cin, self.hidden, self.L, self.nout = ptr, cin, hidden, L, nout
+
+    def __del__(self):
+        try:
+            opf_net_destroy(self)
+        except Exception:
+            pass
+
+
+def opf_net_create(cin, hidden, L, nout, seed=1):
+    ptr = lib().opf_net_create(cin, hidden, L, nout, seed)
+    if not ptr:
+        raise OpfError(OPF_EINVAL, lib().opf_last_error().decode())
+    return NetHandle(ptr, cin, hidden, L, nout)
+
+
+def opf_net_destroy(n):
+    if n.ptr:
+        lib().opf_net_destroy(n.ptr)
+        n.ptr = None
+
+
+def opf_net_param_count(n):
+    tot = ctypes.c_long()
+    sizes = (ctypes.c_long * 8)()
+    _check(lib().opf_net_param_count(n.ptr, ctypes.byref(tot), sizes))
+    return tot.value, list(sizes)
+
+
+def opf_net_get_params(n, grads=False):
+    tot, _ = opf_net_param_count(n)
+    out = np.empty(tot, dtype=np.float32)
+    _check(lib().opf_net_get_params(n.ptr, out.ctypes.data, int(grads)))
+    return out
+
+
+def opf_net_set_params(n, flat):
+    a = np.ascontiguousarray(flat, dtype=np.float32)
+    _check(lib().opf_net_set_params(n.ptr, a.ctypes.data))
+
+
+def opf_net_forward(n, d_x, B, d_y, d_z):
+    """device pointers (float32): x [B][L][cin] -> y [B][L][cin], z [B][nout]"""
+    _check(lib().opf_net_forward(n.ptr, ctypes.c_void_p(d_x), int(B), ctypes.c_void_p(d_y),
+                                 ctypes.c_void_p(d_z)))
+
+
+def opf_net_gradients(n, d_x, d_ty, d_tz, B, lam):
+    loss = ctypes.c_double()
+    _check(lib().opf_net_gradients(n.ptr, ctypes.c_void_p(d_x), ctypes.c_void_p(d_ty), ctypes.c_void_p(d_tz),
+                                   int(B), float(lam), ctypes.byref(loss)))
+    return loss.value
+
+
+def opf_net_train_step(n, d_x, d_ty, d_tz, B, lam, lr):
+    loss = ctypes.c_double()
+    _check(lib().opf_net_train_step(n.ptr, ctypes.c_void_p(d_x), ctypes.c_void_p(d_ty), ctypes.c_void_p(d_tz),
+                                    int(B), float(lam), float(lr), ctypes.byref(loss)))
+    return loss.value
 
 
 def opf_setup_query(N, K, M, m_p, alpha, Re, dt, what):
