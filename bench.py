@@ -403,6 +403,49 @@ def run_large(args):
     print(json.dumps(line), flush=True)
 
 
+LEARNED = dict(N=48, K=24, M=16, m_p=2, alpha=1.25, dt=0.005, precision=1,
+               Re_train=(2000.0, 2500.0), Re_test=2250.0, amp=(0.03, 0.12), B_train=56, B_val=6, B_test=8,
+               seed=1705, warmup=20.0, n_snap=320, every=0.5, T_min=10.0, T_max=100.0, thresh=0.3,
+               hidden=384, steps=3000, batch=64, lr=1e-3, lam=1.0, net_seed=5, eval_every=200,
+               nk_guesses=16, nk_T_max=20.0,
+               nk=dict(max_newton=2, max_krylov=12, max_hook=4, dt=0.005, tol=1e-10))
+
+
+def run_learned(args):
+    """Learned Newton-Krylov proposals: 64 trajectories (56 for training, 6 of
+    them for validation, at Re uniform in [2000, 2500]; 8 held out at Re = 2250)
+    of N=48, |k|<24, m<16, m_p=2, 20,480 snapshots every 0.5 time units; the
+    BF16 network trained by the library's own kernels; Newton-Krylov-hookstep
+    from the 16 best held-out recurrences with recurrence, learned and
+    learned-state guesses under the same budget."""
+    import torch
+
+    from paper_1705_03838_gb300 import build as _build, learned, opf
+
+    torch.cuda.set_device(0)
+    _build.build()
+    opf.lib()
+    t0 = time.perf_counter()
+    res = learned.run_pipeline(opf, torch, LEARNED,
+                               log=lambda *a: print(*a, f"[{time.perf_counter() - t0:.0f} s]", file=sys.stderr,
+                                                    flush=True))
+    nk = res.get("nk", {})
+    line = {
+        "metric": "Newton-Krylov-hookstep from learned vs recurrence guesses: median final relative residual",
+        "value": nk.get("learned", {}).get("median_final"),
+        "unit": "relative residual",
+        "higher_is_better": False,
+        "n_gpus": 1,
+        "dtype": "bf16 net (f32 accumulate); f32+f64 snapshots; f64 Newton",
+        "data": "synthetic (the solver's own trajectories from seeded perturbations)",
+        "config": {"workload": "learned proposals: N=48 |k|<24 m<16 m_p=2 alpha=1.25, Re in [2000,2500], "
+                               "64 trajectories x 320 snapshots"},
+        "recurrence_median_final": nk.get("recurrence", {}).get("median_final"),
+        "details": res,
+    }
+    print(json.dumps(line, default=float), flush=True)
+
+
 def run_gpu(args, w):
     import numpy as np
     import torch
@@ -578,8 +621,9 @@ def main():
                     help="headline precision: 1 = mixed (default), 0 = FP64; both are timed")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="medium", choices=["medium", "ensemble", "large"],
-                    help="medium: the default single-run line; ensemble: the batched workload")
+    ap.add_argument("--workload", default="medium", choices=["medium", "ensemble", "large", "learned"],
+                    help="medium: the default single-run line; ensemble: the batched workload; large: the "
+                         "CFL-controlled large run; learned: the learned Newton-Krylov proposal pipeline")
     ap.add_argument("--autotune", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -591,6 +635,8 @@ def main():
         run_ensemble(args)
     elif args.workload == "large":
         run_large(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_gpu(args, w)
 
