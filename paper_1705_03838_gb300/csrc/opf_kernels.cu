@@ -413,6 +413,11 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
+// Bulk L2 prefetch by the TMA unit: p 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void band_solve4(const double* __restrict__ L, double* x, int st, int N) {
   const int t = threadIdx.x & 3;
   const unsigned full = 0xffffffffu;
@@ -505,7 +510,23 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   const long fs = d.F;
   const long base = (long)m * N * nk;
 
+  // Pull this block's factor blocks (pressure, u+, u-, u_z per mode) and
+  // basis blocks towards L2 with one bulk prefetch each, so they arrive while
+  // the right-hand sides are staged.  Factor blocks start on 16 bytes only for
+  // even N (104 N bytes per operator); basis blocks (48 N bytes) always do.
+  if (tid < 5 * T) {
+    const int mi = tid % T, which = tid / T;
+    const int ik = abs(min(kk0 + mi, nk - 1) - (K - 1));
+    if (which == 4) {
+      prefetch_l2_bulk(s.basis + (long)(ik * M + m) * 6 * N, 48u * N);
+    } else if (!(N & 1)) {
+      const long op = which == 0 ? ((ik == 0 && m == 0) ? K * M : ik * M + m) : ik * s.nJ + s.hop[3 * m + which - 1];
+      prefetch_l2_bulk((which == 0 ? s.luP : s.luH) + op * N * kLuSlots, (unsigned)N * kLuSlots * 8u);
+    }
+  }
+
   for (int e = tid; e < 2 * N * 9; e += NB) W1[e] = s.d1[e];
+#pragma unroll 4
   for (int e = tid; e < 3 * N * T; e += NB) {
     const int mi = e % T, i = (e / T) % N, f = e / (T * N);
     const int kk = min(kk0 + mi, nk - 1);
@@ -520,6 +541,7 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
     NE[(f * N + i) * T + mi] = v;
     UJ[(f * N + i) * T + mi] = a.Uj[g];
   }
+#pragma unroll 4
   for (int e = tid; e < 6 * N * T; e += NB) {
     const int i = e % N, b = (e / N) % 6, mi = e / (6 * N);
     const int ik = abs(min(kk0 + mi, nk - 1) - (K - 1));
