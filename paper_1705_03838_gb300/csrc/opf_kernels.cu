@@ -401,93 +401,124 @@ struct SolveDev {
   int nJ;
 };
 
+// Bulk L2 prefetch by the TMA unit: p 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // Banded substitution on one real right-hand side held in shared memory at
 // x[i * st], i < N, by a group of 4 consecutive lanes (column-oriented):
 // lane t keeps the partial sum of row c+1+t (and of row c+5+t for the wall
 // rows, whose lower band reaches 8); once row c is final its value is
 // broadcast and each lane subtracts its row's multiple of it.  Factor rows
 // use 13 slots (8 L entries for columns i-8..i-1, 1/U_ii, 4 U entries for
-// columns i+1..i+4); slots outside a row's band hold zeros.  All 32 lanes
-// of the warp must call this together (8 right-hand sides per warp).
-__device__ __forceinline__ void prefetch_l1(const void* p) {
-  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-}
-
-// Bulk L2 prefetch by the TMA unit: p 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
+// columns i+1..i+4, stored divided by U_ii); slots outside a row's band hold
+// zeros.  Each lane needs one factor entry per row; it is loaded kAhead rows
+// ahead into a register queue (the loop is unrolled by kAhead so the queue is
+// indexed statically), which keeps the L2 latency off the recursion.  All 32
+// lanes of the warp must call this together (8 right-hand sides per warp).
 __device__ __forceinline__ void band_solve4(const double* __restrict__ L, double* x, int st, int N) {
   const int t = threadIdx.x & 3;
   const unsigned full = 0xffffffffu;
-  constexpr int kAhead = 8;  // factor rows are pulled into L1 this many steps ahead
-  for (int q = 0; q < kAhead; ++q)
-    if (q + t < N) prefetch_l1(L + (q + t) * kLuSlots);
-  // forward: y = L^{-1} b
+  constexpr int kAhead = 16;
+  // forward: y = L^{-1} b.  Row c+1+t's entry in column c, queued kAhead rows
+  // ahead; on the wall rows (c >= N-9) also row c+5+t's entry in column c,
+  // all nine loaded up front.
+  auto la_of = [&](int c) {
+    const int r = c + 1 + t;
+    return (c < N && r < N) ? __ldg(L + r * kLuSlots + 7 - t) : 0.0;
+  };
+  double qa[kAhead], qw[9];
+#pragma unroll
+  for (int j = 0; j < kAhead; ++j) qa[j] = la_of(j);
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    const int c = N - 9 + j, r = c + 5 + t;
+    qw[j] = (c >= 0 && r < N) ? __ldg(L + r * kLuSlots + 3 - t) : 0.0;
+  }
   double sa = t < N ? x[t * st] : 0.0;
   double sb = 4 + t < N ? x[(4 + t) * st] : 0.0;
-  int r = 1 + t;  // row whose partial sum is in sa after the shift
-  double la = r < N ? L[r * kLuSlots + 7 - t] : 0.0;
-  for (int c = 0; c < N; ++c) {
-    const double y = __shfl_sync(full, sa, 0, 4);
-    if (t == 0) x[c * st] = y;
-    const double next_b = (t == 3 && c + 8 < N) ? x[(c + 8) * st] : 0.0;
-    double san = __shfl_down_sync(full, sa, 1, 4);
-    const double sb0 = __shfl_sync(full, sb, 0, 4);
-    double sbn = __shfl_down_sync(full, sb, 1, 4);
-    if (t == 3) {
-      san = sb0;
-      sbn = next_b;
+  for (int c0 = 0; c0 < N; c0 += kAhead) {
+#pragma unroll
+    for (int j = 0; j < kAhead; ++j) {
+      const int c = c0 + j;  // warp-uniform
+      if (c < N) {
+        const double y = __shfl_sync(full, sa, 0, 4);
+        if (t == 0) x[c * st] = y;
+        const double next_b = (t == 3 && c + 8 < N) ? x[(c + 8) * st] : 0.0;
+        double san = __shfl_down_sync(full, sa, 1, 4);
+        const double sb0 = __shfl_sync(full, sb, 0, 4);
+        double sbn = __shfl_down_sync(full, sb, 1, 4);
+        if (t == 3) {
+          san = sb0;
+          sbn = next_b;
+        }
+        sa = san - qa[j] * y;
+        if (c >= N - 9) {
+          double w = qw[0];
+#pragma unroll
+          for (int q = 1; q < 9; ++q)
+            if (c == N - 9 + q) w = qw[q];
+          sbn -= w * y;
+        }
+        sb = sbn;
+        qa[j] = la_of(c + kAhead);
+      }
     }
-    sa = san - la * y;
-    if (c >= N - 9) {  // wall rows: band reaches 8 below the diagonal
-      const int r2 = c + 5 + t;
-      if (r2 < N) sbn -= L[r2 * kLuSlots + 3 - t] * y;
-    }
-    sb = sbn;
-    if (c + 1 + kAhead + t < N) prefetch_l1(L + (c + 1 + kAhead + t) * kLuSlots);
-    r = c + 2 + t;
-    la = r < N ? L[r * kLuSlots + 7 - t] : 0.0;
   }
-  // backward: x = U^{-1} y
+  // y_i / U_ii for all rows at once (off the recursion; the U rows are stored
+  // scaled by 1/U_ii, so the backward sweep has a single FMA per row)
+  __syncwarp();
+  for (int i = t; i < N; i += 4) x[i * st] *= __ldg(L + i * kLuSlots + 8);
+  __syncwarp();
+  // backward: x = U~^{-1} (y / diag U).  Row c-1-t's scaled entry in column c.
+  auto ua_of = [&](int c) {
+    const int r = c - 1 - t;
+    return (c >= 0 && r >= 0) ? __ldg(L + r * kLuSlots + 9 + t) : 0.0;
+  };
+  double qu[kAhead];
+#pragma unroll
+  for (int j = 0; j < kAhead; ++j) qu[j] = ua_of(N - 1 - j);
   sa = N - 1 - t >= 0 ? x[(N - 1 - t) * st] : 0.0;
-  r = N - 2 - t;
-  double ua = r >= 0 ? L[r * kLuSlots + 9 + t] : 0.0;
-  double rinv = L[(N - 1) * kLuSlots + 8];
-  for (int c = N - 1; c >= 0; --c) {
-    const double xc = __shfl_sync(full, sa, 0, 4) * rinv;
-    if (t == 0) x[c * st] = xc;
-    const double next_y = (t == 3 && c - 4 >= 0) ? x[(c - 4) * st] : 0.0;
-    double san = __shfl_down_sync(full, sa, 1, 4);
-    if (t == 3) san = next_y;
-    sa = san - ua * xc;
-    if (c - 2 - kAhead - t >= 0) prefetch_l1(L + (c - 2 - kAhead - t) * kLuSlots);
-    r = c - 2 - t;
-    ua = r >= 0 ? L[r * kLuSlots + 9 + t] : 0.0;
-    rinv = c >= 1 ? L[(c - 1) * kLuSlots + 8] : 0.0;
+  for (int c0 = N - 1; c0 >= 0; c0 -= kAhead) {
+#pragma unroll
+    for (int j = 0; j < kAhead; ++j) {
+      const int c = c0 - j;  // warp-uniform
+      if (c >= 0) {
+        const double xc = __shfl_sync(full, sa, 0, 4);
+        if (t == 0) x[c * st] = xc;
+        const double next_y = (t == 3 && c - 4 >= 0) ? x[(c - 4) * st] : 0.0;
+        double san = __shfl_down_sync(full, sa, 1, 4);
+        if (t == 3) san = next_y;
+        sa = san - qu[j] * xc;
+        qu[j] = ua_of(c - kAhead);
+      }
+    }
   }
 }
 
-// One block: T consecutive k at fixed m.  Row-parallel phases use all 6T
-// threads over (chain, row); only the banded substitutions are sequential in r
-// (one thread per real right-hand side: 2T pressure chains, then 6T velocity
-// chains = (u+, u-, u_z) x T modes x (re, im)).
+// One block: T consecutive k at fixed m (24T threads).  Row-parallel phases
+// use all threads over (chain, row); only the banded substitutions are
+// sequential in r, with 4 lanes per real right-hand side (2T pressure chains,
+// then 6T velocity chains = (u+, u-, u_z) x T modes x (re, im)).  While warp
+// 0 solves the pressure system the other warps assemble the p-independent part
+// of the velocity right-hand sides; the last pass applies u_j, the influence
+// correction and the flux correction on the way out to global memory.
 template <int T>
 __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = d.N, nk = d.nk, M = d.M, K = d.K;
   constexpr int NT = 6 * T;   // velocity right-hand sides (chains)
   constexpr int NB = 24 * T;  // threads: 4 lanes per velocity chain
+  constexpr int NP = 8 * T;   // threads of the pressure substitution (2T chains x 4 lanes)
   double2* NE = (double2*)smraw;        // [3][N][T]  N_eff
   double2* S = NE + 3 * N * T;          // [N][T]     N+ + N-, later d_r p
   double2* P = S + N * T;               // [N][T]     pressure
   double2* coef = P + N * T;            // [T][4]     influence coefficients
   double* X = (double*)(coef + 4 * T);  // [N][6T]    velocity chains
   double* W1 = X + N * NT;              // [2][N][9]  first-derivative stencils
-  double* misc = W1 + 2 * N * 9;        // [2]        flux correction
-  double2* UJ = (double2*)(misc + 2);   // [3][N][T]  u_j
-  double* BS = (double*)(UJ + 3 * N * T);  // [T][6][N] influence basis of each mode's |k|
+  double* RI = W1 + 2 * N * 9;          // [N]        1/r
+  double* misc = RI + N;                // [2]        flux correction
   const int m = blockIdx.y, kk0 = blockIdx.x * T, tid = threadIdx.x;
   const int mt = d.m_p * m, ps = mt & 1, pv = ps ^ 1;
   s.d1 = bofs(s.d1, d.ps);
@@ -509,11 +540,17 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   const double ci = 1.0 / (cc * dtb), cu = (1.0 - cc) / cc;
   const long fs = d.F;
   const long base = (long)m * N * nk;
+  const double* wv = W1 + pv * N * 9;  // stencils of u_r, u_theta parity
+  const double* ws = W1 + ps * N * 9;  // stencils of u_z, p parity
+  // chain c -> (field f, mode mi, part); element (f, row i, mode mi) of a field
+  auto uj = [&](int f, int i, int mi) {
+    return a.Uj[f * fs + base + (long)i * nk + min(kk0 + mi, nk - 1)];
+  };
 
   // Pull this block's factor blocks (pressure, u+, u-, u_z per mode) and
   // basis blocks towards L2 with one bulk prefetch each, so they arrive while
-  // the right-hand sides are staged.  Factor blocks start on 16 bytes only for
-  // even N (104 N bytes per operator); basis blocks (48 N bytes) always do.
+  // the right-hand sides are assembled.  Factor blocks start on 16 bytes only
+  // for even N (104 N bytes per operator); basis blocks (48 N bytes) always do.
   if (tid < 5 * T) {
     const int mi = tid % T, which = tid / T;
     const int ik = abs(min(kk0 + mi, nk - 1) - (K - 1));
@@ -525,12 +562,13 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
     }
   }
 
+  // ---- N_eff = wa N_a + wb N_b, and N+ + N- for the divergence
   for (int e = tid; e < 2 * N * 9; e += NB) W1[e] = s.d1[e];
+  for (int e = tid; e < N; e += NB) RI[e] = s.rinv[e];
 #pragma unroll 4
   for (int e = tid; e < 3 * N * T; e += NB) {
     const int mi = e % T, i = (e / T) % N, f = e / (T * N);
-    const int kk = min(kk0 + mi, nk - 1);
-    const long g = f * fs + base + (long)i * nk + kk;
+    const long g = f * fs + base + (long)i * nk + min(kk0 + mi, nk - 1);
     const double2 u = a.Na[g];
     double2 v = double2{a.wa * u.x, a.wa * u.y};
     if (a.Nb) {
@@ -539,13 +577,6 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
       v.y += a.wb * w.y;
     }
     NE[(f * N + i) * T + mi] = v;
-    UJ[(f * N + i) * T + mi] = a.Uj[g];
-  }
-#pragma unroll 4
-  for (int e = tid; e < 6 * N * T; e += NB) {
-    const int i = e % N, b = (e / N) % 6, mi = e / (6 * N);
-    const int ik = abs(min(kk0 + mi, nk - 1) - (K - 1));
-    BS[(mi * 6 + b) * N + i] = s.basis[((long)(ik * M + m) * 6 + b) * N + i];
   }
   __syncthreads();
   for (int e = tid; e < N * T; e += NB) {
@@ -553,8 +584,6 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
     S[e] = double2{p.x + q.x, p.y + q.y};
   }
   __syncthreads();
-  const double* wv = W1 + pv * N * 9;
-  const double* ws = W1 + ps * N * 9;
 
   // ---- pressure right-hand side: div N_eff (rows < N-1), 0 at the wall
   for (int e = tid; e < N * T; e += NB) {
@@ -568,11 +597,12 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
         const double2 sv = S[(lo + q) * T + mi];
-        ax += wv[i * 9 + q] * sv.x;
-        ay += wv[i * 9 + q] * sv.y;
+        const double w = wv[i * 9 + q];
+        ax += w * sv.x;
+        ay += w * sv.y;
       }
       const double2 np = NE[i * T + mi], nm = NE[(N + i) * T + mi], nz = NE[(2 * N + i) * T + mi];
-      const double ri = 0.5 * s.rinv[i];
+      const double ri = 0.5 * RI[i];
       b.x = 0.5 * ax + ri * ((1 + mt) * np.x + (1 - mt) * nm.x) - ak * nz.y;
       b.y = 0.5 * ay + ri * ((1 + mt) * np.y + (1 - mt) * nm.y) + ak * nz.x;
     }
@@ -580,16 +610,29 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   }
   __syncthreads();
 
-  // ---- pressure-Poisson solve (provisional dp/dr(1) = 0; (0,0): p(1) = 0)
-  if (tid < 8 * T) {  // 2T chains x 4 lanes
+  if (tid < NP) {
+    // ---- pressure-Poisson solve (provisional dp/dr(1) = 0; (0,0): p(1) = 0)
     const int j = tid >> 2, part = j & 1, mi = j >> 1;
     const int k = min(kk0 + mi, nk - 1) - (K - 1), ik = abs(k);
     const int op = (ik == 0 && m == 0) ? K * M : ik * M + m;
     band_solve4(s.luP + (long)op * N * kLuSlots, (double*)P + 2 * mi + part, 2 * T, N);
+  } else {
+    // ---- meanwhile: the p-independent part of the velocity right-hand sides
+    for (int e = tid - NP; e < N * NT; e += NB - NP) {
+      const int c = e % NT, i = e / NT;
+      const int part = c & 1, mi = (c >> 1) % T, f = (c >> 1) / T;
+      double b = 0.0;
+      if (i < N - 1) {
+        const double2 u = uj(f, i, mi);
+        const double2 ne = NE[(f * N + i) * T + mi];
+        b = ci * (part ? u.y : u.x) + (part ? ne.y : ne.x);
+      }
+      X[i * NT + c] = b;
+    }
   }
   __syncthreads();
 
-  // ---- d_r p once per (mode, row) into S, then velocity right-hand sides
+  // ---- d_r p once per (mode, row), then subtract grad p from the right-hand sides
   for (int e = tid; e < N * T; e += NB) {
     const int mi = e % T, i = e / T;
     const int lo = row_lo_d(i, N);
@@ -597,33 +640,28 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
       const double2 pv2 = P[(lo + q) * T + mi];
-      ax += ws[i * 9 + q] * pv2.x;
-      ay += ws[i * 9 + q] * pv2.y;
+      const double w = ws[i * 9 + q];
+      ax += w * pv2.x;
+      ay += w * pv2.y;
     }
     S[i * T + mi] = double2{ax, ay};
   }
   __syncthreads();
-  for (int e = tid; e < N * NT; e += NB) {
+#pragma unroll 4
+  for (int e = tid; e < (N - 1) * NT; e += NB) {
     const int c = e % NT, i = e / NT;
     const int part = c & 1, mi = (c >> 1) % T, f = (c >> 1) / T;
-    const int kk = min(kk0 + mi, nk - 1);
-    const double ak = d.alpha * (kk - (K - 1));
-    double b = 0.0;
-    if (i < N - 1) {
-      const double2 pp = P[i * T + mi];
-      double gp;
-      if (f < 2) {
-        const double2 dp = S[i * T + mi];
-        const double q = mt * s.rinv[i] * (part ? pp.y : pp.x);
-        gp = (part ? dp.y : dp.x) + (f == 0 ? -q : q);
-      } else {
-        gp = part == 0 ? -ak * pp.y : ak * pp.x;
-      }
-      const double2 u = UJ[(f * N + i) * T + mi];
-      const double2 ne = NE[(f * N + i) * T + mi];
-      b = ci * (part ? u.y : u.x) + (part ? ne.y : ne.x) - gp;
+    const double2 pp = P[i * T + mi];
+    double gp;
+    if (f < 2) {
+      const double2 dp = S[i * T + mi];
+      const double q = mt * RI[i] * (part ? pp.y : pp.x);
+      gp = (part ? dp.y : dp.x) + (f == 0 ? -q : q);
+    } else {
+      const double ak = d.alpha * (min(kk0 + mi, nk - 1) - (K - 1));
+      gp = part == 0 ? -ak * pp.y : ak * pp.x;
     }
-    X[i * NT + c] = b;
+    X[i * NT + c] -= gp;
   }
   __syncthreads();
 
@@ -637,85 +675,84 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   }
   __syncthreads();
 
-  // ---- u = v - ((1-c)/c) u_j; influence matrix: g = (u+(1), u-(1), u_z(1), div u(1))
-  for (int e = tid; e < N * NT; e += NB) {
-    const int c = e % NT, i = e / NT;
-    const int part = c & 1, mi = (c >> 1) % T, f = (c >> 1) / T;
-    const double2 u = UJ[(f * N + i) * T + mi];
-    X[i * NT + c] -= cu * (part ? u.y : u.x);
-  }
-  __syncthreads();
-  if (tid < T && kk0 + tid < nk) {
-    const int mj = tid, kj = kk0 + tid;
+  // ---- influence matrix on u = v - ((1-c)/c) u_j:
+  //      g = (u+(1), u-(1), u_z(1), div u(1)),  a = -A^{-1} g  (thread: mode, row of A^{-1})
+  if (tid < 4 * T && kk0 + (tid >> 2) < nk) {
+    const int mj = tid >> 2, r = tid & 3, kj = kk0 + mj;
     const double akj = d.alpha * (kj - (K - 1));
-    auto xv = [&](int ff, int i) {
+    auto uv = [&](int ff, int i) {
       const int c = (ff * T + mj) << 1;
-      return double2{X[i * NT + c], X[i * NT + c + 1]};
+      const double2 w = uj(ff, i, mj);
+      return double2{X[i * NT + c] - cu * w.x, X[i * NT + c + 1] - cu * w.y};
     };
-    const double2 g0 = xv(0, N - 1), g1 = xv(1, N - 1), g2 = xv(2, N - 1);
+    const double2 g0 = uv(0, N - 1), g1 = uv(1, N - 1), g2 = uv(2, N - 1);
     const int lo = N - 9;
     double ax = 0.0, ay = 0.0;
+#pragma unroll
     for (int q = 0; q < 9; ++q) {
       const double w = wv[(N - 1) * 9 + q];
-      const double2 p = xv(0, lo + q), mm = xv(1, lo + q);
+      const double2 p = uv(0, lo + q), mm = uv(1, lo + q);
       ax += w * (p.x + mm.x);
       ay += w * (p.y + mm.y);
     }
-    const double ri = 0.5 * s.rinv[N - 1];
-    double2 g[4] = {g0, g1, g2,
-                    double2{0.5 * ax + ri * ((1 + mt) * g0.x + (1 - mt) * g1.x) - akj * g2.y,
-                            0.5 * ay + ri * ((1 + mt) * g0.y + (1 - mt) * g1.y) + akj * g2.x}};
-    const double2* Ai = s.ainv + ((long)m * nk + kj) * 16;
-    for (int r = 0; r < 4; ++r) {
-      double sx = 0.0, sy = 0.0;
-      for (int c = 0; c < 4; ++c) {
-        const double2 A = Ai[r * 4 + c];
-        sx += A.x * g[c].x - A.y * g[c].y;
-        sy += A.x * g[c].y + A.y * g[c].x;
-      }
-      coef[mj * 4 + r] = double2{-sx, -sy};
+    const double ri = 0.5 * RI[N - 1];
+    const double2 g[4] = {g0, g1, g2,
+                          double2{0.5 * ax + ri * ((1 + mt) * g0.x + (1 - mt) * g1.x) - akj * g2.y,
+                                  0.5 * ay + ri * ((1 + mt) * g0.y + (1 - mt) * g1.y) + akj * g2.x}};
+    const double2* Ai = s.ainv + ((long)m * nk + kj) * 16 + r * 4;
+    double sx = 0.0, sy = 0.0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double2 A = Ai[c];
+      sx += A.x * g[c].x - A.y * g[c].y;
+      sy += A.x * g[c].y + A.y * g[c].x;
     }
+    coef[mj * 4 + r] = double2{-sx, -sy};
   }
   __syncthreads();
 
-  // ---- add basis responses
-  for (int e = tid; e < N * NT; e += NB) {
-    const int c = e % NT, i = e / NT;
+  // final value of chain c at row i: v - ((1-c)/c) u_j + basis responses
+  auto final_value = [&](int i, int c) {
     const int part = c & 1, mi = (c >> 1) % T, f = (c >> 1) / T;
-    const int k = min(kk0 + mi, nk - 1) - (K - 1);
-    const double* Bv = BS + mi * 6 * N;
+    const int kk = min(kk0 + mi, nk - 1), k = kk - (K - 1);
+    const double* Bv = s.basis + (long)(abs(k) * M + m) * 6 * N;
     const double2 a0 = coef[mi * 4 + 0], ax = coef[mi * 4 + 1 + f];
     const double sk = k > 0 ? 1.0 : (k < 0 ? -1.0 : 0.0);
     const double c0 = f == 2 ? (part ? sk * a0.x : -sk * a0.y) : (part ? a0.y : a0.x);
     const double c1 = part ? ax.y : ax.x;
-    X[i * NT + c] += c0 * Bv[f * N + i] + c1 * Bv[(3 + f) * N + i];
-  }
-  __syncthreads();
+    const double2 w = a.Uj[f * fs + base + (long)i * nk + kk];
+    return X[i * NT + c] - cu * (part ? w.y : w.x) + c0 * Bv[f * N + i] + c1 * Bv[(3 + f) * N + i];
+  };
 
   // ---- fixed flux on (0,0): beta' so that 2 pi int u_z r dr = pi/2
   const bool has_mean = (m == 0 && kk0 <= K - 1 && K - 1 < kk0 + T);
+  const int cz = (2 * T + (K - 1 - kk0)) << 1;  // chain (u_z, mode k=0, re)
   if (has_mean) {
-    const int cz = (2 * T + (K - 1 - kk0)) << 1;  // chain (u_z, mode k=0, re)
-    if (tid == 0) {
+    if (tid < 32) {  // warp 0 (full: NB >= 96)
       double q = 0.0;
-      for (int i = 0; i < N; ++i) q += s.wq[i] * X[i * NT + cz];
-      const double bp = (0.25 - q) / s.prm[kPrmSumWG];
-      misc[0] = bp;
-      *a.beta_p = bp;
+      for (int i = tid; i < N; i += 32) q += s.wq[i] * final_value(i, cz);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      if (tid == 0) {
+        const double bp = (0.25 - q) / s.prm[kPrmSumWG];
+        misc[0] = bp;
+        *a.beta_p = bp;
+      }
     }
     __syncthreads();
-    const double bp = misc[0];
-    for (int i = tid; i < N; i += NB) X[i * NT + cz] += bp * s.G[i];
-    __syncthreads();
   }
+  const double bp = has_mean ? misc[0] : 0.0;
 
   // ---- write out (coalesced over k)
+#pragma unroll 4
   for (int e = tid; e < N * NT; e += NB) {
     const int c = e % NT, i = e / NT;
     const int part = c & 1, mi = (c >> 1) % T, f = (c >> 1) / T;
     if (kk0 + mi >= nk) continue;
+    double v = final_value(i, c);
+    if (has_mean && c == cz) v += bp * s.G[i];
     double* out = (double*)(a.Uout + f * fs + base + (long)i * nk + kk0 + mi) + part;
-    *out = X[i * NT + c];
+    *out = v;
   }
 }
 
@@ -735,8 +772,7 @@ static int solve_tile(const Dims& d) {
 size_t solve_smem_bytes(int N, int T) { return solve_smem(N, T); }
 
 static size_t solve_smem(int N, int T) {
-  return (size_t)(5 * N * T + 4 * T) * 16 + (size_t)6 * N * T * 8 + (size_t)(2 * N * 9 + 2) * 8 +
-         (size_t)3 * N * T * 16 + (size_t)6 * N * T * 8;
+  return (size_t)(5 * N * T + 4 * T) * 16 + (size_t)6 * N * T * 8 + (size_t)(2 * N * 9 + N + 2) * 8;
 }
 
 // Chunk sizes keep every transform block within ~96 KB of shared memory (two

@@ -189,6 +189,18 @@ static void wall_neumann(const Setup* s, int par, Op* op) {
 
 // Pivot-free banded LU of op into 13-slot rows; checks the factor on a test
 // right-hand side against the unfactored matrix.
+// Solve with a factor stored by factor(): unit-lower L, then 1/U_ii, then the
+// row-scaled unit-upper U (the same order as the GPU substitution).
+static void lu_solve(const double* f, int N, double* x) {
+  for (int i = 0; i < N; ++i)
+    for (int t = 0; t < 8; ++t)
+      if (i - 8 + t >= 0) x[i] -= f[(size_t)i * kLuSlots + t] * x[i - 8 + t];
+  for (int i = 0; i < N; ++i) x[i] *= f[(size_t)i * kLuSlots + 8];
+  for (int i = N - 1; i >= 0; --i)
+    for (int t = 1; t <= 4; ++t)
+      if (i + t < N) x[i] -= f[(size_t)i * kLuSlots + 8 + t] * x[i + t];
+}
+
 static bool factor(Op* op, double* out, std::string* err, const char* what) {
   const int N = op->N;
   const std::vector<double> orig = op->a;
@@ -213,20 +225,15 @@ static bool factor(Op* op, double* out, std::string* err, const char* what) {
       row[t] = (j >= 0) ? op->at(i, j) : 0.0;
     }
     row[8] = 1.0 / op->at(i, i);
-    for (int t = 1; t <= 4; ++t) row[8 + t] = (i + t < N) ? op->at(i, i + t) : 0.0;
+    // U stored row-scaled by 1/U_ii (unit upper triangle), so the backward
+    // recursion needs no division: x_i = y_i / U_ii - sum_t (U_i,i+t / U_ii) x_i+t
+    for (int t = 1; t <= 4; ++t) row[8 + t] = (i + t < N) ? op->at(i, i + t) * row[8] : 0.0;
   }
   // self-check: solve A x = b and compare A x with b
   std::vector<double> b(N), x(N);
   for (int i = 0; i < N; ++i) b[i] = std::sin(1.0 + i) + 0.5;
   x = b;
-  for (int i = 0; i < N; ++i)
-    for (int t = 0; t < 8; ++t)
-      if (i - 8 + t >= 0) x[i] -= out[(size_t)i * kLuSlots + t] * x[i - 8 + t];
-  for (int i = N - 1; i >= 0; --i) {
-    for (int t = 1; t <= 4; ++t)
-      if (i + t < N) x[i] -= out[(size_t)i * kLuSlots + 8 + t] * x[i + t];
-    x[i] *= out[(size_t)i * kLuSlots + 8];
-  }
+  lu_solve(out, N, x.data());
   double res = 0.0, anorm = 0.0, xnorm = 0.0;
   for (int i = 0; i < N; ++i) {
     double acc = 0.0, rs = 0.0;
@@ -249,16 +256,6 @@ static bool factor(Op* op, double* out, std::string* err, const char* what) {
 }
 
 // Banded LU solve with the 13-slot factor (same arithmetic as the device).
-static void lu_solve(const double* f, int N, double* x) {
-  for (int i = 0; i < N; ++i)
-    for (int t = 0; t < 8; ++t)
-      if (i - 8 + t >= 0) x[i] -= f[(size_t)i * kLuSlots + t] * x[i - 8 + t];
-  for (int i = N - 1; i >= 0; --i) {
-    for (int t = 1; t <= 4; ++t)
-      if (i + t < N) x[i] -= f[(size_t)i * kLuSlots + 8 + t] * x[i + t];
-    x[i] *= f[(size_t)i * kLuSlots + 8];
-  }
-}
 
 static void d1_apply(const Setup* s, int par, const double* v, double* out) {
   const int N = s->N;
