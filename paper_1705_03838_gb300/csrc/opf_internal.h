@@ -135,4 +135,22 @@ int energy_blocks(const Dims& d);
 void launch_wall(const Dims& d, const DevSetup& s, const double2* U, double* out2, cudaStream_t st);
 void launch_nan_check(const double* x, long n, int* flag, cudaStream_t st);
 
+// Tensor-core GEMM (tcgen05, BF16 operands, FP32 accumulation):
+// C[m][n] = sum_k A[m][k] B[n][k] for m < M, n < N; A [Mp][Kp] and B [Np][Kp]
+// row-major BF16, zero padded (Mp, Np multiples of 128, Kp of 64), 16-byte
+// aligned.  Epilogue per (m, n): x = C + bias[n]; pre_f32 = x; x = gelu(x)
+// if gelu; out_f32 = x (+= x if accumulate); out_bf16 = bf16(x); outputs
+// have row stride ldo.  d_err (device int) is set on a timed-out wait.
+struct TcEpilogue {
+  const float* bias;
+  int gelu;
+  float* pre_f32;
+  float* out_f32;
+  int accumulate;
+  void* out_bf16;
+  long ldo;
+};
+int tc_gemm(const void* A, const void* B, int M, int N, int Mp, int Np, int Kp, const TcEpilogue& e, int* d_err,
+            cudaStream_t st);
+
 }  // namespace opf

@@ -9,9 +9,11 @@
 //
 // conv3 is a width-3 convolution along l with zero padding.  Every
 // convolution and its two backward products is one GEMM on BF16 operands
-// with FP32 accumulation (mma.sync m16n8k16 tensor-core instructions); the
-// im2col matrix is never formed -- the tile loader reads x[b][l + j - 1][c]
-// for column j*C + c.  Master weights and Adam moments are FP32.
+// with FP32 accumulation on the tcgen05 tensor cores (opf_tcgemm.cu), which
+// take row-major K-contiguous operands zero padded to 128-row / 64-column
+// multiples; small kernels here lay the operands out that way (im2col rows
+// x[b][l + j - 1][c] at column j*C + c, transposes, padded weights).  Master
+// weights and Adam moments are FP32.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -26,172 +28,75 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-// ------------------------------------------------------------------ GEMM
-// C[m][n] = sum_k A(m,k) B(n,k).  Operand addressing modes:
-enum AMode { A_ROWMAJOR = 0, A_IM2COL = 1, A_IM2COL_REV = 2, A_COLMAJOR = 3 };
-enum BMode { B_ROWMAJOR = 0, B_COLMAJOR = 1, B_WT_SHIFT = 2, B_IM2COL_T = 3 };
-
-struct GemmArgs {
-  int M, N, K;
-  // A
-  const void* A;
-  int a_mode, a_f32;  // a_f32: A is float (converted to bf16 on load)
-  long lda;           // ROWMAJOR: A[m*lda + k]; COLMAJOR: A[k*lda + m]
-  int L, C;           // IM2COL: m = b*L + l, k = j*C + c, src x[(b*L + l + s(j-1))*C + c]
-  // B
-  const void* Bp;
-  int b_mode, b_f32;
-  long ldb;           // ROWMAJOR: B[n*ldb + k]; COLMAJOR: B[k*ldb + n]
-  int bN, bC;         // WT_SHIFT: k = j*bN + o, value W[o*ldb + j*bC + n]
-                      // IM2COL_T: n = j*bC + c, k = b*bN + l -> x[(b*bN + l + j - 1)*bC + c]
-  // epilogue
-  const float* bias;  // per n (may be null)
-  int gelu;           // 1: out = gelu(acc + bias)
-  float* out_f32;     // [m][n] (ld = N), may be null
-  float* pre_f32;     // pre-activation (acc + bias), may be null
-  bf16* out_bf16;     // may be null
-  int accumulate;     // out_f32 += acc
-};
-
+// ------------------------------------------------------------------ operand layouts
 __device__ __forceinline__ float gelu_f(float x) {
   return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
 }
+
 __device__ __forceinline__ float gelu_grad(float x) {
   const float cdf = 0.5f * (1.0f + erff(x * 0.70710678118654752f));
   const float pdf = 0.39894228040143268f * expf(-0.5f * x * x);
   return cdf + x * pdf;
 }
 
-template <typename T>
-__device__ __forceinline__ float ldf(const void* p, long i) {
-  return (float)((const T*)p)[i];
-}
+long pad128(long v) { return (v + 127) / 128 * 128; }
+long pad64(long v) { return (v + 63) / 64 * 64; }
 
-__device__ __forceinline__ float load_a(const GemmArgs& g, int m, int k) {
-  if (m >= g.M || k >= g.K) return 0.f;
-  long idx;
-  switch (g.a_mode) {
-    case A_ROWMAJOR: idx = (long)m * g.lda + k; break;
-    case A_COLMAJOR: idx = (long)k * g.lda + m; break;
-    default: {
-      const int b = m / g.L, l = m - b * g.L, j = k / g.C, c = k - j * g.C;
-      const int ls = l + (g.a_mode == A_IM2COL ? (j - 1) : (1 - j));
-      if (ls < 0 || ls >= g.L) return 0.f;
-      idx = ((long)b * g.L + ls) * g.C + c;
+// im2col rows: out[m][j*C + c] = x[b][l + s(j-1)][c] (m = b*L + l; s = +1, or
+// -1 for the transposed convolution), zero outside 0 <= l' < L, m >= M or
+// k >= 3C; out is [Mp][Kp]
+__global__ void k_im2col(const bf16* __restrict__ x, int L, int C, int M, int rev, bf16* __restrict__ out, int Mp,
+                         int Kp) {
+  const long n = (long)Mp * Kp;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int m = (int)(i / Kp), k = (int)(i - (long)m * Kp);
+    bf16 v = __float2bfloat16(0.f);
+    if (m < M && k < 3 * C) {
+      const int j = k / C, c = k - j * C, b = m / L, l = m - b * L;
+      const int ls = l + (rev ? 1 - j : j - 1);
+      if (ls >= 0 && ls < L) v = x[((long)b * L + ls) * C + c];
     }
+    out[i] = v;
   }
-  return g.a_f32 ? ldf<float>(g.A, idx) : __bfloat162float(((const bf16*)g.A)[idx]);
 }
 
-__device__ __forceinline__ float load_b(const GemmArgs& g, int n, int k) {
-  if (n >= g.N || k >= g.K) return 0.f;
-  long idx;
-  switch (g.b_mode) {
-    case B_ROWMAJOR: idx = (long)n * g.ldb + k; break;
-    case B_COLMAJOR: idx = (long)k * g.ldb + n; break;
-    case B_WT_SHIFT: {
-      const int j = k / g.bN, o = k - j * g.bN;
-      idx = (long)o * g.ldb + (long)j * g.bC + n;
-      break;
-    }
-    default: {  // B_IM2COL_T
-      const int L = g.bN, C = g.bC;
-      const int b = k / L, l = k - b * L, j = n / C, c = n - j * C;
-      const int ls = l + j - 1;
-      if (ls < 0 || ls >= L) return 0.f;
-      idx = ((long)b * L + ls) * C + c;
-    }
+// out[c][r] = src[r][c] (r < R, c < C, row stride lds), zero padded; out is [Cp][Rp]
+__global__ void k_transpose(const bf16* __restrict__ src, int R, int C, long lds, bf16* __restrict__ out, int Rp,
+                            int Cp) {
+  __shared__ bf16 tile[32][33];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int r = r0 + q, c = c0 + threadIdx.x;
+    tile[q][threadIdx.x] = (r < R && c < C) ? src[(long)r * lds + c] : __float2bfloat16(0.f);
   }
-  return g.b_f32 ? ldf<float>(g.Bp, idx) : __bfloat162float(((const bf16*)g.Bp)[idx]);
-}
-
-constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
-
-__device__ __forceinline__ uint32_t pack2(const bf16* p) { return *(const uint32_t*)p; }
-
-__global__ void __launch_bounds__(128) k_gemm(GemmArgs g) {
-  __shared__ __align__(16) bf16 As[BM][BK + PAD];
-  __shared__ __align__(16) bf16 Bs[BN][BK + PAD];
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int gq = lane >> 2, tq = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
-    for (int e = tid; e < BM * BK; e += 128) {
-      const int r = e / BK, kk = e % BK;
-      As[r][kk] = __float2bfloat16(load_a(g, m0 + r, k0 + kk));
-      Bs[r][kk] = __float2bfloat16(load_b(g, n0 + r, k0 + kk));
-    }
-    __syncthreads();
-#pragma unroll
-    for (int ks = 0; ks < BK; ks += 16) {
-      uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const int r = wm + a * 16 + gq;
-        af[a][0] = pack2(&As[r][ks + tq * 2]);
-        af[a][1] = pack2(&As[r + 8][ks + tq * 2]);
-        af[a][2] = pack2(&As[r][ks + tq * 2 + 8]);
-        af[a][3] = pack2(&As[r + 8][ks + tq * 2 + 8]);
-      }
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int c = wn + b * 8 + gq;
-        bfr[b][0] = pack2(&Bs[c][ks + tq * 2]);
-        bfr[b][1] = pack2(&Bs[c][ks + tq * 2 + 8]);
-      }
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-              "{%8,%9}, {%0,%1,%2,%3};"
-              : "+f"(acc[a][b][0]), "+f"(acc[a][b][1]), "+f"(acc[a][b][2]), "+f"(acc[a][b][3])
-              : "r"(af[a][0]), "r"(af[a][1]), "r"(af[a][2]), "r"(af[a][3]), "r"(bfr[b][0]),
-                "r"(bfr[b][1]));
-    }
-    __syncthreads();
+  __syncthreads();
+  for (int q = threadIdx.y; q < 32; q += blockDim.y) {
+    const int c = c0 + q, r = r0 + threadIdx.x;
+    if (c < Cp && r < Rp) out[(long)c * Rp + r] = tile[threadIdx.x][q];
   }
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int m = m0 + wm + a * 16 + gq + h * 8;
-          const int n = n0 + wn + b * 8 + tq * 2 + e;
-          if (m >= g.M || n >= g.N) continue;
-          float v = acc[a][b][h * 2 + e] + (g.bias ? g.bias[n] : 0.f);
-          const long o = (long)m * g.N + n;
-          if (g.pre_f32) g.pre_f32[o] = v;
-          if (g.gelu) v = gelu_f(v);
-          if (g.out_f32) g.out_f32[o] = g.accumulate ? g.out_f32[o] + v : v;
-          if (g.out_bf16) g.out_bf16[o] = __float2bfloat16(v);
-        }
 }
 
-void gemm(const GemmArgs& g, cudaStream_t st) {
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
-  k_gemm<<<grid, 128, 0, st>>>(g);
+// padded copy: out[r][c] = src[r][c] for r < R, c < C, else 0; out is [Rp][Cp]
+__global__ void k_pad(const bf16* __restrict__ src, int R, int C, bf16* __restrict__ out, int Rp, int Cp) {
+  const long n = (long)Rp * Cp;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / Cp), c = (int)(i - (long)r * Cp);
+    out[i] = (r < R && c < C) ? src[(long)r * C + c] : __float2bfloat16(0.f);
+  }
 }
 
-GemmArgs gemm_args(int M, int N, int K) {
-  GemmArgs g;
-  std::memset(&g, 0, sizeof g);
-  g.M = M;
-  g.N = N;
-  g.K = K;
-  return g;
+// weights of the input-gradient product: out[c][j*Cout + o] = W[o][j*Cin + c]; out is [Cinp][Kp]
+__global__ void k_wshift(const bf16* __restrict__ W, int Cout, int Cin, bf16* __restrict__ out, int Cinp, int Kp) {
+  const long n = (long)Cinp * Kp;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(i / Kp), k = (int)(i - (long)c * Kp);
+    bf16 v = __float2bfloat16(0.f);
+    if (c < Cin && k < 3 * Cout) {
+      const int j = k / Cout, o = k - j * Cout;
+      v = W[(long)o * 3 * Cin + (long)j * Cin + c];
+    }
+    out[i] = v;
+  }
 }
 
 // ------------------------------------------------------------------ small kernels
@@ -210,13 +115,21 @@ __global__ void k_gelu_back(const float* __restrict__ dy, const float* __restric
   }
 }
 
-// column sums (bias gradients): out[n] = sum_m x[m][n]
-__global__ void k_colsum(const float* __restrict__ x, int M, int N, float* __restrict__ out) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
+// column sums (bias gradients): out[n] = sum_m x[m][n]; block (32 columns x
+// 32 row groups), partial sums reduced in shared memory
+__global__ void __launch_bounds__(1024) k_colsum(const float* __restrict__ x, int M, int N, float* __restrict__ out) {
+  __shared__ float part[32][33];
+  const int n = blockIdx.x * 32 + threadIdx.x;
   float s = 0.f;
-  for (int m = 0; m < M; ++m) s += x[(long)m * N + n];
-  out[n] = s;
+  if (n < N)
+    for (int m = threadIdx.y; m < M; m += 32) s += x[(long)m * N + n];
+  part[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && n < N) {
+    float t = 0.f;
+    for (int q = 0; q < 32; ++q) t += part[q][threadIdx.x];
+    out[n] = t;
+  }
 }
 
 // mean over l of h2 (bf16 -> f32): pooled[b][c]
@@ -318,6 +231,12 @@ struct opf_net {
   int Bcap = 0;
   // activations / workspace for batch capacity Bcap
   bf16 *xb = nullptr, *h1 = nullptr, *h2 = nullptr, *dz = nullptr, *dz2 = nullptr;
+  // GEMM operands (row-major, K contiguous, zero padded): im2col rows of the
+  // three layer inputs, their transposes, transposed / shifted output
+  // gradients, padded and shifted weights
+  bf16 *col[3] = {nullptr, nullptr, nullptr}, *colT = nullptr, *dzT = nullptr, *dzcol = nullptr;
+  bf16 *wp[3] = {nullptr, nullptr, nullptr}, *ws[2] = {nullptr, nullptr};
+  int* err = nullptr;
   float *pre1 = nullptr, *pre2 = nullptr, *y = nullptr, *dy = nullptr, *dh = nullptr;
   float *pooled = nullptr, *z = nullptr, *dzh = nullptr, *dpooled = nullptr;
   double* sums = nullptr;
@@ -342,7 +261,16 @@ int net_reserve(opf_net* n, int B) {
   };
   fr(n->xb), fr(n->h1), fr(n->h2), fr(n->dz), fr(n->dz2), fr(n->pre1), fr(n->pre2), fr(n->y);
   fr(n->dy), fr(n->dh), fr(n->pooled), fr(n->z), fr(n->dzh), fr(n->dpooled), fr(n->sums);
+  for (int i = 0; i < 3; ++i) fr(n->col[i]);
+  fr(n->colT), fr(n->dzT), fr(n->dzcol);
   const long BL = (long)B * n->L, W = std::max(n->H, n->Cin);
+  const long BLp = pad128(BL), K1 = pad64(3L * n->Cin), K2 = pad64(3L * n->H);
+  NCU(cudaMalloc(&n->col[0], BLp * K1 * sizeof(bf16)));
+  NCU(cudaMalloc(&n->col[1], BLp * K2 * sizeof(bf16)));
+  NCU(cudaMalloc(&n->col[2], BLp * K2 * sizeof(bf16)));
+  NCU(cudaMalloc(&n->colT, pad128(3L * W) * BLp * sizeof(bf16)));
+  NCU(cudaMalloc(&n->dzT, pad128(W) * BLp * sizeof(bf16)));
+  NCU(cudaMalloc(&n->dzcol, BLp * pad64(3L * W) * sizeof(bf16)));
   NCU(cudaMalloc(&n->xb, BL * n->Cin * sizeof(bf16)));
   NCU(cudaMalloc(&n->h1, BL * n->H * sizeof(bf16)));
   NCU(cudaMalloc(&n->h2, BL * n->H * sizeof(bf16)));
@@ -366,59 +294,93 @@ float* Pf(opf_net* n, int i) { return n->P + n->off[i]; }
 float* Gf(opf_net* n, int i) { return n->G + n->off[i]; }
 bf16* Pbf(opf_net* n, int i) { return n->Pb + n->off[i]; }
 
+// C = A B^T on padded operands with the given epilogue
+int gemm(opf_net* n, const bf16* A, const bf16* Bm, int M, int N, int Kp, const opf::TcEpilogue& e) {
+  return opf::tc_gemm(A, Bm, M, N, (int)pad128(M), (int)pad128(N), Kp, e, n->err, n->st);
+}
+
+opf::TcEpilogue epi(long ldo) {
+  opf::TcEpilogue e;
+  std::memset(&e, 0, sizeof e);
+  e.ldo = ldo;
+  return e;
+}
+
+// padded copies of the weight matrices (after every parameter change)
+void prepare_weights(opf_net* n) {
+  const int Ci = n->Cin, H = n->H;
+  const int rows[3] = {H, H, Ci}, cols[3] = {3 * Ci, 3 * H, 3 * H};
+  for (int i = 0; i < 3; ++i) {
+    const long Rp = pad128(rows[i]), Cp = pad64(cols[i]);
+    k_pad<<<gs(Rp * Cp), 256, 0, n->st>>>(Pbf(n, 2 * i), rows[i], cols[i], n->wp[i], (int)Rp, (int)Cp);
+  }
+  // input-gradient weights of layers 3 (Cout = Cin, input H) and 2 (Cout = H, input H)
+  k_wshift<<<gs(pad128(H) * pad64(3L * Ci)), 256, 0, n->st>>>(Pbf(n, 4), Ci, H, n->ws[1], (int)pad128(H),
+                                                               (int)pad64(3L * Ci));
+  k_wshift<<<gs(pad128(H) * pad64(3L * H)), 256, 0, n->st>>>(Pbf(n, 2), H, H, n->ws[0], (int)pad128(H),
+                                                              (int)pad64(3L * H));
+}
+
 // forward for B samples whose features are at x (f32 [B][L][Cin])
 int net_forward(opf_net* n, const float* x, int B) {
   const int L = n->L, Ci = n->Cin, H = n->H, O = n->O;
-  const long BL = (long)B * L;
+  const long BL = (long)B * L, BLp = pad128(BL), K1 = pad64(3L * Ci), K2 = pad64(3L * H);
   k_to_bf16<<<gs(BL * Ci), 256, 0, n->st>>>(x, n->xb, BL * Ci);
-  GemmArgs g = gemm_args((int)BL, H, 3 * Ci);  // layer 1
-  g.A = n->xb, g.a_mode = A_IM2COL, g.L = L, g.C = Ci;
-  g.Bp = Pbf(n, 0), g.b_mode = B_ROWMAJOR, g.ldb = 3 * Ci;
-  g.bias = Pf(n, 1), g.gelu = 1, g.pre_f32 = n->pre1, g.out_bf16 = n->h1;
-  gemm(g, n->st);
-  g = gemm_args((int)BL, H, 3 * H);  // layer 2
-  g.A = n->h1, g.a_mode = A_IM2COL, g.L = L, g.C = H;
-  g.Bp = Pbf(n, 2), g.b_mode = B_ROWMAJOR, g.ldb = 3 * H;
-  g.bias = Pf(n, 3), g.gelu = 1, g.pre_f32 = n->pre2, g.out_bf16 = n->h2;
-  gemm(g, n->st);
-  g = gemm_args((int)BL, Ci, 3 * H);  // layer 3 (linear)
-  g.A = n->h2, g.a_mode = A_IM2COL, g.L = L, g.C = H;
-  g.Bp = Pbf(n, 4), g.b_mode = B_ROWMAJOR, g.ldb = 3 * H;
-  g.bias = Pf(n, 5), g.out_f32 = n->y;
-  gemm(g, n->st);
+  int rc;
+  // layer 1: h1 = gelu(col(x) W1^T + b1)
+  k_im2col<<<gs(BLp * K1), 256, 0, n->st>>>(n->xb, L, Ci, (int)BL, 0, n->col[0], (int)BLp, (int)K1);
+  opf::TcEpilogue e = epi(H);
+  e.bias = Pf(n, 1), e.gelu = 1, e.pre_f32 = n->pre1, e.out_bf16 = n->h1;
+  if ((rc = gemm(n, n->col[0], n->wp[0], (int)BL, H, (int)K1, e))) return rc;
+  // layer 2
+  k_im2col<<<gs(BLp * K2), 256, 0, n->st>>>(n->h1, L, H, (int)BL, 0, n->col[1], (int)BLp, (int)K2);
+  e = epi(H);
+  e.bias = Pf(n, 3), e.gelu = 1, e.pre_f32 = n->pre2, e.out_bf16 = n->h2;
+  if ((rc = gemm(n, n->col[1], n->wp[1], (int)BL, H, (int)K2, e))) return rc;
+  // layer 3 (linear)
+  k_im2col<<<gs(BLp * K2), 256, 0, n->st>>>(n->h2, L, H, (int)BL, 0, n->col[2], (int)BLp, (int)K2);
+  e = epi(Ci);
+  e.bias = Pf(n, 5), e.out_f32 = n->y;
+  if ((rc = gemm(n, n->col[2], n->wp[2], (int)BL, Ci, (int)K2, e))) return rc;
   k_pool<<<(B * H + 255) / 256, 256, 0, n->st>>>(n->h2, B, L, H, n->pooled);
   k_head<<<(B * O + 255) / 256, 256, 0, n->st>>>(n->pooled, Pf(n, 6), Pf(n, 7), B, H, O, n->z);
   return OPF_OK;
 }
 
-// gradient of one width-3 conv layer given dZ (bf16 [BL][Cout], f32 copy dZf):
-//   dW[o][j*Cin + c] = sum_m dZ[m][o] xcol[m][j*Cin + c]     (reduction over m)
-//   db[o] = sum_m dZ[m][o]
-//   dx[(b,l)][c] = sum_{j,o} dZ[(b, l + 1 - j)][o] W[o][j*Cin + c]
-void conv_backward(opf_net* n, int B, const bf16* x, int Cin, int Cout, const bf16* dZ, const float* dZf,
-                   const bf16* Wb, float* dW, float* db, float* dx) {
+// gradient of one width-3 conv layer (input width Cin, output Cout) given
+// dZ (bf16 [BL][Cout], f32 copy dZf) and the layer's im2col rows col:
+//   dW[o][k] = sum_m dZ[m][o] col[m][k]        (operands dZ^T, col^T; K = BL)
+//   db[o]    = sum_m dZ[m][o]
+//   dx[m][c] = sum_{j,o} dZ[(b, l + 1 - j)][o] W[o][j*Cin + c]   (operands col_rev(dZ), ws)
+int conv_backward(opf_net* n, int B, const bf16* col, int Kc, int Cin, int Cout, const bf16* dZ, const float* dZf,
+                  const bf16* wsh, float* dW, float* db, float* dx) {
   const int L = n->L;
-  const long BL = (long)B * L;
-  GemmArgs w = gemm_args(Cout, 3 * Cin, (int)BL);
-  w.A = dZ, w.a_mode = A_COLMAJOR, w.lda = Cout;
-  w.Bp = x, w.b_mode = B_IM2COL_T, w.bN = L, w.bC = Cin;
-  w.out_f32 = dW;
-  gemm(w, n->st);
-  k_colsum<<<(Cout + 255) / 256, 256, 0, n->st>>>(dZf, (int)BL, Cout, db);
+  const long BL = (long)B * L, BLp = pad128(BL);
+  int rc;
+  dim3 tb(32, 8);
+  k_transpose<<<dim3((unsigned)(BLp / 32), (unsigned)(pad128(Cout) / 32)), tb, 0, n->st>>>(
+      dZ, (int)BL, Cout, Cout, n->dzT, (int)BLp, (int)pad128(Cout));
+  k_transpose<<<dim3((unsigned)(BLp / 32), (unsigned)(pad128(3L * Cin) / 32)), tb, 0, n->st>>>(
+      col, (int)BL, 3 * Cin, Kc, n->colT, (int)BLp, (int)pad128(3L * Cin));
+  opf::TcEpilogue e = epi(3L * Cin);
+  e.out_f32 = dW;
+  if ((rc = gemm(n, n->dzT, n->colT, Cout, 3 * Cin, (int)BLp, e))) return rc;
+  k_colsum<<<(Cout + 31) / 32, dim3(32, 32), 0, n->st>>>(dZf, (int)BL, Cout, db);
   if (dx) {
-    GemmArgs v = gemm_args((int)BL, Cin, 3 * Cout);
-    v.A = dZ, v.a_mode = A_IM2COL_REV, v.L = L, v.C = Cout;
-    v.Bp = Wb, v.b_mode = B_WT_SHIFT, v.ldb = 3 * Cin, v.bN = Cout, v.bC = Cin;
-    v.out_f32 = dx;
-    gemm(v, n->st);
+    const long Kd = pad64(3L * Cout);
+    k_im2col<<<gs(BLp * Kd), 256, 0, n->st>>>(dZ, L, Cout, (int)BL, 1, n->dzcol, (int)BLp, (int)Kd);
+    e = epi(Cin);
+    e.out_f32 = dx;
+    if ((rc = gemm(n, n->dzcol, wsh, (int)BL, Cin, (int)Kd, e))) return rc;
   }
+  return OPF_OK;
 }
 
 // loss and all parameter gradients into n->G for targets ty [B][L][Cin], tz [B][O]
 int net_gradients(opf_net* n, const float* x, const float* ty, const float* tz, int B, float lambda,
                   double* loss) {
   const int L = n->L, Ci = n->Cin, H = n->H, O = n->O;
-  const long BL = (long)B * L;
+  const long BL = (long)B * L, K1 = pad64(3L * Ci), K2 = pad64(3L * H);
   int rc = net_forward(n, x, B);
   if (rc) return rc;
   NCU(cudaMemsetAsync(n->sums, 0, 2 * sizeof(double), n->st));
@@ -427,7 +389,8 @@ int net_gradients(opf_net* n, const float* x, const float* ty, const float* tz, 
   k_mse<<<1, 256, 0, n->st>>>(n->z, tz, (long)B * O, lambda / (float)(B * O), n->dzh, n->sums + 1);
   // layer 3 (linear): dZ3 = dy
   k_to_bf16<<<gs(BL * Ci), 256, 0, n->st>>>(n->dy, n->dz, BL * Ci);
-  conv_backward(n, B, n->h2, H, Ci, n->dz, n->dy, Pbf(n, 4), Gf(n, 4), Gf(n, 5), n->dh);
+  if ((rc = conv_backward(n, B, n->col[2], (int)K2, H, Ci, n->dz, n->dy, n->ws[1], Gf(n, 4), Gf(n, 5), n->dh)))
+    return rc;
   // head: pooled mean of h2
   const int hb = (int)std::max<long>((long)O * H, (long)B * H);
   k_head_back<<<(hb + 255) / 256, 256, 0, n->st>>>(n->dzh, n->pooled, Pf(n, 6), B, H, O, Gf(n, 6), Gf(n, 7),
@@ -435,10 +398,12 @@ int net_gradients(opf_net* n, const float* x, const float* ty, const float* tz, 
   k_unpool_add<<<gs(BL * H), 256, 0, n->st>>>(n->dpooled, B, L, H, n->dh);
   // layer 2
   k_gelu_back<<<gs(BL * H), 256, 0, n->st>>>(n->dh, n->pre2, n->dz, n->dy, BL * H);
-  conv_backward(n, B, n->h1, H, H, n->dz, n->dy, Pbf(n, 2), Gf(n, 2), Gf(n, 3), n->dh);
+  if ((rc = conv_backward(n, B, n->col[1], (int)K2, H, H, n->dz, n->dy, n->ws[0], Gf(n, 2), Gf(n, 3), n->dh)))
+    return rc;
   // layer 1 (input gradient not needed)
   k_gelu_back<<<gs(BL * H), 256, 0, n->st>>>(n->dh, n->pre1, n->dz2, n->dy, BL * H);
-  conv_backward(n, B, n->xb, Ci, H, n->dz2, n->dy, Pbf(n, 0), Gf(n, 0), Gf(n, 1), nullptr);
+  if ((rc = conv_backward(n, B, n->col[0], (int)K1, Ci, H, n->dz2, n->dy, nullptr, Gf(n, 0), Gf(n, 1), nullptr)))
+    return rc;
   if (loss) {
     double h[2];
     NCU(cudaMemcpyAsync(h, n->sums, sizeof h, cudaMemcpyDeviceToHost, n->st));
@@ -451,6 +416,7 @@ int net_gradients(opf_net* n, const float* x, const float* ty, const float* tz, 
 
 void refresh_bf16(opf_net* n) {
   k_to_bf16<<<gs(n->total), 256, 0, n->st>>>(n->P, n->Pb, n->total);
+  prepare_weights(n);
 }
 
 }  // namespace
@@ -495,7 +461,13 @@ opf_net_t* opf_net_create(int cin, int hidden, int L, int nout, unsigned long lo
   if (cudaStreamCreateWithFlags(&n->st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMalloc(&n->P, t * sizeof(float)) != cudaSuccess || cudaMalloc(&n->G, t * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&n->M1, t * sizeof(float)) != cudaSuccess || cudaMalloc(&n->M2, t * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&n->Pb, t * sizeof(bf16)) != cudaSuccess) {
+      cudaMalloc(&n->Pb, t * sizeof(bf16)) != cudaSuccess ||
+      cudaMalloc(&n->wp[0], pad128(hidden) * pad64(3L * cin) * sizeof(bf16)) != cudaSuccess ||
+      cudaMalloc(&n->wp[1], pad128(hidden) * pad64(3L * hidden) * sizeof(bf16)) != cudaSuccess ||
+      cudaMalloc(&n->wp[2], pad128(cin) * pad64(3L * hidden) * sizeof(bf16)) != cudaSuccess ||
+      cudaMalloc(&n->ws[0], pad128(hidden) * pad64(3L * hidden) * sizeof(bf16)) != cudaSuccess ||
+      cudaMalloc(&n->ws[1], pad128(hidden) * pad64(3L * cin) * sizeof(bf16)) != cudaSuccess ||
+      cudaMalloc(&n->err, sizeof(int)) != cudaSuccess) {
     opf::set_last_error("opf_net_create: device allocation failed");
     opf_net_destroy(n);
     return nullptr;
@@ -504,6 +476,7 @@ opf_net_t* opf_net_create(int cin, int hidden, int L, int nout, unsigned long lo
   cudaMemset(n->G, 0, t * sizeof(float));
   cudaMemset(n->M1, 0, t * sizeof(float));
   cudaMemset(n->M2, 0, t * sizeof(float));
+  cudaMemset(n->err, 0, sizeof(int));
   refresh_bf16(n);
   if (cudaStreamSynchronize(n->st) != cudaSuccess) {
     opf::set_last_error("opf_net_create: initialisation failed");
@@ -519,7 +492,9 @@ void opf_net_destroy(opf_net_t* n) {
   for (void* p : {(void*)n->P, (void*)n->G, (void*)n->M1, (void*)n->M2, (void*)n->Pb, (void*)n->xb,
                   (void*)n->h1, (void*)n->h2, (void*)n->dz, (void*)n->dz2, (void*)n->pre1, (void*)n->pre2,
                   (void*)n->y, (void*)n->dy, (void*)n->dh, (void*)n->pooled, (void*)n->z, (void*)n->dzh,
-                  (void*)n->dpooled, (void*)n->sums})
+                  (void*)n->dpooled, (void*)n->sums, (void*)n->col[0], (void*)n->col[1], (void*)n->col[2],
+                  (void*)n->colT, (void*)n->dzT, (void*)n->dzcol, (void*)n->wp[0], (void*)n->wp[1],
+                  (void*)n->wp[2], (void*)n->ws[0], (void*)n->ws[1], (void*)n->err})
     if (p) cudaFree(p);
   if (n->st) cudaStreamDestroy(n->st);
   delete n;
@@ -558,6 +533,18 @@ int opf_net_set_params(opf_net_t* n, const float* host) {
   return OPF_OK;
 }
 
+// a tensor-core GEMM whose bounded wait ran out leaves the flag set
+static int net_check(opf_net_t* n) {
+  int h = 0;
+  NCU(cudaMemcpy(&h, n->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    cudaMemset(n->err, 0, sizeof(int));
+    opf::set_last_error("proposal network: a tensor-core GEMM timed out waiting for its operands");
+    return OPF_ETIMEOUT;
+  }
+  return OPF_OK;
+}
+
 int opf_net_forward(opf_net_t* n, const float* d_x, int B, float* d_y, float* d_z) {
   if (!n || !d_x || B < 1) return OPF_EINVAL;
   int rc = net_reserve(n, B);
@@ -569,7 +556,7 @@ int opf_net_forward(opf_net_t* n, const float* d_x, int B, float* d_y, float* d_
   if (d_z) NCU(cudaMemcpyAsync(d_z, n->z, (long)B * n->O * sizeof(float), cudaMemcpyDeviceToDevice, n->st));
   NCU(cudaStreamSynchronize(n->st));
   NCU(cudaGetLastError());
-  return OPF_OK;
+  return net_check(n);
 }
 
 int opf_net_gradients(opf_net_t* n, const float* d_x, const float* d_ty, const float* d_tz, int B,
@@ -580,7 +567,7 @@ int opf_net_gradients(opf_net_t* n, const float* d_x, const float* d_ty, const f
   rc = net_gradients(n, d_x, d_ty, d_tz, B, lambda, loss);
   if (rc) return rc;
   NCU(cudaStreamSynchronize(n->st));
-  return OPF_OK;
+  return net_check(n);
 }
 
 int opf_net_train_step(opf_net_t* n, const float* d_x, const float* d_ty, const float* d_tz, int B,
@@ -591,6 +578,7 @@ int opf_net_train_step(opf_net_t* n, const float* d_x, const float* d_ty, const 
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.f - std::pow(b1, (float)n->step), c2 = 1.f - std::pow(b2, (float)n->step);
   k_adam<<<gs(n->total), 256, 0, n->st>>>(n->P, n->G, n->M1, n->M2, n->total, lr, b1, b2, c1, c2, 1e-8f, n->Pb);
+  prepare_weights(n);
   NCU(cudaStreamSynchronize(n->st));
   NCU(cudaGetLastError());
   return OPF_OK;

@@ -1,0 +1,281 @@
+// Dense BF16 GEMM on the 5th-generation tensor cores (tcgen05) for the
+// proposal network: C[m][n] = sum_k A[m][k] B[n][k] with FP32 accumulation in
+// tensor memory (TMEM) and a fused epilogue (bias, GELU, FP32 / BF16 outputs).
+//
+// Operands are row-major BF16 with K contiguous ("K-major"), zero padded to
+// Mp, Np (multiples of 128) and Kp (a multiple of 64), so every TMA box lies
+// inside its tensor.  One CTA computes a 128 x 128 tile:
+//   warp 0, one thread: TMA producer -- 128 x 64 tiles of A and B, 128-byte
+//     swizzle, into a 4-stage shared-memory ring (mbarrier with tx count);
+//   warp 1, one thread: issues tcgen05.mma (M=128, N=128, K=16) per 16-wide
+//     K slice and commits each stage back to the producer;
+//   all 4 warps: read the accumulator with tcgen05.ld (warp w owns TMEM
+//     lanes 32w..32w+31 = tile rows) and apply the epilogue.
+// Every mbarrier wait is bounded (about 2 s of wall time); on a timeout the
+// kernel records an error flag, still frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "opf_internal.h"
+
+namespace opf {
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 4;
+constexpr int kTileBytes = kBM * kBK * 2;  // A and B tiles are both 128 rows x 128 bytes
+constexpr unsigned kTmemCols = 128;         // FP32 accumulator: 128 lanes x 128 columns
+constexpr unsigned long long kWaitNs = 2000000000ull;
+// instruction descriptor (kind::f16): D = F32 (bits 4-5), A = B = BF16 (bits
+// 7-9, 10-12), both K-major (bits 15, 16 = 0), N >> 3 (bits 17-22), M >> 4 (bits 24-28)
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+constexpr size_t kSmemBytes = 1024 + 2 * kStages * kTileBytes + 256;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Wait for the phase of the given parity to complete; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = now_ns();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (now_ns() - t0 > kWaitNs) return false;
+    __nanosleep(64);
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(dst),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with the
+// 128-byte swizzle: 8-row x 128-byte atoms, 1024 bytes apart (stride offset).
+__device__ __forceinline__ unsigned long long sw128_desc(uint32_t saddr) {
+  unsigned long long d = (unsigned long long)((saddr & 0x3FFFFu) >> 4);
+  d |= 1ull << 16;                  // leading offset (unused for swizzled K-major)
+  d |= (unsigned long long)(1024 >> 4) << 32;
+  d |= 1ull << 46;                  // descriptor version
+  d |= 2ull << 61;                  // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, unsigned long long a, unsigned long long b,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N, int Kp,
+              TcEpilogue e, int* err) {
+  extern __shared__ unsigned char sraw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)sraw + 1023) & ~(uintptr_t)1023);  // 128B swizzle: 1 KB aligned
+  unsigned char* sA = sm;
+  unsigned char* sB = sm + kStages * kTileBytes;
+  uint64_t* bars = (uint64_t*)(sB + kStages * kTileBytes);  // full[kStages], empty[kStages], done
+  uint32_t* tmem_holder = (uint32_t*)(bars + 2 * kStages + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  const int nk = Kp / kBK;
+  auto full = [&](int s) { return smem_u32(bars + s); };
+  auto empty = [&](int s) { return smem_u32(bars + kStages + s); };
+  const uint32_t done = smem_u32(bars + 2 * kStages);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {  // whole warp: allocate the accumulator columns
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  bool ok = true;
+
+  if (warp == 0 && lane == 0) {  // TMA producer
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kStages;
+      if (kb >= kStages && !mbar_wait(empty(s), ((kb / kStages) - 1) & 1)) {
+        ok = false;
+        break;
+      }
+      mbar_expect_tx(full(s), 2 * kTileBytes);
+      tma_load_2d(smem_u32(sA + s * kTileBytes), &ta, kb * kBK, m0, full(s));
+      tma_load_2d(smem_u32(sB + s * kTileBytes), &tb, kb * kBK, n0, full(s));
+      ++issued;
+    }
+    if (!ok)  // let the copies already issued land before the CTA can exit
+      for (int kb = issued - 1; kb >= 0 && kb >= issued - kStages; --kb)
+        mbar_wait(full(kb % kStages), (kb / kStages) & 1);
+  } else if (warp == 1 && lane == 0) {  // MMA issuer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kStages;
+      if (!mbar_wait(full(s), (kb / kStages) & 1)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sA + s * kTileBytes), b0 = smem_u32(sB + s * kTileBytes);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 16; ++kk)  // 16 BF16 = 32 bytes per K slice
+        umma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), (kb | kk) != 0);
+      umma_commit(empty(s));
+    }
+    umma_commit(done);  // arrives once every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // epilogue: TMEM lane = tile row (warp w: rows 32w..32w+31), 32 columns per load
+  if (!mbar_wait(done, 0)) ok = false;
+  tc_fence_after();
+  const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+  for (int c0 = 0; c0 < kBN; c0 += 32) {
+    uint32_t v[32];
+    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    if (row < M) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int n = n0 + c0 + j;
+        if (n >= N) break;
+        float x = __uint_as_float(v[j]) + (e.bias ? e.bias[n] : 0.f);
+        const long o = (long)row * e.ldo + n;
+        if (e.pre_f32) e.pre_f32[o] = x;
+        if (e.gelu) x = gelu_f(x);
+        if (e.out_f32) e.out_f32[o] = e.accumulate ? e.out_f32[o] + x : x;
+        if (e.out_bf16) ((bf16*)e.out_bf16)[o] = __float2bfloat16(x);
+      }
+    }
+  }
+  if (!ok) atomicExch(err, 1);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  }
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiled)p;
+  });
+  return fn;
+}
+
+// 2-D map of a row-major BF16 matrix [rows][Kp]: boxes of 128 rows x 64 columns
+bool make_map(CUtensorMap* m, const void* base, int rows, int Kp) {
+  EncodeTiled enc = encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+int tc_gemm(const void* A, const void* B, int M, int N, int Mp, int Np, int Kp, const TcEpilogue& e, int* d_err,
+            cudaStream_t st) {
+  if (M < 1 || N < 1 || M > Mp || N > Np || Mp % kBM || Np % kBN || Kp < kBK || Kp % kBK ||
+      ((uintptr_t)A & 15) || ((uintptr_t)B & 15)) {
+    set_last_error("tc_gemm: operand shapes must be padded to 128 x 64 multiples on 16-byte boundaries");
+    return OPF_EINVAL;
+  }
+  static std::once_flag once;
+  static bool attr_ok = false;
+  std::call_once(once, [] {
+    attr_ok = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) ==
+              cudaSuccess;
+  });
+  CUtensorMap ta, tb;
+  if (!attr_ok || !make_map(&ta, A, Mp, Kp) || !make_map(&tb, B, Np, Kp)) {
+    set_last_error("tc_gemm: tensor map or kernel attribute setup failed");
+    return OPF_ECUDA;
+  }
+  dim3 grid(Np / kBN, Mp / kBM);
+  k_tc_gemm<<<grid, 128, kSmemBytes, st>>>(ta, tb, M, N, Kp, e, d_err);
+  const cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) {
+    set_last_error(std::string("tc_gemm launch: ") + cudaGetErrorString(err));
+    return OPF_ECUDA;
+  }
+  return OPF_OK;
+}
+
+}  // namespace opf
