@@ -82,6 +82,13 @@ def kernel_costs(w):
     }
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the current
+# kernels on the medium workload (one ncu capture each, summarised in the
+# named profile), keyed by (kernel, precision of the step)
+PROFILED_DRAM_BYTES = {("solve", 0): 22.5e6, ("solve", 1): 22.5e6}
+PROFILE_FILES = {"solve": "profiles/k_solve_medium.md"}
+
+
 # which arithmetic bounds each kernel: FP64 for the solve and the curl (both
 # precisions), the transforms follow the precision
 def kernel_peak(name, precision):
@@ -446,6 +453,48 @@ def run_learned(args):
     print(json.dumps(line, default=float), flush=True)
 
 
+def run_net(args):
+    """Proposal-network training step (the only dense contraction): B=64
+    snapshots of 720 channels over L=48 radial points, hidden 384 (2.10 M
+    parameters), forward + backward + Adam on the tensor cores.  Reports
+    the step time and the GEMM throughput against the measured BF16 peak."""
+    import torch
+
+    from paper_1705_03838_gb300 import build as _build, opf
+
+    torch.cuda.set_device(0)
+    _build.build()
+    opf.lib()
+    cin, hid, L, nout, B = 720, 384, 48, 3, 64
+    net = opf.opf_net_create(cin, hid, L, nout, seed=1)
+    g = torch.Generator().manual_seed(0)
+    x = torch.randn(B, L, cin, generator=g).cuda()
+    ty = 0.1 * torch.randn(B, L, cin, generator=g).cuda()
+    tz = torch.randn(B, nout, generator=g).cuda()
+    step = lambda: opf.opf_net_train_step(net, x.data_ptr(), ty.data_ptr(), tz.data_ptr(), B, 1.0, 1e-4)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1000.0 / args.steps
+    F1, F2, F3 = (2.0 * B * L * 3 * cin * hid, 2.0 * B * L * 3 * hid * hid, 2.0 * B * L * 3 * hid * cin)
+    flops = 2 * F1 + 3 * F2 + 3 * F3  # forward, weight gradients, input gradients of layers 2 and 3
+    peaks, src = load_peaks()
+    line = {
+        "metric": "proposal-network training steps/s (BF16 tensor-core GEMMs, FP32 accumulate)",
+        "value": 1000.0 / ms, "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"net: B={B} L={L} channels={cin} hidden={hid} params={opf.opf_net_param_count(net)[0]}"},
+        "gemm_tflops_per_step": flops / (ms * 1e-3) / 1e12,
+        "bf16_peak_tflops": peaks.get("bf16_tflops"),
+        "bf16_peak_source": src,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args, w):
     import numpy as np
     import torch
@@ -556,8 +605,11 @@ def run_gpu(args, w):
         pk, src = kernel_peak(dom, precision)
         ach = costs[dom]["flops"] / (dom_ms * 1e-3) / 1e12
         tot = sum(x[0] for x in kt.values())
+        traffic = PROFILED_DRAM_BYTES.get((dom, precision))
         return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                "frac": ach / pk, "traffic": None, "peak_source": src, "launch_ms": dom_ms,
+                "frac": ach / pk, "traffic": traffic,
+                "traffic_source": PROFILE_FILES.get(dom) if traffic is not None else None,
+                "peak_source": src, "launch_ms": dom_ms,
                 "share": {k: v[0] / tot for k, v in kt.items()}}
 
     roof = roofline(ktimes, args.precision)
@@ -621,9 +673,10 @@ def main():
                     help="headline precision: 1 = mixed (default), 0 = FP64; both are timed")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="medium", choices=["medium", "ensemble", "large", "learned"],
+    ap.add_argument("--workload", default="medium", choices=["medium", "ensemble", "large", "learned", "net"],
                     help="medium: the default single-run line; ensemble: the batched workload; large: the "
-                         "CFL-controlled large run; learned: the learned Newton-Krylov proposal pipeline")
+                         "CFL-controlled large run; learned: the learned Newton-Krylov proposal pipeline; "
+                         "net: the proposal network's training step")
     ap.add_argument("--autotune", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -637,6 +690,8 @@ def main():
         run_large(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "net":
+        run_net(args)
     else:
         run_gpu(args, w)
 
