@@ -414,7 +414,7 @@ LEARNED = dict(N=48, K=24, M=16, m_p=2, alpha=1.25, dt=0.005, precision=1,
                Re_train=(2000.0, 2500.0), Re_test=2250.0, amp=(0.03, 0.12), B_train=56, B_val=6, B_test=8,
                seed=1705, warmup=20.0, n_snap=320, every=0.5, T_min=10.0, T_max=100.0, thresh=0.3,
                hidden=384, steps=3000, batch=64, lr=1e-3, lam=1.0, net_seed=5, eval_every=200,
-               nk_guesses=16, nk_T_max=20.0,
+               nk_guesses=12, nk_T_max=16.0,
                nk=dict(max_newton=2, max_krylov=12, max_hook=4, dt=0.005, tol=1e-10))
 
 
@@ -423,8 +423,8 @@ def run_learned(args):
     them for validation, at Re uniform in [2000, 2500]; 8 held out at Re = 2250)
     of N=48, |k|<24, m<16, m_p=2, 20,480 snapshots every 0.5 time units; the
     BF16 network trained by the library's own kernels; Newton-Krylov-hookstep
-    from the 16 best held-out recurrences with recurrence, learned and
-    learned-state guesses under the same budget."""
+    from the 12 best held-out recurrences with recurrence, learned,
+    learned-state and snapshot-with-mean-period guesses under the same budget."""
     import torch
 
     from paper_1705_03838_gb300 import build as _build, learned, opf
@@ -448,6 +448,7 @@ def run_learned(args):
         "config": {"workload": "learned proposals: N=48 |k|<24 m<16 m_p=2 alpha=1.25, Re in [2000,2500], "
                                "64 trajectories x 320 snapshots"},
         "recurrence_median_final": nk.get("recurrence", {}).get("median_final"),
+        "snapshot_mean_T_median_final": nk.get("snapshot_mean_T", {}).get("median_final"),
         "details": res,
     }
     print(json.dumps(line, default=float), flush=True)

@@ -141,6 +141,9 @@ void launch_nan_check(const double* x, long n, int* flag, cudaStream_t st);
 // aligned.  Epilogue per (m, n): x = C + bias[n]; pre_f32 = x; x = gelu(x)
 // if gelu; out_f32 = x (+= x if accumulate); out_bf16 = bf16(x); outputs
 // have row stride ldo.  d_err (device int) is set on a timed-out wait.
+// work (device, work_floats floats; may be null) lets plain FP32 outputs (no
+// bias, GELU or BF16 copy) split K across CTAs; the partial sums are added in
+// a fixed order, so results do not depend on scheduling.
 struct TcEpilogue {
   const float* bias;
   int gelu;
@@ -151,6 +154,6 @@ struct TcEpilogue {
   long ldo;
 };
 int tc_gemm(const void* A, const void* B, int M, int N, int Mp, int Np, int Kp, const TcEpilogue& e, int* d_err,
-            cudaStream_t st);
+            cudaStream_t st, float* work = nullptr, long work_floats = 0);
 
 }  // namespace opf

@@ -563,6 +563,7 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   }
 
   // ---- N_eff = wa N_a + wb N_b, and N+ + N- for the divergence
+#pragma unroll 9
   for (int e = tid; e < 2 * N * 9; e += NB) W1[e] = s.d1[e];
   for (int e = tid; e < N; e += NB) RI[e] = s.rinv[e];
 #pragma unroll 4
@@ -651,17 +652,17 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   for (int e = tid; e < (N - 1) * NT; e += NB) {
     const int c = e % NT, i = e / NT;
     const int part = c & 1, mi = (c >> 1) % T, f = (c >> 1) / T;
+    // rhs -= grad p:  (grad p)+- = d_r p -+ m~ p / r,  (grad p)_z = i ak p
     const double2 pp = P[i * T + mi];
-    double gp;
+    double& xv = X[i * NT + c];
     if (f < 2) {
       const double2 dp = S[i * T + mi];
-      const double q = mt * RI[i] * (part ? pp.y : pp.x);
-      gp = (part ? dp.y : dp.x) + (f == 0 ? -q : q);
+      const double mr = (f == 0 ? mt : -mt) * RI[i];
+      xv = fma(mr, part ? pp.y : pp.x, xv - (part ? dp.y : dp.x));
     } else {
       const double ak = d.alpha * (min(kk0 + mi, nk - 1) - (K - 1));
-      gp = part == 0 ? -ak * pp.y : ak * pp.x;
+      xv = part == 0 ? fma(ak, pp.y, xv) : fma(-ak, pp.x, xv);
     }
-    X[i * NT + c] -= gp;
   }
   __syncthreads();
 
@@ -776,15 +777,23 @@ static size_t solve_smem(int N, int T) {
 }
 
 // Chunk sizes keep every transform block within ~96 KB of shared memory (two
-// blocks per SM), then raise each kernel's dynamic shared-memory limit.
+// blocks per SM) and give each transform kernel at least two blocks per SM
+// (smaller chunks, same arithmetic per column).
 void choose_chunks(Dims* d) {
   const size_t budget = 96 * 1024, vb = sizeof(double2);
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long target = 2L * sms;
+  auto blocks = [&](int extent, int chunk, long rest) { return (long)((extent + chunk - 1) / chunk) * rest; };
   d->mcz = 8;
-  while (d->mcz > 1 && zsynth_smem(*d, d->mcz, vb) > budget) d->mcz /= 2;
+  while (d->mcz > 1 && (zsynth_smem(*d, d->mcz, vb) > budget || blocks(d->M, d->mcz, 6L * d->N * d->B) < target))
+    d->mcz /= 2;
   d->mca = 8;
-  while (d->mca > 1 && zanalysis_smem(*d, d->mca, vb) > budget) d->mca /= 2;
+  while (d->mca > 1 && (zanalysis_smem(*d, d->mca, vb) > budget || blocks(d->M, d->mca, (long)d->N * d->B) < target))
+    d->mca /= 2;
   d->zc = 4;
-  while (d->zc > 1 && product_smem(*d, d->zc, vb) > budget) d->zc /= 2;
+  while (d->zc > 1 && (product_smem(*d, d->zc, vb) > budget || blocks(d->nz, d->zc, (long)d->N * d->B) < target))
+    d->zc /= 2;
 }
 
 // The dynamic shared-memory limit is a per-kernel, process-wide attribute, so

@@ -237,6 +237,8 @@ struct opf_net {
   bf16 *col[3] = {nullptr, nullptr, nullptr}, *colT = nullptr, *dzT = nullptr, *dzcol = nullptr;
   bf16 *wp[3] = {nullptr, nullptr, nullptr}, *ws[2] = {nullptr, nullptr};
   int* err = nullptr;
+  float* gwork = nullptr;  // split-K partial sums of the weight-gradient GEMMs
+  long gwork_floats = 0;
   float *pre1 = nullptr, *pre2 = nullptr, *y = nullptr, *dy = nullptr, *dh = nullptr;
   float *pooled = nullptr, *z = nullptr, *dzh = nullptr, *dpooled = nullptr;
   double* sums = nullptr;
@@ -296,7 +298,8 @@ bf16* Pbf(opf_net* n, int i) { return n->Pb + n->off[i]; }
 
 // C = A B^T on padded operands with the given epilogue
 int gemm(opf_net* n, const bf16* A, const bf16* Bm, int M, int N, int Kp, const opf::TcEpilogue& e) {
-  return opf::tc_gemm(A, Bm, M, N, (int)pad128(M), (int)pad128(N), Kp, e, n->err, n->st);
+  return opf::tc_gemm(A, Bm, M, N, (int)pad128(M), (int)pad128(N), Kp, e, n->err, n->st, n->gwork,
+                      n->gwork_floats);
 }
 
 opf::TcEpilogue epi(long ldo) {
@@ -467,7 +470,9 @@ opf_net_t* opf_net_create(int cin, int hidden, int L, int nout, unsigned long lo
       cudaMalloc(&n->wp[2], pad128(cin) * pad64(3L * hidden) * sizeof(bf16)) != cudaSuccess ||
       cudaMalloc(&n->ws[0], pad128(hidden) * pad64(3L * hidden) * sizeof(bf16)) != cudaSuccess ||
       cudaMalloc(&n->ws[1], pad128(hidden) * pad64(3L * cin) * sizeof(bf16)) != cudaSuccess ||
-      cudaMalloc(&n->err, sizeof(int)) != cudaSuccess) {
+      cudaMalloc(&n->err, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&n->gwork, (n->gwork_floats = 8L * std::max(3L * hidden * std::max(cin, hidden), 1L)) *
+                                sizeof(float)) != cudaSuccess) {
     opf::set_last_error("opf_net_create: device allocation failed");
     opf_net_destroy(n);
     return nullptr;
@@ -494,7 +499,7 @@ void opf_net_destroy(opf_net_t* n) {
                   (void*)n->y, (void*)n->dy, (void*)n->dh, (void*)n->pooled, (void*)n->z, (void*)n->dzh,
                   (void*)n->dpooled, (void*)n->sums, (void*)n->col[0], (void*)n->col[1], (void*)n->col[2],
                   (void*)n->colT, (void*)n->dzT, (void*)n->dzcol, (void*)n->wp[0], (void*)n->wp[1],
-                  (void*)n->wp[2], (void*)n->ws[0], (void*)n->ws[1], (void*)n->err})
+                  (void*)n->wp[2], (void*)n->ws[0], (void*)n->ws[1], (void*)n->err, (void*)n->gwork})
     if (p) cudaFree(p);
   if (n->st) cudaStreamDestroy(n->st);
   delete n;

@@ -4,10 +4,14 @@
 //
 // Operands are row-major BF16 with K contiguous ("K-major"), zero padded to
 // Mp, Np (multiples of 128) and Kp (a multiple of 64), so every TMA box lies
-// inside its tensor.  One CTA computes a 128 x 128 tile:
-//   warp 0, one thread: TMA producer -- 128 x 64 tiles of A and B, 128-byte
-//     swizzle, into a 4-stage shared-memory ring (mbarrier with tx count);
-//   warp 1, one thread: issues tcgen05.mma (M=128, N=128, K=16) per 16-wide
+// inside its tensor.  One CTA computes a 128 x BN tile (BN = 128 or 64, the
+// narrower one when 128-wide tiles would leave SMs idle) over one K range
+// (split K: the ranges' partial sums go to separate slices that a second
+// kernel adds up in a fixed order):
+//   warp 0, one thread: TMA producer -- 128 x 64 (A) and BN x 64 (B) tiles,
+//     128-byte swizzle, into a 4-stage shared-memory ring (mbarrier with tx
+//     count);
+//   warp 1, one thread: issues tcgen05.mma (M=128, N=BN, K=16) per 16-wide
 //     K slice and commits each stage back to the producer;
 //   all 4 warps: read the accumulator with tcgen05.ld (warp w owns TMEM
 //     lanes 32w..32w+31 = tile rows) and apply the epilogue.
@@ -16,6 +20,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -26,16 +31,19 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 4;
-constexpr int kTileBytes = kBM * kBK * 2;  // A and B tiles are both 128 rows x 128 bytes
-constexpr unsigned kTmemCols = 128;         // FP32 accumulator: 128 lanes x 128 columns
+constexpr int kBM = 128, kBK = 64, kStages = 4;
+constexpr int kTileA = kBM * kBK * 2;  // 128 rows x 128 bytes
 constexpr unsigned long long kWaitNs = 2000000000ull;
 // instruction descriptor (kind::f16): D = F32 (bits 4-5), A = B = BF16 (bits
 // 7-9, 10-12), both K-major (bits 15, 16 = 0), N >> 3 (bits 17-22), M >> 4 (bits 24-28)
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
-                            ((uint32_t)(kBM >> 4) << 24);
-constexpr size_t kSmemBytes = 1024 + 2 * kStages * kTileBytes + 256;
-
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+template <int BN>
+constexpr size_t smem_bytes() {
+  return 1024 + (size_t)kStages * (kTileA + BN * kBK * 2) + 256;
+}
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ unsigned long long now_ns() {
@@ -88,11 +96,11 @@ __device__ __forceinline__ unsigned long long sw128_desc(uint32_t saddr) {
 }
 
 __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, unsigned long long a, unsigned long long b,
-                                          uint32_t accumulate) {
+                                          uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
@@ -117,18 +125,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 
+template <int BN>
 __global__ void __launch_bounds__(128, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N, int Kp,
-              TcEpilogue e, int* err) {
+    k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N, int nk_all,
+              int nsplit, TcEpilogue e, float* part, int* err) {
+  constexpr int kTileB = BN * kBK * 2;
+  constexpr uint32_t kCols = BN;  // FP32 accumulator: 128 lanes x BN columns
   extern __shared__ unsigned char sraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)sraw + 1023) & ~(uintptr_t)1023);  // 128B swizzle: 1 KB aligned
   unsigned char* sA = sm;
-  unsigned char* sB = sm + kStages * kTileBytes;
-  uint64_t* bars = (uint64_t*)(sB + kStages * kTileBytes);  // full[kStages], empty[kStages], done
+  unsigned char* sB = sm + kStages * kTileA;
+  uint64_t* bars = (uint64_t*)(sB + kStages * kTileB);  // full[kStages], empty[kStages], done
   uint32_t* tmem_holder = (uint32_t*)(bars + 2 * kStages + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
-  const int nk = Kp / kBK;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
+  // this CTA's range of 64-wide K blocks
+  const int z = blockIdx.z, per = (nk_all + nsplit - 1) / nsplit;
+  const int kb0 = z * per, nk = max(0, min(nk_all, kb0 + per) - kb0);
   auto full = [&](int s) { return smem_u32(bars + s); };
   auto empty = [&](int s) { return smem_u32(bars + kStages + s); };
   const uint32_t done = smem_u32(bars + 2 * kStages);
@@ -143,7 +156,7 @@ __global__ void __launch_bounds__(128, 1)
   }
   if (warp == 0) {  // whole warp: allocate the accumulator columns
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                 "r"(kTmemCols));
+                 "r"(kCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
@@ -160,9 +173,9 @@ __global__ void __launch_bounds__(128, 1)
         ok = false;
         break;
       }
-      mbar_expect_tx(full(s), 2 * kTileBytes);
-      tma_load_2d(smem_u32(sA + s * kTileBytes), &ta, kb * kBK, m0, full(s));
-      tma_load_2d(smem_u32(sB + s * kTileBytes), &tb, kb * kBK, n0, full(s));
+      mbar_expect_tx(full(s), kTileA + kTileB);
+      tma_load_2d(smem_u32(sA + s * kTileA), &ta, (kb0 + kb) * kBK, m0, full(s));
+      tma_load_2d(smem_u32(sB + s * kTileB), &tb, (kb0 + kb) * kBK, n0, full(s));
       ++issued;
     }
     if (!ok)  // let the copies already issued land before the CTA can exit
@@ -176,10 +189,10 @@ __global__ void __launch_bounds__(128, 1)
         break;
       }
       tc_fence_after();
-      const uint32_t a0 = smem_u32(sA + s * kTileBytes), b0 = smem_u32(sB + s * kTileBytes);
+      const uint32_t a0 = smem_u32(sA + s * kTileA), b0 = smem_u32(sB + s * kTileB);
 #pragma unroll
       for (int kk = 0; kk < kBK / 16; ++kk)  // 16 BF16 = 32 bytes per K slice
-        umma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), (kb | kk) != 0);
+        umma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc<BN>(), (kb | kk) != 0);
       umma_commit(empty(s));
     }
     umma_commit(done);  // arrives once every MMA issued above has completed
@@ -191,20 +204,30 @@ __global__ void __launch_bounds__(128, 1)
   tc_fence_after();
   const int row = m0 + warp * 32 + lane;
 #pragma unroll 1
-  for (int c0 = 0; c0 < kBN; c0 += 32) {
+  for (int c0 = 0; c0 < BN; c0 += 32) {
     uint32_t v[32];
     tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
     if (row < M) {
+      if (part) {  // split K: raw partial sums into this split's slice
+        float* dst = part + ((long)z * M + row) * N;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int n = n0 + c0 + j;
-        if (n >= N) break;
-        float x = __uint_as_float(v[j]) + (e.bias ? e.bias[n] : 0.f);
-        const long o = (long)row * e.ldo + n;
-        if (e.pre_f32) e.pre_f32[o] = x;
-        if (e.gelu) x = gelu_f(x);
-        if (e.out_f32) e.out_f32[o] = e.accumulate ? e.out_f32[o] + x : x;
-        if (e.out_bf16) ((bf16*)e.out_bf16)[o] = __float2bfloat16(x);
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c0 + j;
+          if (n >= N) break;
+          dst[n] = nk ? __uint_as_float(v[j]) : 0.f;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c0 + j;
+          if (n >= N) break;
+          float x = __uint_as_float(v[j]) + (e.bias ? e.bias[n] : 0.f);
+          const long o = (long)row * e.ldo + n;
+          if (e.pre_f32) e.pre_f32[o] = x;
+          if (e.gelu) x = gelu_f(x);
+          if (e.out_f32) e.out_f32[o] = e.accumulate ? e.out_f32[o] + x : x;
+          if (e.out_bf16) ((bf16*)e.out_bf16)[o] = __float2bfloat16(x);
+        }
       }
     }
   }
@@ -213,7 +236,20 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   if (warp == 0) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+  }
+}
+
+// out[m][n] (row stride ldo) = sum over splits, in split order, of part[z][m][n]
+__global__ void k_split_sum(const float* __restrict__ part, int nsplit, int M, int N, float* __restrict__ out,
+                            long ldo, int accumulate) {
+  const long total = (long)M * N;
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < nsplit; ++z) s += part[(long)z * total + i];
+    const long m = i / N, n = i - m * N;
+    float* o = out + m * ldo + n;
+    *o = accumulate ? *o + s : s;
   }
 }
 
@@ -235,41 +271,66 @@ EncodeTiled encoder() {
   return fn;
 }
 
-// 2-D map of a row-major BF16 matrix [rows][Kp]: boxes of 128 rows x 64 columns
-bool make_map(CUtensorMap* m, const void* base, int rows, int Kp) {
+// 2-D map of a row-major BF16 matrix [rows][Kp]: boxes of box_rows rows x 64 columns
+bool make_map(CUtensorMap* m, const void* base, int rows, int Kp, int box_rows) {
   EncodeTiled enc = encoder();
   if (!enc) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
   const cuuint32_t es[2] = {1, 1};
   return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+template <int BN>
+bool set_attr() {
+  return cudaFuncSetAttribute(k_tc_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<BN>()) ==
+         cudaSuccess;
+}
+
 }  // namespace
 
 int tc_gemm(const void* A, const void* B, int M, int N, int Mp, int Np, int Kp, const TcEpilogue& e, int* d_err,
-            cudaStream_t st) {
-  if (M < 1 || N < 1 || M > Mp || N > Np || Mp % kBM || Np % kBN || Kp < kBK || Kp % kBK ||
+            cudaStream_t st, float* work, long work_floats) {
+  if (M < 1 || N < 1 || M > Mp || N > Np || Mp % kBM || Np % 128 || Kp < kBK || Kp % kBK ||
       ((uintptr_t)A & 15) || ((uintptr_t)B & 15)) {
     set_last_error("tc_gemm: operand shapes must be padded to 128 x 64 multiples on 16-byte boundaries");
     return OPF_EINVAL;
   }
   static std::once_flag once;
   static bool attr_ok = false;
-  std::call_once(once, [] {
-    attr_ok = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes) ==
-              cudaSuccess;
-  });
+  std::call_once(once, [] { attr_ok = set_attr<128>() && set_attr<64>(); });
+  // launch shape: 64-wide tiles when 128-wide ones leave SMs idle; split K
+  // (plain outputs only) while the tiles still fill fewer than 152 SMs
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles128 = (Mp / kBM) * (Np / 128);
+  const int BN = tiles128 < sms ? 64 : 128;
+  const int tiles = (Mp / kBM) * (Np / BN), nk = Kp / kBK;
+  int nsplit = 1;
+  const bool plain = !e.bias && !e.gelu && !e.pre_f32 && !e.out_bf16 && e.out_f32;
+  if (plain && work)
+    while (nsplit < 8 && tiles * nsplit * 2 <= 2 * sms && nk / (nsplit * 2) >= 4 &&
+           (long)(nsplit * 2) * M * N <= work_floats)
+      nsplit *= 2;
   CUtensorMap ta, tb;
-  if (!attr_ok || !make_map(&ta, A, Mp, Kp) || !make_map(&tb, B, Np, Kp)) {
+  if (!attr_ok || !make_map(&ta, A, Mp, Kp, kBM) || !make_map(&tb, B, Np, Kp, BN)) {
     set_last_error("tc_gemm: tensor map or kernel attribute setup failed");
     return OPF_ECUDA;
   }
-  dim3 grid(Np / kBN, Mp / kBM);
-  k_tc_gemm<<<grid, 128, kSmemBytes, st>>>(ta, tb, M, N, Kp, e, d_err);
+  dim3 grid(Np / BN, Mp / kBM, nsplit);
+  float* part = nsplit > 1 ? work : nullptr;
+  if (BN == 64)
+    k_tc_gemm<64><<<grid, 128, smem_bytes<64>(), st>>>(ta, tb, M, N, nk, nsplit, e, part, d_err);
+  else
+    k_tc_gemm<128><<<grid, 128, smem_bytes<128>(), st>>>(ta, tb, M, N, nk, nsplit, e, part, d_err);
+  if (part) {
+    const long total = (long)M * N;
+    const int blocks = (int)std::min<long>((total + 255) / 256, 4L * sms);
+    k_split_sum<<<blocks, 256, 0, st>>>(part, nsplit, M, N, e.out_f32, e.ldo, e.accumulate);
+  }
   const cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) {
     set_last_error(std::string("tc_gemm launch: ") + cudaGetErrorString(err));

@@ -434,9 +434,14 @@ def run_pipeline(opf, torch, cfg, log=None):
     T_net, s_net = decode_z(z, alpha, T_scale)
     T_net = np.clip(T_net, c["T_min"], c["T_max"])
     U_net = [apply_features(u, y[q], K, M, N) for q, u in enumerate(U0)]
+    T_mean, s_mean = decode_z(mean_tz[None, :], alpha, T_scale)
+    T_mean = float(np.clip(T_mean[0], c["T_min"], c["T_max"]))
     arms = {"recurrence": (U0, T_rec, s_rec),
             "learned": (U_net, list(T_net), list(s_net)),
-            "learned_state_recurrence_T": (U_net, T_rec, s_rec)}
+            "learned_state_recurrence_T": (U_net, T_rec, s_rec),
+            # the single-snapshot guess without a network: the snapshot with the
+            # training-mean period and shift
+            "snapshot_mean_T": (U0, [T_mean] * len(U0), [float(s_mean[0])] * len(U0))}
     nk = dict(c.get("nk", {}))
     Re_te = [float(c["Re_test"])] * len(U0)
     out["nk"] = {}
