@@ -4,8 +4,10 @@ Workload: the medium single-run configuration -- N=48 radial points, |k|<32,
 m<24, m_p=2, Re=2400, alpha=1.25, dt=0.005, seeded puff-like perturbation of
 amplitude 0.1 -- one "step" = one full predictor-corrector time step
 (2 nonlinear evaluations + 2 banded-solve passes) of that grid.  The state
-fits in L2, so L2 is flushed (256 MB write) between timed steps and each
-step is timed alone with CUDA events on the launching stream.
+fits in L2, so L2 is flushed between timed steps (a 256 MB write, then a
+256 MB read of another buffer, so the lines left in L2 are clean and no
+write-back of the flush lands inside the step) and each step is timed alone
+with CUDA events on the launching stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision 0|1] [--impl reference]
 
@@ -49,7 +51,7 @@ def config_dict(w, precision):
         "grid": f"{3 * w['K']}x{3 * w['M']} (z x theta) per radial point",
         "dof": dof(w),
         "precision": "fp64" if precision == 0 else "mixed (fp32 transforms, fp64 solves)",
-        "l2": "flushed (256 MB write) before every timed step",
+        "l2": "flushed before every timed step (256 MB write, then 256 MB read of a second buffer)",
         "parallelism": "replicas (one trajectory per GPU)",
     }
 
@@ -523,13 +525,18 @@ def run_gpu(args, w):
                              w["seed"] + rank, w["envelope"])
     opf.opf_set_state(h, U0)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    clean = torch.ones(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def flush_l2():
+        flush.zero_()  # evicts the step's working set
+        clean.sum()    # evicts the flush's dirty lines outside the timed region
 
     def timed(precision):
         """K steps at one precision from U0; per-step CUDA events, L2 flushed between."""
         opf.opf_set_option(h, "precision", precision)
         opf.opf_set_state(h, U0)
         for _ in range(args.warmup):
-            flush.zero_()
+            flush_l2()
             opf.opf_step(h, 1)
         opf.opf_set_state(h, U0)
         opf.opf_set_option(h, "timing", 1)
@@ -546,7 +553,7 @@ def run_gpu(args, w):
         torch.cuda.synchronize()
         wall0 = time.time()
         for i in range(args.steps):
-            flush.zero_()
+            flush_l2()
             ev0[i].record(stream)
             opf.opf_step(h, 1)
             ev1[i].record(stream)
