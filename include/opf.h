@@ -101,7 +101,10 @@ int opf_nonlinear(opf_t* h, const double* coeffs, double* out);
  *                product, FP64 radial solves and boundary correction)
  *   "n_corr":    corrector iterations per step (default 1)
  *   "graph":     1 = replay the step as a CUDA graph (default), 0 = plain launches
- *   "timing":    1 = record per-kernel device times (opf_kernel_times)
+ *   "timing":    1 = record per-kernel device times (opf_kernel_times); 2 = only
+ *                the kernel named by "timed_kernel" (0 curl, 1 z synthesis,
+ *                2 theta product, 3 z analysis, 4 solve; default 4), so the
+ *                other kernels run without event records between them
  *   "autotune":  1 = on the next step, time the launch shapes of each kernel
  *                (columns/rows per block of the transforms, modes per block of
  *                the solve) on the current state and keep the fastest; reads

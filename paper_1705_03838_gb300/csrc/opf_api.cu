@@ -343,14 +343,19 @@ struct Runner {
   double tot_ms[kNumNames] = {0};
   int tot_n[kNumNames] = {0};
 
+  // timing 1: every kernel; timing 2: only kernel `timed_kernel` (fewer event nodes)
+  int timed_kernel = 4;
+  bool timed(int name) const { return timing == 1 || (timing == 2 && name == timed_kernel); }
+  int open_name = -1;
   void begin(int name) {
-    if (!timing || nslots >= kMaxSlots) return;
+    open_name = name;
+    if (!timed(name) || nslots >= kMaxSlots) return;
     slot_name[nslots] = name;
     // external: inside stream capture this becomes an event-record node
     cudaEventRecordWithFlags(ev[nslots][0], stream, cudaEventRecordExternal);
   }
   void end() {
-    if (!timing || nslots >= kMaxSlots) return;
+    if (!timed(open_name) || nslots >= kMaxSlots) return;
     cudaEventRecordWithFlags(ev[nslots][1], stream, cudaEventRecordExternal);
     ++nslots;
   }
@@ -613,8 +618,12 @@ int runner_option(Runner* r, const char* key, double v) {
     if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "graph: 0 or 1");
     r->use_graph = (int)v;
   } else if (!strcmp(key, "timing")) {
-    if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "timing: 0 or 1");
+    if (v != 0.0 && v != 1.0 && v != 2.0) return fail(OPF_EINVAL, "timing: 0, 1 or 2");
+    if ((int)v != r->timing) r->drop_graph();  // the event nodes are part of the graph
     r->timing = (int)v;
+  } else if (!strcmp(key, "timed_kernel")) {
+    if (!(v >= 0 && v <= 4 && v == std::floor(v))) return fail(OPF_EINVAL, "timed_kernel: 0..4");
+    r->timed_kernel = (int)v;
   } else if (!strcmp(key, "autotune")) {
     if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "autotune: 0 or 1");
     r->autotune = (int)v;
@@ -631,6 +640,7 @@ int runner_get_option(Runner* r, const char* key, double* v) {
   else if (!strcmp(key, "n_corr")) *v = r->n_corr;
   else if (!strcmp(key, "graph")) *v = r->use_graph;
   else if (!strcmp(key, "timing")) *v = r->timing;
+  else if (!strcmp(key, "timed_kernel")) *v = r->timed_kernel;
   else if (!strcmp(key, "autotune")) *v = r->autotune;
   else if (!strcmp(key, "tile")) *v = r->groups.empty() ? 0 : r->groups[0]->d.tile;
   else if (!strcmp(key, "mcz")) *v = r->groups.empty() ? 0 : r->groups[0]->d.mcz;
