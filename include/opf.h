@@ -214,6 +214,39 @@ int opf_nk_solve(int N, int K, int M, int m_p, double alpha, double Re, int coun
                  double* states, double* T, double* s, const opf_nk_opts* opts,
                  double* residual, int* iters);
 
+/* ---- Leading eigenvalues of linear maps: stability of invariant solutions
+ * (the paper's Newton utility converges travelling waves and periodic orbits;
+ * section 3.2 quotes the leading eigenvalue of one) --------------------------
+ * opf_arnoldi_core runs kdim Arnoldi steps (modified Gram-Schmidt applied
+ * twice, FP64) for count linear maps of size n in lockstep: each step calls
+ * A once for all maps still running (idx[j] names the map of v[j]; write
+ * A v[j] to av[j]; return non-zero to abort).  A map stops early when its
+ * Krylov space becomes invariant.  Ritz values are the eigenvalues of the
+ * Hessenberg matrix (implicit double-shift QR); the nev of largest modulus
+ * are returned per map ([count][nev], decreasing modulus) with residual
+ * estimates |h_{k+1,k}| |e_k^T y| (y the unit Ritz vector of H; resid may be
+ * NULL).  v0: [count][n] starting vectors (non-zero); kused: [count] Krylov
+ * dimension reached (may be NULL).  Returns OPF_EINVAL on bad arguments. */
+typedef int (*opf_linear_map)(void* ctx, int count, const int* idx, double* const* v, double* const* av);
+int opf_arnoldi_core(int n, int count, const double* v0, int kdim, int nev, opf_linear_map A, void* ctx,
+                     double* eig_re, double* eig_im, double* resid, int* kused);
+
+/* Floquet multipliers (eigenvalues of the linearised period map
+ * dv -> sigma_s DPhi_T(u) dv) of count states of the pipe flow, e.g. periodic
+ * orbits or travelling waves returned by opf_nk_solve (for a travelling wave
+ * or equilibrium any T > 0 works; the multipliers are then exp(lambda T)).
+ * Phi_T: n = ceil(max T / dt) steps of T_i / n; products by finite
+ * differences with relative step eps (perturbation eps |u| / |dv|);
+ * precision: 0 FP64, 1 mixed time integration; start: [count] starting
+ * vectors in the state layout, or NULL for SplitMix64 uniforms from seed (a
+ * start inside an invariant subspace, e.g. one Fourier mode of one component,
+ * restricts the search to it).  states: [count] host states (state layout);
+ * outputs as for opf_arnoldi_core, over the independent coefficients (m = 0
+ * with k >= 0, all k for m > 0).  No counterpart call exists in the paper. */
+int opf_floquet(int N, int K, int M, int m_p, double alpha, double Re, int count, const double* states,
+                const double* T, const double* s, int kdim, int nev, double dt, double eps, int precision,
+                unsigned long long seed, const double* start, double* eig_re, double* eig_im, double* resid);
+
 /* ---- Proposal network for Newton-Krylov initial guesses (no counterpart in
  * the paper; the learned-proposal part of this implementation) ---------------
  * A 1-D convolution net over the L radial points of the lowest Fourier modes:

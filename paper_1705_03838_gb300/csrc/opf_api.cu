@@ -1386,3 +1386,116 @@ extern "C" int opf_nk_solve(int N, int K, int M, int m_p, double alpha, double R
   delete c;
   return rc;
 }
+
+// ---- Floquet multipliers / eigenvalues of invariant solutions
+namespace {
+struct FqCtx {
+  NkCtx* c;
+  double eps;
+  std::vector<std::vector<double>> base;  // packed sigma_s Phi_T(u) per problem
+};
+
+// av = (sigma_s Phi_T(u + e v) - sigma_s Phi_T(u)) / e, e = eps |u| / |v|
+int fq_apply(void* vctx, int cnt, const int* idx, double* const* v, double* const* av) {
+  FqCtx* f = (FqCtx*)vctx;
+  NkCtx* c = f->c;
+  const long L = nk_state_len(c);
+  std::vector<std::vector<double>> up(cnt, std::vector<double>(L));
+  std::vector<double> e(cnt), tmp(c->ndof);
+  for (int j = 0; j < cnt; ++j) {
+    const std::vector<double>& u = c->ubase[idx[j]];
+    double un = 0.0, vn = 0.0;
+    for (long t = 0; t < c->ndof; ++t) {
+      un += u[t] * u[t];
+      vn += v[j][t] * v[j][t];
+    }
+    e[j] = vn > 0 ? f->eps * std::sqrt(un / vn) : 1.0;
+    for (long t = 0; t < c->ndof; ++t) tmp[t] = u[t] + e[j] * v[j][t];
+    c->pk.unpack(tmp.data(), up[j].data());
+  }
+  int rc = nk_integrate(c, cnt, idx, up, c->nsteps);
+  if (rc) return rc;
+  for (int j = 0; j < cnt; ++j) {
+    const int i = idx[j];
+    shift_state(*c, up[j].data(), c->s[i], false);
+    c->pk.pack(up[j].data(), av[j]);
+    for (long t = 0; t < c->ndof; ++t) av[j][t] = (av[j][t] - f->base[i][t]) / e[j];
+  }
+  return OPF_OK;
+}
+}  // namespace
+
+extern "C" int opf_floquet(int N, int K, int M, int m_p, double alpha, double Re, int count, const double* states,
+                           const double* T, const double* s, int kdim, int nev, double dt, double eps,
+                           int precision, unsigned long long seed, const double* start, double* eig_re,
+                           double* eig_im, double* resid) {
+  if (count < 1 || !states || !T || !s || kdim < 1 || nev < 1 || nev > kdim || !(dt > 0) || !(eps > 0) ||
+      !eig_re || !eig_im || (precision != 0 && precision != 1))
+    return fail(OPF_EINVAL, "opf_floquet: bad arguments");
+  for (int i = 0; i < count; ++i)
+    if (!(T[i] > 0)) return fail(OPF_EINVAL, "opf_floquet: periods must be positive");
+  NkCtx* c = new NkCtx(N, K, M);
+  c->N = N;
+  c->K = K;
+  c->M = M;
+  c->m_p = m_p;
+  c->alpha = alpha;
+  c->count = count;
+  double Tmax = 0.0;
+  for (int i = 0; i < count; ++i) Tmax = std::max(Tmax, T[i]);
+  c->nsteps = std::max(1, (int)std::ceil(Tmax / dt - 1e-9));
+  std::vector<double> Re_v(count, Re), dt_v(count);
+  for (int i = 0; i < count; ++i) dt_v[i] = T[i] / c->nsteps;
+  int rc = group_build(&c->g, N, K, M, m_p, alpha, count, Re_v.data(), dt_v.data(), true);
+  if (rc == OPF_OK) rc = runner_init(&c->run);
+  if (rc != OPF_OK) {
+    group_free(&c->g);
+    runner_free(&c->run);
+    delete c;
+    return rc;
+  }
+  c->run.groups = {&c->g};
+  c->run.precision = precision;
+  c->ndof = c->pk.ndof;
+  c->n = c->ndof;
+  c->T.assign(T, T + count);
+  c->s.assign(s, s + count);
+  c->ubase.resize(count);
+  FqCtx f{c, eps, {}};
+  f.base.resize(count);
+  const long L = nk_state_len(c);
+  std::vector<int> all(count);
+  std::vector<std::vector<double>> u(count);
+  for (int i = 0; i < count; ++i) {
+    all[i] = i;
+    c->ubase[i].resize(c->ndof);
+    c->pk.pack(states + (size_t)i * L, c->ubase[i].data());
+    u[i].assign(states + (size_t)i * L, states + (size_t)(i + 1) * L);
+  }
+  rc = nk_integrate(c, count, all.data(), u, c->nsteps);
+  if (rc == OPF_OK) {
+    // base points, and seeded starting vectors (SplitMix64 uniforms in [-1, 1))
+    std::vector<double> v0((size_t)count * c->ndof);
+    unsigned long long z = seed;
+    for (size_t t = 0; t < v0.size(); ++t) {
+      z += 0x9E3779B97F4A7C15ull;
+      unsigned long long q = z;
+      q = (q ^ (q >> 30)) * 0xBF58476D1CE4E5B9ull;
+      q = (q ^ (q >> 27)) * 0x94D049BB133111EBull;
+      q ^= q >> 31;
+      v0[t] = 2.0 * ((double)(q >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+    }
+    if (start)  // caller's starting vectors, state layout
+      for (int i = 0; i < count; ++i) c->pk.pack(start + (size_t)i * L, &v0[(size_t)i * c->ndof]);
+    for (int i = 0; i < count; ++i) {
+      shift_state(*c, u[i].data(), c->s[i], false);
+      f.base[i].resize(c->ndof);
+      c->pk.pack(u[i].data(), f.base[i].data());
+    }
+    rc = opf_arnoldi_core((int)c->ndof, count, v0.data(), kdim, nev, fq_apply, &f, eig_re, eig_im, resid, nullptr);
+  }
+  runner_free(&c->run);
+  group_free(&c->g);
+  delete c;
+  return rc;
+}

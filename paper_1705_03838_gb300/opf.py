@@ -113,6 +113,11 @@ def lib():
         L.opf_nk_solve.restype = i
         L.opf_nk_solve.argtypes = [i, i, i, i, d, d, i, vp, _dp, _dp, ctypes.POINTER(NkOpts), _dp,
                                    ctypes.POINTER(i)]
+        L.opf_arnoldi_core.restype = i
+        L.opf_arnoldi_core.argtypes = [i, i, _dp, i, i, LINEAR_MAP, vp, _dp, _dp, _dp, ctypes.POINTER(i)]
+        L.opf_floquet.restype = i
+        L.opf_floquet.argtypes = [i, i, i, i, d, d, i, vp, _dp, _dp, i, i, d, d, i, ctypes.c_ulonglong, vp,
+                                  _dp, _dp, _dp]
         L.opf_net_create.restype = vp
         L.opf_net_create.argtypes = [i, i, i, i, ctypes.c_ulonglong]
         L.opf_net_destroy.restype = None
@@ -403,6 +408,56 @@ def opf_nk_solve(N, K, M, m_p, alpha, Re, states, T, s, **opts):
     _check(lib().opf_nk_solve(N, K, M, m_p, alpha, Re, count, st.ctypes.data, Ta.ctypes.data_as(_dp),
                               sa.ctypes.data_as(_dp), ctypes.byref(o), res.ctypes.data_as(_dp), it))
     return list(st), Ta, sa, res, np.array(it[:])
+
+
+LINEAR_MAP = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _pdp, _pdp)
+
+
+def opf_arnoldi_core(v0, A, kdim, nev):
+    """Leading eigenvalues of count linear maps (host Arnoldi): v0 (count, n);
+    A(idx, vs) -> list of A v arrays.  Returns (eigenvalues (count, nev)
+    complex, residual estimates (count, nev), Krylov dimensions (count,))."""
+    v = np.ascontiguousarray(v0, dtype=np.float64)
+    count, n = v.shape
+
+    def cb(ctx, cnt, idx, vp, ap):
+        try:
+            ids = [idx[j] for j in range(cnt)]
+            vs = [np.ctypeslib.as_array(vp[j], shape=(n,)).copy() for j in range(cnt)]
+            out = A(ids, vs)
+            for j in range(cnt):
+                np.ctypeslib.as_array(ap[j], shape=(n,))[:] = out[j]
+            return 0
+        except Exception:
+            return -1
+
+    fn = LINEAR_MAP(cb)
+    er = np.zeros((count, nev))
+    ei = np.zeros((count, nev))
+    rs = np.zeros((count, nev))
+    ku = (ctypes.c_int * count)()
+    _check(lib().opf_arnoldi_core(n, count, v.ctypes.data_as(_dp), int(kdim), int(nev), fn, None,
+                                  er.ctypes.data_as(_dp), ei.ctypes.data_as(_dp), rs.ctypes.data_as(_dp), ku))
+    return er + 1j * ei, rs, np.array(ku[:])
+
+
+def opf_floquet(N, K, M, m_p, alpha, Re, states, T, s, kdim, nev, dt, eps=1e-7, precision=0, seed=1,
+                start=None):
+    """Floquet multipliers of count states (time-T maps with axial shift s):
+    returns (multipliers (count, nev) complex, residual estimates)."""
+    count = len(states)
+    st = np.ascontiguousarray(np.stack(states), dtype=np.complex128)
+    Ta = np.ascontiguousarray(T, dtype=np.float64)
+    sa = np.ascontiguousarray(s, dtype=np.float64)
+    sv = None if start is None else np.ascontiguousarray(np.stack(start), dtype=np.complex128)
+    er = np.zeros((count, nev))
+    ei = np.zeros((count, nev))
+    rs = np.zeros((count, nev))
+    _check(lib().opf_floquet(N, K, M, m_p, float(alpha), float(Re), count, st.ctypes.data, Ta.ctypes.data_as(_dp),
+                             sa.ctypes.data_as(_dp), int(kdim), int(nev), float(dt), float(eps), int(precision),
+                             ctypes.c_ulonglong(seed), None if sv is None else sv.ctypes.data,
+                             er.ctypes.data_as(_dp), ei.ctypes.data_as(_dp), rs.ctypes.data_as(_dp)))
+    return er + 1j * ei, rs
 
 
 class NetHandle:
