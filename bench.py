@@ -507,6 +507,39 @@ def run_net(args):
     print(json.dumps(line), flush=True)
 
 
+def run_floquet(args):
+    """Leading Floquet multipliers of 16 perturbed laminar states (N=32,
+    |k|<16, m<16, m_p=2, alpha=1.25, Re=2000), period T=2 at dt=0.01: 30
+    Arnoldi steps, each one batched 200-step integration of all 16 states."""
+    import numpy as np
+    import torch
+
+    from paper_1705_03838_gb300 import build as _build, inputs, opf
+
+    torch.cuda.set_device(0)
+    _build.build()
+    opf.lib()
+    N, K, M, m_p, alpha, Re, T, dt, k, count = 32, 16, 16, 2, 1.25, 2000.0, 2.0, 0.01, 30, 16
+    lam = inputs.laminar_state(N, K, M)
+    states = [lam + inputs.seeded_state(N, K, M, m_p, alpha, 1e-3, 700 + i, laminar=False) for i in range(count)]
+    t0 = time.perf_counter()
+    ev, res = opf.opf_floquet(N, K, M, m_p, alpha, Re, states, [T] * count, [0.0] * count, k, 4, dt, precision=0)
+    sec = time.perf_counter() - t0
+    steps = (k + 1) * int(round(T / dt)) * count
+    line = {
+        "metric": "Floquet multipliers: batched Arnoldi trajectory-steps/s (FP64 integrations)",
+        "value": steps / sec, "unit": "trajectory-steps/s", "n_gpus": 1, "higher_is_better": True,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"floquet: {count} states N={N} |k|<{K} m<{M} m_p={m_p} Re={Re} T={T} dt={dt}, "
+                               f"{k} Arnoldi steps"},
+        "seconds": sec,
+        "leading_multipliers_state0": [[float(z.real), float(z.imag)] for z in ev[0]],
+        "residual_estimates_state0": [float(r) for r in res[0]],
+        "max_modulus_all_states": float(np.abs(ev).max()),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args, w):
     import numpy as np
     import torch
@@ -707,10 +740,12 @@ def main():
                     help="headline precision: 1 = mixed (default), 0 = FP64; both are timed")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="medium", choices=["medium", "ensemble", "large", "learned", "net"],
+    ap.add_argument("--workload", default="medium",
+                    choices=["medium", "ensemble", "large", "learned", "net", "floquet"],
                     help="medium: the default single-run line; ensemble: the batched workload; large: the "
                          "CFL-controlled large run; learned: the learned Newton-Krylov proposal pipeline; "
-                         "net: the proposal network's training step")
+                         "net: the proposal network's training step; floquet: batched Arnoldi "
+                         "Floquet multipliers")
     ap.add_argument("--autotune", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -726,6 +761,8 @@ def main():
         run_learned(args)
     elif args.workload == "net":
         run_net(args)
+    elif args.workload == "floquet":
+        run_floquet(args)
     else:
         run_gpu(args, w)
 
