@@ -533,9 +533,11 @@ def run_floquet(args):
         "config": {"workload": f"floquet: {count} states N={N} |k|<{K} m<{M} m_p={m_p} Re={Re} T={T} dt={dt}, "
                                f"{k} Arnoldi steps"},
         "seconds": sec,
-        "leading_multipliers_state0": [[float(z.real), float(z.imag)] for z in ev[0]],
+        # Ritz values of largest modulus and their residual estimates: after 30
+        # steps on this strongly non-normal map they are not yet converged
+        # eigenvalues (large residuals); the line measures the throughput
+        "ritz_values_state0": [[float(z.real), float(z.imag)] for z in ev[0]],
         "residual_estimates_state0": [float(r) for r in res[0]],
-        "max_modulus_all_states": float(np.abs(ev).max()),
     }
     print(json.dumps(line), flush=True)
 
