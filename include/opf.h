@@ -289,6 +289,17 @@ int opf_net_train_step(opf_net_t* n, const float* d_x, const float* d_ty, const 
 int opf_nonlinear_noalloc(int N, int K, int M, int m_p, double alpha, double Re,
                           const double* d_state, double* d_out, void* stream);
 
+/* Host-only (no GPU needed): a state of resolution (N1, K1, M1) at another
+ * resolution (N2, K2, M2), same m_p (the paper: initial conditions of another
+ * resolution are truncated or interpolated automatically).  Fourier modes
+ * present in both are copied, the others are zero; radial profiles are
+ * interpolated by the 9-point Lagrange interpolant through the nearest nodes
+ * of the source mesh extended to negative r with the field's axis parity.
+ * in / out: state layout [3][M][2K-1][N] complex (interleaved), caller-owned.
+ * OPF_EINVAL for non-positive sizes or N1 < 9. */
+int opf_change_resolution(int N1, int K1, int M1, const double* in, int N2, int K2, int M2, int m_p,
+                          double* out);
+
 /* Host-only diagnostics (no GPU needed): build the radial setup that
  * opf_create would build for these parameters and copy one array into
  * out[0..cap).  what = "r" (N radial points), "wq" (N quadrature weights,

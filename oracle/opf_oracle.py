@@ -406,3 +406,35 @@ class Oracle:
         V = U.copy()
         V[:, 0] = 0.5 * (U[:, 0] + np.conj(U[:, 0, ::-1]))
         return V
+
+
+def change_resolution(U, N2, K2, M2, m_p):
+    """A state (3, M1, 2K1-1, N1) at resolution (N2, K2, M2), same m_p
+    (section 2: initial conditions of another resolution are truncated or
+    interpolated).  Fourier modes present in both are copied, others zero;
+    each radial profile is evaluated at the new points by the Lagrange
+    polynomial through the 9 nodes of the parity-extended old mesh nearest to
+    the new point (reading R3's extension), its basis written out as
+    products."""
+    _, M1, nk1, N1 = U.shape
+    K1 = (nk1 + 1) // 2
+    r1, r2 = mesh(N1), mesh(N2)
+    ext = np.concatenate([-r1[::-1], r1])
+    out = np.zeros((3, M2, 2 * K2 - 1, N2), dtype=np.complex128)
+    for n in range(N2):
+        z = r2[n]
+        q = int(np.argmin(np.abs(ext - z)))
+        f = min(max(q - 4, 0), 2 * N1 - 9)
+        nodes = ext[f:f + 9]
+        basis = np.array([np.prod([(z - nodes[j]) / (nodes[i] - nodes[j]) for j in range(9) if j != i])
+                          for i in range(9)])
+        for c in range(3):
+            for m in range(min(M1, M2)):
+                mt = m_p * m
+                parity = (-1) ** mt if c == 2 else (-1) ** (mt + 1)
+                for k in range(-(min(K1, K2) - 1), min(K1, K2)):
+                    prof = U[c, m, k + K1 - 1]
+                    vals = np.array([prof[e - N1] if e >= N1 else parity * prof[N1 - 1 - e]
+                                     for e in range(f, f + 9)])
+                    out[c, m, k + K2 - 1, n] = basis @ vals
+    return out

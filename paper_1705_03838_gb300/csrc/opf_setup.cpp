@@ -460,3 +460,68 @@ bool build_setup(Setup* s, std::string* err) {
 }
 
 }  // namespace opf
+
+// ---- resolution change (the paper: initial conditions of another resolution
+// are truncated or interpolated automatically).  Fourier modes: copied where
+// both resolutions have them, zero otherwise.  Radial profiles: the 9-point
+// Lagrange interpolant through the source mesh extended to negative r by the
+// field's axis parity ((-1)^(m_p m) for u_z, (-1)^(m_p m + 1) for u_r and
+// u_theta), nodes nearest the target point, shifted inward at the ends.
+extern "C" int opf_change_resolution(int N1, int K1, int M1, const double* in, int N2, int K2, int M2, int m_p,
+                                     double* out) {
+  if (N1 < 9 || N2 < 1 || K1 < 1 || K2 < 1 || M1 < 1 || M2 < 1 || m_p < 1 || !in || !out) {
+    opf::set_last_error("opf_change_resolution: sizes must be positive and the source N >= 9");
+    return OPF_EINVAL;
+  }
+  auto mesh = [](int N) {
+    std::vector<double> r(N);
+    for (int n = 0; n < N; ++n) r[n] = std::cos(M_PI * (double)(N - 1 - n) / (2.0 * N - 1.0));
+    return r;
+  };
+  const std::vector<double> r1 = mesh(N1), r2 = mesh(N2);
+  // extended source nodes: e < N1 -> -r1[N1-1-e] (ghost), else r1[e-N1]
+  auto ext_x = [&](int e) { return e < N1 ? -r1[N1 - 1 - e] : r1[e - N1]; };
+  std::vector<int> first(N2);
+  std::vector<double> w((size_t)N2 * 9);
+  for (int n = 0; n < N2; ++n) {
+    const double z = r2[n];
+    int q = N1;  // nearest extended node
+    for (int e = 0; e < 2 * N1; ++e)
+      if (std::fabs(ext_x(e) - z) < std::fabs(ext_x(q) - z)) q = e;
+    const int f = std::min(std::max(q - 4, 0), 2 * N1 - 9);
+    first[n] = f;
+    double x[9], c[9];
+    for (int t = 0; t < 9; ++t) x[t] = ext_x(f + t);
+    opf::fornberg(z, x, 9, 0, c);
+    for (int t = 0; t < 9; ++t) w[(size_t)n * 9 + t] = c[t];
+    if (ext_x(q) == z)  // a target on a source node takes its value exactly
+      for (int t = 0; t < 9; ++t) w[(size_t)n * 9 + t] = (f + t == q) ? 1.0 : 0.0;
+  }
+  const int nk1 = 2 * K1 - 1, nk2 = 2 * K2 - 1;
+  for (int c = 0; c < 3; ++c)
+    for (int m = 0; m < M2; ++m)
+      for (int kk2 = 0; kk2 < nk2; ++kk2) {
+        const int k = kk2 - (K2 - 1), kk1 = k + (K1 - 1);
+        double* o = out + 2 * ((((size_t)c * M2 + m) * nk2 + kk2) * N2);
+        if (m >= M1 || kk1 < 0 || kk1 >= nk1) {
+          for (int n = 0; n < 2 * N2; ++n) o[n] = 0.0;
+          continue;
+        }
+        const double* s = in + 2 * ((((size_t)c * M1 + m) * nk1 + kk1) * N1);
+        const int mt = m_p * m;
+        const double par = ((c == 2 ? mt : mt + 1) % 2 == 0) ? 1.0 : -1.0;
+        for (int n = 0; n < N2; ++n) {
+          double re = 0.0, im = 0.0;
+          for (int t = 0; t < 9; ++t) {
+            const int e = first[n] + t;
+            const int col = e < N1 ? N1 - 1 - e : e - N1;
+            const double sg = e < N1 ? par : 1.0;
+            re += w[(size_t)n * 9 + t] * sg * s[2 * col];
+            im += w[(size_t)n * 9 + t] * sg * s[2 * col + 1];
+          }
+          o[2 * n] = re;
+          o[2 * n + 1] = im;
+        }
+      }
+  return OPF_OK;
+}

@@ -136,6 +136,8 @@ def lib():
         L.opf_net_train_step.argtypes = [vp, vp, vp, vp, i, ctypes.c_float, ctypes.c_float, _dp]
         L.opf_nonlinear_noalloc.restype = i
         L.opf_nonlinear_noalloc.argtypes = [i, i, i, i, d, d, vp, vp, vp]
+        L.opf_change_resolution.restype = i
+        L.opf_change_resolution.argtypes = [i, i, i, vp, i, i, i, i, vp]
         L.opf_setup_query.restype = i
         L.opf_setup_query.argtypes = [i, i, i, i, d, d, d, cp, _dp, ctypes.c_long,
                                       ctypes.POINTER(ctypes.c_long)]
@@ -458,6 +460,15 @@ def opf_floquet(N, K, M, m_p, alpha, Re, states, T, s, kdim, nev, dt, eps=1e-7, 
                              ctypes.c_ulonglong(seed), None if sv is None else sv.ctypes.data,
                              er.ctypes.data_as(_dp), ei.ctypes.data_as(_dp), rs.ctypes.data_as(_dp)))
     return er + 1j * ei, rs
+
+
+def opf_change_resolution(state, N2, K2, M2, m_p):
+    """state (3, M1, 2K1-1, N1) -> the same flow at (N2, K2, M2)."""
+    a = np.ascontiguousarray(state, dtype=np.complex128)
+    _, M1, nk1, N1 = a.shape
+    out = np.empty((3, M2, 2 * K2 - 1, N2), dtype=np.complex128)
+    _check(lib().opf_change_resolution(N1, (nk1 + 1) // 2, M1, a.ctypes.data, N2, K2, M2, m_p, out.ctypes.data))
+    return out
 
 
 class NetHandle:
