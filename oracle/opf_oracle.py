@@ -52,10 +52,15 @@ __all__ = [
 class Params:
     """Run parameters (paper section 2): resolution (N, K, M), m_p, alpha, Re, dt."""
 
-    def __init__(self, N, K, M, m_p, alpha, Re, dt, c=0.5, n_corr=1):
+    def __init__(self, N, K, M, m_p, alpha, Re, dt, c=0.5, n_corr=1, rotation=(0.0, 0.0, 0.0), forcing=None):
         self.N, self.K, self.M, self.m_p = int(N), int(K), int(M), int(m_p)
         self.alpha, self.Re, self.dt = float(alpha), float(Re), float(dt)
         self.c, self.n_corr = float(c), int(n_corr)
+        # frame rotation Omega (Cartesian, pipe axis z): Coriolis force -2 Omega x u
+        # (section 3.3 adds it through the forcing hook); forcing: a constant
+        # spectral body force (3, M, 2K-1, N) in (r, theta, z) components
+        self.rotation = tuple(float(x) for x in rotation)
+        self.forcing = forcing
         self.nk = 2 * self.K - 1
         self.nz = 3 * self.K  # 3/2 dealiasing: 3K x 3M grid (section 2)
         self.nth = 3 * self.M
@@ -285,8 +290,19 @@ class Oracle:
         n_r = u[1] * w[2] - u[2] * w[1]
         n_t = u[2] * w[0] - u[0] * w[2]
         n_z = u[0] * w[1] - u[1] * w[0]
+        ox, oy, oz = self.p.rotation
+        if ox or oy or oz:
+            # Omega in cylindrical components at theta = 2 pi q / (m_p 3M)
+            th = 2.0 * np.pi * np.arange(self.p.nth) / (self.p.m_p * self.p.nth)
+            o_r = (ox * np.cos(th) + oy * np.sin(th))[None, None, :]
+            o_t = (-ox * np.sin(th) + oy * np.cos(th))[None, None, :]
+            n_r = n_r - 2.0 * (o_t * u[2] - oz * u[1])
+            n_t = n_t - 2.0 * (oz * u[0] - o_r * u[2])
+            n_z = n_z - 2.0 * (o_r * u[1] - o_t * u[0])
         Nl = np.stack([self.analyse(n_r), self.analyse(n_t), self.analyse(n_z)])
         Nl[2, 0, self.p.K - 1] += 4.0 / self.p.Re
+        if self.p.forcing is not None:
+            Nl = Nl + self.p.forcing
         return Nl
 
     # ---- implicit solve, one dense system per mode
