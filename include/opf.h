@@ -110,6 +110,10 @@ int opf_nonlinear(opf_t* h, const double* coeffs, double* out);
  *                the solve) on the current state and keep the fastest; reads
  *                back as 2 once done.  Read-only keys "tile", "mcz", "mca", "zc"
  *                report the shapes in use.
+ *   "rot_x", "rot_y", "rot_z": frame rotation Omega (Cartesian components, pipe
+ *                axis z; default 0): the Coriolis force -2 Omega x u joins the
+ *                nonlinear term (section 3.3's rotating pipe; a transverse axis
+ *                needs m_p = 1).  Single handles only.
  *   "cfl":       C > 0 switches on automatic time-step control (section 2):
  *                after every step dt = min(dt_max, C / max(|u_r|/dr,
  *                |u_theta|/(r dtheta), |u_z|/dz)) over the 3K x 3M grid, applied
@@ -288,6 +292,12 @@ int opf_net_train_step(opf_net_t* n, const float* d_x, const float* d_ty, const 
  * library routine); a failure only stores its message for opf_last_error. */
 int opf_nonlinear_noalloc(int N, int K, int M, int m_p, double alpha, double Re,
                           const double* d_state, double* d_out, void* stream);
+
+/* Constant body force f (paper section 3.3: a user forcing hook; state layout,
+ * components (f_r, f_theta, f_z), host memory, copied) added to the nonlinear
+ * term at every evaluation; NULL removes it.  A uniform axial force on the
+ * (0,0) mode is absorbed by the fixed-flux driving (beta shifts by -f Re / 4). */
+int opf_set_forcing(opf_t* h, const double* coeffs);
 
 /* Host-only (no GPU needed): a state of resolution (N1, K1, M1) at another
  * resolution (N2, K2, M2), same m_p (the paper: initial conditions of another

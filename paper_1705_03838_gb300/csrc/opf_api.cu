@@ -736,6 +736,7 @@ int traj_beta(Group* g, int b, double* beta, cudaStream_t st) {
 struct opf_ctx {
   Group g;
   Runner run;
+  double2* forcing = nullptr;  // constant body force, internal +- layout (opf_set_forcing)
 };
 
 struct opf_ens {
@@ -777,7 +778,28 @@ void opf_destroy(opf_t* h) {
   cudaStreamSynchronize(h->run.stream);
   runner_free(&h->run);
   group_free(&h->g);
+  if (h->forcing) cudaFree(h->forcing);
   delete h;
+}
+
+int opf_set_forcing(opf_t* h, const double* coeffs) {
+  if (check_handle(h)) return OPF_EINVAL;
+  CU(cudaStreamSynchronize(h->run.stream));
+  h->run.drop_graph();
+  if (!coeffs) {
+    h->g.d.forcing = nullptr;
+    return OPF_OK;
+  }
+  const size_t bytes = 3 * (size_t)h->g.d.F * sizeof(double2);
+  if (!h->forcing) CU(cudaMalloc((void**)&h->forcing, bytes));
+  double2* abi = h->g.at(h->g.abi, 0);  // staging in the ABI layout
+  CU(cudaMemcpyAsync(abi, coeffs, bytes, cudaMemcpyHostToDevice, h->run.stream));
+  opf::Dims d1 = h->g.single(0);
+  opf::launch_abi_to_internal(d1, abi, h->forcing, h->run.stream);
+  CU(cudaStreamSynchronize(h->run.stream));
+  CU(cudaGetLastError());
+  h->g.d.forcing = h->forcing;
+  return OPF_OK;
 }
 
 int opf_set_state_device(opf_t* h, const double* d_coeffs) {
@@ -860,6 +882,20 @@ int opf_set_option(opf_t* h, const char* key, double v) {
     h->run.dt_max = v;
     return OPF_OK;
   }
+  if (key && (!strcmp(key, "rot_x") || !strcmp(key, "rot_y") || !strcmp(key, "rot_z"))) {
+    if (!std::isfinite(v)) return fail(OPF_EINVAL, "rotation: finite value");
+    opf::Dims& d = h->g.d;
+    double x = d.rot_x, y = d.rot_y, z = d.rot_z;
+    (key[4] == 'x' ? x : key[4] == 'y' ? y : z) = v;
+    if ((x != 0.0 || y != 0.0) && d.m_p != 1)
+      return fail(OPF_EINVAL, "rotation about a transverse axis needs m_p = 1 (it couples m to m +- 1)");
+    d.rot_x = x;
+    d.rot_y = y;
+    d.rot_z = z;
+    d.rotate = (x != 0.0 || y != 0.0 || z != 0.0) ? 1 : 0;
+    h->run.drop_graph();
+    return OPF_OK;
+  }
   if (key && !strcmp(key, "dt")) {  // set the time step; dt-dependent operators are refactored
     if (!(v > 0.0) || !std::isfinite(v)) return fail(OPF_EINVAL, "dt: > 0");
     if (v != h->g.dt[0]) {
@@ -883,6 +919,9 @@ int opf_get_option(opf_t* h, const char* key, double* v) {
     *v = h->run.dt_max > 0.0 ? h->run.dt_max : h->g.dt[0];
     return OPF_OK;
   }
+  if (key && v && !strcmp(key, "rot_x")) return (*v = h->g.d.rot_x), OPF_OK;
+  if (key && v && !strcmp(key, "rot_y")) return (*v = h->g.d.rot_y), OPF_OK;
+  if (key && v && !strcmp(key, "rot_z")) return (*v = h->g.d.rot_z), OPF_OK;
   if (key && v && !strcmp(key, "cfl_number")) {  // max |u| dt / spacing of the last step
     double c = 0.0;
     CU(cudaMemcpy(&c, h->g.cfl, sizeof(double), cudaMemcpyDeviceToHost));

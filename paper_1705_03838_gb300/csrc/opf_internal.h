@@ -88,6 +88,13 @@ struct Dims {
   // points from rinv_cfl (+ b*ps)
   double* cfl = nullptr;
   const double* rinv_cfl = nullptr;
+  // frame rotation Omega (Cartesian, pipe axis z): Coriolis force -2 Omega x u
+  // added to the nonlinear term in the product kernel (rotate: any non-zero)
+  int rotate = 0;
+  double rot_x = 0.0, rot_y = 0.0, rot_z = 0.0;
+  // constant body force in the internal +- layout [3][m][n][kk] added to the
+  // nonlinear term after truncation (null: none)
+  const double2* forcing = nullptr;
 };
 
 void choose_chunks(Dims* d);

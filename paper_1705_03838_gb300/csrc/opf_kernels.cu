@@ -143,7 +143,12 @@ __global__ void __launch_bounds__(256) k_curl(Dims d, const double* __restrict__
     if (mean) nrx -= Ub * Ob;
     const double ntx = Ub * (-xi), nty = Ub * xr;
     Nlin[w] = double2{nrx - nty, nry + ntx};
-    Nlin[fs + w] = double2{nrx + nty, nry - ntx};
+    double2 nminus = double2{nrx + nty, nry - ntx};
+    if (d.rotate && mt == 1 && kk == d.K - 1) {  // Coriolis force of U z: N- = -2 U (Omega_y + i Omega_x)
+      nminus.x -= 2.0 * Ub * d.rot_y;
+      nminus.y -= 2.0 * Ub * d.rot_x;
+    }
+    Nlin[fs + w] = nminus;
     Nlin[2 * fs + w] = double2{Ob * urx, Ob * ury};
   }
   W6[0 * fs + w] = V{(T)urx, (T)ury};
@@ -214,6 +219,9 @@ void launch_zsynth(const Dims& d, const DevSetup& s, const FftPlan& pz, const do
 
 // ------------------------------------------------------------------ product (A3)
 
+__device__ __forceinline__ void sincos_pi(double x, double* s, double* c) { sincospi(x, s, c); }
+__device__ __forceinline__ void sincos_pi(float x, float* s, float* c) { sincospif(x, s, c); }
+
 template <typename V>
 __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* __restrict__ twth,
                                                  const V* __restrict__ Z6, V* __restrict__ ZN) {
@@ -270,8 +278,18 @@ __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* _
     const int q = e % nth, zr = e / nth;
     const V x0 = res[(zr * 3 + 0) * ld + q], x1 = res[(zr * 3 + 1) * ld + q], x2 = res[(zr * 3 + 2) * ld + q];
     const T ur = x0.x, ut = x0.y, uz = x1.x, wr = x1.y, wt = x2.x, wz = x2.y;
-    C[(zr * 2 + 0) * ld + q] = V{ut * wz - uz * wt, uz * wr - ur * wz};
-    C[(zr * 2 + 1) * ld + q] = V{ur * wt - ut * wr, (T)0};
+    T nr = ut * wz - uz * wt, nt = uz * wr - ur * wz, nz = ur * wt - ut * wr;
+    if (d.rotate) {  // Coriolis -2 Omega x u, Omega in cylindrical components at theta_q
+      T sn, cs;
+      sincos_pi((T)(2 * q) / (T)(d.m_p * nth), &sn, &cs);
+      const T o_r = (T)d.rot_x * cs + (T)d.rot_y * sn, o_t = -(T)d.rot_x * sn + (T)d.rot_y * cs;
+      const T o_z = (T)d.rot_z;
+      nr -= (T)2 * (o_t * uz - o_z * ut);
+      nt -= (T)2 * (o_z * ur - o_r * uz);
+      nz -= (T)2 * (o_r * ut - o_t * ur);
+    }
+    C[(zr * 2 + 0) * ld + q] = V{nr, nt};
+    C[(zr * 2 + 1) * ld + q] = V{nz, (T)0};
     if (cfl)
       cmax = fmax(cmax, fmax(fabs((double)ur) * inv_dr,
                              fmax(fabs((double)ut) * inv_rdt, fabs((double)uz + Ubase) * inv_dz)));
@@ -353,6 +371,15 @@ __global__ void __launch_bounds__(128) k_zanalysis(Dims d, FftPlan pz, const V* 
     const long o = ((long)m * d.N + n) * nk + kk;
     double2 np = double2{nrx - nty, nry + ntx};        // N+ = N_r + i N_theta
     double2 nm = double2{nrx + nty, nry - ntx};        // N- = N_r - i N_theta
+    if (d.forcing) {  // constant body force (shared by the trajectories of a group)
+      const double2 a = d.forcing[o], b = d.forcing[fs + o], c = d.forcing[2 * fs + o];
+      np.x += a.x;
+      np.y += a.y;
+      nm.x += b.x;
+      nm.y += b.y;
+      nz2.x += c.x;
+      nz2.y += c.y;
+    }
     if (Nlin) {  // terms linear in the perturbation, evaluated in FP64
       const double2 a = Nlin[o], b = Nlin[fs + o], c = Nlin[2 * fs + o];
       np.x += a.x;

@@ -136,6 +136,8 @@ def lib():
         L.opf_net_train_step.argtypes = [vp, vp, vp, vp, i, ctypes.c_float, ctypes.c_float, _dp]
         L.opf_nonlinear_noalloc.restype = i
         L.opf_nonlinear_noalloc.argtypes = [i, i, i, i, d, d, vp, vp, vp]
+        L.opf_set_forcing.restype = i
+        L.opf_set_forcing.argtypes = [vp, vp]
         L.opf_change_resolution.restype = i
         L.opf_change_resolution.argtypes = [i, i, i, vp, i, i, i, i, vp]
         L.opf_setup_query.restype = i
@@ -460,6 +462,15 @@ def opf_floquet(N, K, M, m_p, alpha, Re, states, T, s, kdim, nev, dt, eps=1e-7, 
                              ctypes.c_ulonglong(seed), None if sv is None else sv.ctypes.data,
                              er.ctypes.data_as(_dp), ei.ctypes.data_as(_dp), rs.ctypes.data_as(_dp)))
     return er + 1j * ei, rs
+
+
+def opf_set_forcing(h, forcing):
+    """Constant body force (state layout, components r, theta, z); None removes it."""
+    if forcing is None:
+        _check(lib().opf_set_forcing(h.ptr, None))
+        return
+    a = np.ascontiguousarray(forcing, dtype=np.complex128)
+    _check(lib().opf_set_forcing(h.ptr, a.ctypes.data))
 
 
 def opf_change_resolution(state, N2, K2, M2, m_p):
