@@ -218,6 +218,17 @@ int opf_nk_solve(int N, int K, int M, int m_p, double alpha, double Re, int coun
                  double* states, double* T, double* s, const opf_nk_opts* opts,
                  double* residual, int* iters);
 
+/* Multiple shooting (paper section 2: orbits may be split into sections):
+ * as opf_nk_solve, with each orbit split into S sections of duration T/S,
+ * each integrated as its own trajectory of the batched group.  Unknowns: the
+ * S section starts, T and s; residual Phi_{T/S}(u_q) - u_{q+1} (q < S-1) and
+ * sigma_s Phi_{T/S}(u_{S-1}) - u_0; phase conditions on u_0.  states:
+ * [count][S] host states (section starts, state layout) in/out; residual:
+ * |F| / |(u_0 .. u_{S-1})|.  S = 1 is single shooting. */
+int opf_nk_solve_ms(int N, int K, int M, int m_p, double alpha, double Re, int count, int S,
+                    double* states, double* T, double* s, const opf_nk_opts* opts, double* residual,
+                    int* iters);
+
 /* ---- Leading eigenvalues of linear maps: stability of invariant solutions
  * (the paper's Newton utility converges travelling waves and periodic orbits;
  * section 3.2 quotes the leading eigenvalue of one) --------------------------

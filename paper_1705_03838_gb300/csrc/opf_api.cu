@@ -1319,6 +1319,12 @@ int nk_residual(void* vctx, int cnt, const int* idx, double* const* x, double* c
 int nk_jv(void* vctx, int cnt, const int* idx, double* const* x, double* const* v, double* const* jv) {
   NkCtx* c = (NkCtx*)vctx;
   const long L = nk_state_len(c);
+  {  // a rejected trial may have left its period in the setup: back to the base point's
+    std::vector<double> Tb(cnt);
+    for (int j = 0; j < cnt; ++j) Tb[j] = c->T[idx[j]];
+    int rc0 = nk_set_periods(c, idx, cnt, Tb.data());
+    if (rc0) return rc0;
+  }
   std::vector<std::vector<double>> up(cnt, std::vector<double>(L));
   std::vector<double> eps(cnt);
   std::vector<double> tmp(c->ndof);
@@ -1414,6 +1420,251 @@ extern "C" int opf_nk_solve(int N, int K, int M, int m_p, double alpha, double R
       const double* xi = &x[(size_t)i * c->n];
       c->pk.unpack(xi, states + (size_t)i * L);
       long q = c->ndof;
+      if (!o->fix_T) T[i] = xi[q++];
+      if (!o->fix_s) s[i] = xi[q++];
+      if (residual) residual[i] = res[i];
+      if (iters) iters[i] = it[i];
+    }
+  }
+  runner_free(&c->run);
+  group_free(&c->g);
+  delete c;
+  return rc;
+}
+
+// ---- multiple shooting (section 2: the orbit is split into S sections, each
+// integrated over T/S as its own trajectory of the batched group).  Unknowns
+// per problem: the S section starts (u_0 .. u_{S-1}), then T and s unless
+// fixed.  Residual: F_q = Phi_{T/S}(u_q) - u_{q+1} (q < S-1),
+// F_{S-1} = sigma_s Phi_{T/S}(u_{S-1}) - u_0; phase conditions on section 0.
+// Problem i's section q is trajectory i*S + q.
+namespace {
+struct MsCtx {
+  NkCtx* c;
+  int S;
+  // per trajectory (i*S + q): packed base point, Phi(u_q) (the last one shifted),
+  // d/dt of it; per problem: d/ds of the shifted last section, du_0/dt, du_0/dz
+  std::vector<std::vector<double>> ubase, phi, dphi_dt, dphi_ds, du_dt, du_dz;
+};
+
+int ms_set_periods(MsCtx* m, const int* idx, int cnt, const double* Ts) {
+  NkCtx* c = m->c;
+  bool changed = false;
+  for (int j = 0; j < cnt; ++j)
+    for (int q = 0; q < m->S; ++q) {
+      const int t = idx[j] * m->S + q;
+      const double dt = Ts[j] / (m->S * c->nsteps);
+      if (dt != c->g.dt[t]) {
+        c->g.dt[t] = dt;
+        changed = true;
+      }
+    }
+  if (changed) return group_fill_setups(&c->g, false);
+  return OPF_OK;
+}
+
+int ms_residual(void* vctx, int cnt, const int* idx, double* const* x, double* const* f, int commit) {
+  MsCtx* m = (MsCtx*)vctx;
+  NkCtx* c = m->c;
+  const int S = m->S;
+  const long L = nk_state_len(c), nd = c->ndof;
+  std::vector<int> tr(cnt * S);
+  std::vector<std::vector<double>> u(cnt * S, std::vector<double>(L));
+  std::vector<double> Ts(cnt), ss(cnt);
+  for (int j = 0; j < cnt; ++j) {
+    long o = S * nd;
+    Ts[j] = c->o.fix_T ? c->T[idx[j]] : x[j][o++];
+    ss[j] = c->o.fix_s ? c->s[idx[j]] : x[j][o++];
+    if (!(Ts[j] > 0)) return fail(OPF_EINVAL, "nk: non-positive period");
+    for (int q = 0; q < S; ++q) {
+      tr[j * S + q] = idx[j] * S + q;
+      c->pk.unpack(x[j] + q * nd, u[j * S + q].data());
+    }
+  }
+  int rc = ms_set_periods(m, idx, cnt, Ts.data());
+  if (rc) return rc;
+  std::vector<std::vector<double>> v = u;
+  rc = nk_integrate(c, cnt * S, tr.data(), v, c->nsteps);
+  if (rc) return rc;
+  std::vector<double> w(L), pk(nd);
+  for (int j = 0; j < cnt; ++j) {
+    for (int q = 0; q < S; ++q) {
+      w = v[j * S + q];
+      if (q == S - 1) shift_state(*c, w.data(), ss[j], false);
+      c->pk.pack(w.data(), pk.data());
+      const double* next = x[j] + ((q + 1) % S) * nd;
+      for (long t = 0; t < nd; ++t) f[j][q * nd + t] = pk[t] - next[t];
+    }
+    for (long t = S * nd; t < c->n; ++t) f[j][t] = 0.0;
+  }
+  if (!commit) return OPF_OK;
+  std::vector<std::vector<double>> v1 = v, u1 = u;
+  rc = nk_integrate(c, cnt * S, tr.data(), v1, 1);  // one more step from each Phi(u_q)
+  if (rc) return rc;
+  rc = nk_integrate(c, cnt * S, tr.data(), u1, 1);  // one step from each u_q
+  if (rc) return rc;
+  for (int j = 0; j < cnt; ++j) {
+    const int i = idx[j];
+    c->T[i] = Ts[j];
+    c->s[i] = ss[j];
+    for (int q = 0; q < S; ++q) {
+      const int t = i * S + q, k = j * S + q;
+      const double dt = c->g.dt[t];
+      const bool last = q == S - 1;
+      w = v[k];
+      if (last) shift_state(*c, w.data(), ss[j], false);
+      m->phi[t].resize(nd);
+      c->pk.pack(w.data(), m->phi[t].data());
+      std::vector<double> a = v1[k];
+      for (long e = 0; e < L; ++e) a[e] = (a[e] - v[k][e]) / dt;
+      if (last) shift_state(*c, a.data(), ss[j], false);
+      m->dphi_dt[t].resize(nd);
+      c->pk.pack(a.data(), m->dphi_dt[t].data());
+      m->ubase[t].assign(x[j] + q * nd, x[j] + (q + 1) * nd);
+      if (last) {
+        std::vector<double> b = v[k];
+        shift_state(*c, b.data(), ss[j], true);
+        m->dphi_ds[i].resize(nd);
+        c->pk.pack(b.data(), m->dphi_ds[i].data());
+      }
+      if (q == 0) {
+        std::vector<double> e1 = u1[k];
+        for (long e = 0; e < L; ++e) e1[e] = (e1[e] - u[k][e]) / dt;
+        m->du_dt[i].resize(nd);
+        c->pk.pack(e1.data(), m->du_dt[i].data());
+        std::vector<double> zz = u[k];
+        shift_state(*c, zz.data(), 0.0, true);
+        m->du_dz[i].resize(nd);
+        c->pk.pack(zz.data(), m->du_dz[i].data());
+      }
+    }
+  }
+  return OPF_OK;
+}
+
+int ms_jv(void* vctx, int cnt, const int* idx, double* const* x, double* const* v, double* const* jv) {
+  MsCtx* m = (MsCtx*)vctx;
+  NkCtx* c = m->c;
+  const int S = m->S;
+  const long L = nk_state_len(c), nd = c->ndof;
+  {  // a rejected trial may have left its period in the setup: back to the base point's
+    std::vector<double> Tb(cnt);
+    for (int j = 0; j < cnt; ++j) Tb[j] = c->T[idx[j]];
+    int rc0 = ms_set_periods(m, idx, cnt, Tb.data());
+    if (rc0) return rc0;
+  }
+  std::vector<int> tr(cnt * S);
+  std::vector<std::vector<double>> up(cnt * S, std::vector<double>(L));
+  std::vector<double> eps(cnt * S), tmp(nd);
+  for (int j = 0; j < cnt; ++j)
+    for (int q = 0; q < S; ++q) {
+      const int t = idx[j] * S + q;
+      tr[j * S + q] = t;
+      const std::vector<double>& ub = m->ubase[t];
+      const double* d = v[j] + q * nd;
+      double un = 0.0, vn = 0.0;
+      for (long e = 0; e < nd; ++e) {
+        un += ub[e] * ub[e];
+        vn += d[e] * d[e];
+      }
+      const double ep = vn > 0 ? c->o.eps * std::sqrt(un / vn) : 1.0;
+      eps[j * S + q] = ep;
+      for (long e = 0; e < nd; ++e) tmp[e] = ub[e] + ep * d[e];
+      c->pk.unpack(tmp.data(), up[j * S + q].data());
+    }
+  int rc = nk_integrate(c, cnt * S, tr.data(), up, c->nsteps);
+  if (rc) return rc;
+  std::vector<double> pk(nd);
+  for (int j = 0; j < cnt; ++j) {
+    const int i = idx[j];
+    const double dT = c->o.fix_T ? 0.0 : v[j][S * nd];
+    const double ds = c->o.fix_s ? 0.0 : v[j][S * nd + (c->o.fix_T ? 0 : 1)];
+    for (int q = 0; q < S; ++q) {
+      const int t = i * S + q, k = j * S + q;
+      if (q == S - 1) shift_state(*c, up[k].data(), c->s[i], false);
+      c->pk.pack(up[k].data(), pk.data());
+      const double* dn = v[j] + ((q + 1) % S) * nd;
+      for (long e = 0; e < nd; ++e) {
+        double r = (pk[e] - m->phi[t][e]) / eps[k] - dn[e] + (dT / S) * m->dphi_dt[t][e];
+        if (q == S - 1) r += ds * m->dphi_ds[i][e];
+        jv[j][q * nd + e] = r;
+      }
+    }
+    double pt = 0.0, pz = 0.0;
+    for (long e = 0; e < nd; ++e) {
+      pt += m->du_dt[i][e] * v[j][e];
+      pz += m->du_dz[i][e] * v[j][e];
+    }
+    long o = S * nd;
+    if (!c->o.fix_T) jv[j][o++] = pt;
+    if (!c->o.fix_s) jv[j][o++] = pz;
+  }
+  return OPF_OK;
+}
+}  // namespace
+
+extern "C" int opf_nk_solve_ms(int N, int K, int M, int m_p, double alpha, double Re, int count, int S,
+                               double* states, double* T, double* s, const opf_nk_opts* o, double* residual,
+                               int* iters) {
+  if (count < 1 || S < 1 || !states || !T || !s || !o || !(o->dt > 0) || !(o->eps > 0))
+    return fail(OPF_EINVAL, "opf_nk_solve_ms: bad arguments");
+  for (int i = 0; i < count; ++i)
+    if (!(T[i] > 0)) return fail(OPF_EINVAL, "opf_nk_solve_ms: periods must be positive");
+  NkCtx* c = new NkCtx(N, K, M);
+  c->N = N;
+  c->K = K;
+  c->M = M;
+  c->m_p = m_p;
+  c->alpha = alpha;
+  c->count = count;
+  c->o = *o;
+  double Tmax = 0.0;
+  for (int i = 0; i < count; ++i) Tmax = std::max(Tmax, T[i]);
+  c->nsteps = std::max(1, (int)std::ceil(Tmax / S / o->dt - 1e-9));  // steps per section
+  const int ntr = count * S;
+  std::vector<double> Re_v(ntr, Re), dt_v(ntr);
+  for (int t = 0; t < ntr; ++t) dt_v[t] = T[t / S] / (S * c->nsteps);
+  int rc = group_build(&c->g, N, K, M, m_p, alpha, ntr, Re_v.data(), dt_v.data(), true);
+  if (rc == OPF_OK) rc = runner_init(&c->run);
+  if (rc != OPF_OK) {
+    group_free(&c->g);
+    runner_free(&c->run);
+    delete c;
+    return rc;
+  }
+  c->run.groups = {&c->g};
+  c->run.precision = o->precision;
+  c->ndof = c->pk.ndof;
+  c->n = S * c->ndof + (o->fix_T ? 0 : 1) + (o->fix_s ? 0 : 1);
+  c->T.assign(T, T + count);
+  c->s.assign(s, s + count);
+  MsCtx m{c, S, {}, {}, {}, {}, {}, {}};
+  m.ubase.resize(ntr);
+  m.phi.resize(ntr);
+  m.dphi_dt.resize(ntr);
+  m.dphi_ds.resize(count);
+  m.du_dt.resize(count);
+  m.du_dz.resize(count);
+  const long L = nk_state_len(c);
+  std::vector<double> x((size_t)count * c->n), scale(count);
+  for (int i = 0; i < count; ++i) {
+    double* xi = &x[(size_t)i * c->n];
+    for (int q = 0; q < S; ++q) c->pk.pack(states + ((size_t)i * S + q) * L, xi + q * c->ndof);
+    long q = S * c->ndof;
+    if (!o->fix_T) xi[q++] = T[i];
+    if (!o->fix_s) xi[q++] = s[i];
+    double nn = 0.0;
+    for (long t = 0; t < S * c->ndof; ++t) nn += xi[t] * xi[t];
+    scale[i] = std::sqrt(nn);
+  }
+  std::vector<double> res(count, 0.0);
+  std::vector<int> it(count, 0);
+  rc = opf_nk_core((int)c->n, count, x.data(), scale.data(), ms_residual, ms_jv, &m, o, res.data(), it.data());
+  if (rc == OPF_OK) {
+    for (int i = 0; i < count; ++i) {
+      const double* xi = &x[(size_t)i * c->n];
+      for (int q = 0; q < S; ++q) c->pk.unpack(xi + q * c->ndof, states + ((size_t)i * S + q) * L);
+      long q = S * c->ndof;
       if (!o->fix_T) T[i] = xi[q++];
       if (!o->fix_s) s[i] = xi[q++];
       if (residual) residual[i] = res[i];

@@ -113,6 +113,9 @@ def lib():
         L.opf_nk_solve.restype = i
         L.opf_nk_solve.argtypes = [i, i, i, i, d, d, i, vp, _dp, _dp, ctypes.POINTER(NkOpts), _dp,
                                    ctypes.POINTER(i)]
+        L.opf_nk_solve_ms.restype = i
+        L.opf_nk_solve_ms.argtypes = [i, i, i, i, d, d, i, i, vp, _dp, _dp, ctypes.POINTER(NkOpts), _dp,
+                                      ctypes.POINTER(i)]
         L.opf_arnoldi_core.restype = i
         L.opf_arnoldi_core.argtypes = [i, i, _dp, i, i, LINEAR_MAP, vp, _dp, _dp, _dp, ctypes.POINTER(i)]
         L.opf_floquet.restype = i
@@ -480,6 +483,21 @@ def opf_change_resolution(state, N2, K2, M2, m_p):
     out = np.empty((3, M2, 2 * K2 - 1, N2), dtype=np.complex128)
     _check(lib().opf_change_resolution(N1, (nk1 + 1) // 2, M1, a.ctypes.data, N2, K2, M2, m_p, out.ctypes.data))
     return out
+
+
+def opf_nk_solve_ms(N, K, M, m_p, alpha, Re, sections, T, s, **opts):
+    """Multiple shooting: sections[i] is the list of S section starts of
+    guess i.  Returns (sections, T, s, relative residuals, Newton iterations)."""
+    count, S = len(sections), len(sections[0])
+    st = np.ascontiguousarray(np.stack([np.stack(x) for x in sections]), dtype=np.complex128)
+    Ta = np.ascontiguousarray(T, dtype=np.float64).copy()
+    sa = np.ascontiguousarray(s, dtype=np.float64).copy()
+    res = np.zeros(count)
+    it = (ctypes.c_int * count)()
+    o = nk_opts(**opts)
+    _check(lib().opf_nk_solve_ms(N, K, M, m_p, alpha, Re, count, S, st.ctypes.data, Ta.ctypes.data_as(_dp),
+                                 sa.ctypes.data_as(_dp), ctypes.byref(o), res.ctypes.data_as(_dp), it))
+    return [list(x) for x in st], Ta, sa, res, np.array(it[:])
 
 
 class NetHandle:
