@@ -76,6 +76,7 @@ struct Group {
   // setup-arena offsets (same for every trajectory), for in-place rebuilds
   size_t o_prm = 0, o_rinv = 0, o_d1 = 0, o_wq = 0, o_hop = 0, o_luH = 0, o_luP = 0;
   size_t o_basis = 0, o_ainv = 0, o_G = 0, o_twz = 0, o_twt = 0, o_twz32 = 0, o_twt32 = 0;
+  size_t o_r = 0, o_d1f = 0;
 
   template <typename P>
   P* at(P* p, int b) const {
@@ -100,6 +101,8 @@ struct Group {
     s.tw_th = sh(s.tw_th);
     s.tw_z32 = sh(s.tw_z32);
     s.tw_th32 = sh(s.tw_th32);
+    s.r = sh(s.r);
+    s.d1f = sh(s.d1f);
     return s;
   }
   // launch dimensions of trajectory b alone (pointers offset on the host)
@@ -188,6 +191,8 @@ int group_fill_setups(Group* g, bool first) {
   g->o_twt = pl.add(d.nth * sizeof(double2));
   g->o_twz32 = pl.add(d.nz * sizeof(float2));
   g->o_twt32 = pl.add(d.nth * sizeof(float2));
+  g->o_r = pl.add(s0.r.size() * 8);
+  g->o_d1f = pl.add((s0.d1.size() + s0.rinv.size()) * sizeof(float));
   if (first) {
     g->pstride = pl.off;
     if (cudaMalloc((void**)&g->parena, g->pstride * nsetup) != cudaSuccess)
@@ -227,6 +232,10 @@ int group_fill_setups(Group* g, bool first) {
     put(g->o_twt, twt.data(), d.nth * sizeof(double2));
     put(g->o_twz32, twz32.data(), d.nz * sizeof(float2));
     put(g->o_twt32, twt32.data(), d.nth * sizeof(float2));
+    put(g->o_r, s.r.data(), s.r.size() * 8);
+    std::vector<float> d1f(s.d1.begin(), s.d1.end());  // FP32 stencils, then FP32 1/r
+    d1f.insert(d1f.end(), s.rinv.begin(), s.rinv.end());
+    put(g->o_d1f, d1f.data(), d1f.size() * sizeof(float));
     CU(cudaMemcpy(g->parena + (size_t)b * g->pstride, host.data(), g->pstride, cudaMemcpyHostToDevice));
   }
   return OPF_OK;
@@ -283,6 +292,8 @@ int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, con
   g->ds.tw_th = (double2*)(P + g->o_twt);
   g->ds.tw_z32 = (float2*)(P + g->o_twz32);
   g->ds.tw_th32 = (float2*)(P + g->o_twt32);
+  g->ds.r = (double*)(P + g->o_r);
+  g->ds.d1f = (float*)(P + g->o_d1f);
   d.ps = g->shared_setup ? 0 : (long)g->pstride;
   d.prm = g->ds.prm;
 

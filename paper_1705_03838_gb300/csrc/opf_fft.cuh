@@ -1,5 +1,5 @@
 // Batched mixed-radix FFTs in shared memory (Stockham autosort, radices
-// 2, 3, 4, 5), used for the Eq. 1 transforms on the 3K x 3M grid.
+// 2, 3, 4, 5, 8), used for the Eq. 1 transforms on the 3K x 3M grid.
 //
 // A block transforms `batch` sequences of length p.n stored at stride `ld`
 // (complex elements) in buffer a, ping-ponging with buffer b; the returned
@@ -8,6 +8,8 @@
 // tw[t] = e^{+2 pi i t/n}, t < n, in shared or global memory.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "opf_internal.h"
 
@@ -54,6 +56,25 @@ __device__ __forceinline__ void butterfly(V* v, int sign) {
     v[0] = cadd(v[0], t1);
     v[1] = cadd(base, rot);
     v[2] = csub(base, rot);
+  } else if constexpr (R == 8) {
+    // two radix-4 transforms of the even and odd points, joined by the
+    // eighth roots of unity w^q = e^{sign 2 pi i q/8}
+    V e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    butterfly<4>(e, sign);
+    butterfly<4>(o, sign);
+    const T h = (T)0.70710678118654752440;  // 1 / sqrt(2)
+    const T s = (T)sign;
+    const V o1 = V{h * (o[1].x - s * o[1].y), h * (o[1].y + s * o[1].x)};
+    const V o2 = cmul_si(o[2], sign);
+    const V o3 = V{-h * (o[3].x + s * o[3].y), h * (s * o[3].x - o[3].y)};
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], o1);
+    v[5] = csub(e[1], o1);
+    v[2] = cadd(e[2], o2);
+    v[6] = csub(e[2], o2);
+    v[3] = cadd(e[3], o3);
+    v[7] = csub(e[3], o3);
   } else if constexpr (R == 5) {
     const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;
     const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;
@@ -116,6 +137,82 @@ __device__ V* block_fft(V* a, V* b, int batch, int ld, const FftPlan& p, const V
     Ns *= R;
   }
   return a;
+}
+
+// ---------------------------------------------------------------------------
+// The same Stockham transform for a length N known at compile time (the
+// common grid lengths 3K, 3M): radices, strides and the twiddle stride are
+// constants, so the index arithmetic folds into shifts and multiply-highs, the
+// first stage (all twiddles 1) skips its multiplications, and radix 8 cuts the
+// number of shared-memory passes.  Same conventions as block_fft.
+template <int R, int N, int NS, int SIGN, typename V>
+__device__ __forceinline__ void fft_stage_c(const V* __restrict__ a, V* __restrict__ b, int ld, int batch,
+                                            const V* __restrict__ tw) {
+  constexpr int nR = N / R, step = N / (NS * R);
+  const int work = batch * nR;
+  for (int w = threadIdx.x; w < work; w += blockDim.x) {
+    const int bt = w / nR;
+    const int j = w - bt * nR;
+    const int jm = j % NS;
+    const V* src = a + bt * ld;
+    V* dst = b + bt * ld;
+    V v[R];
+    v[0] = src[j];
+#pragma unroll
+    for (int q = 1; q < R; ++q) {
+      if constexpr (NS == 1) {
+        v[q] = src[j + q * nR];
+      } else {
+        V t = tw[q * jm * step];
+        if constexpr (SIGN < 0) t.y = -t.y;
+        v[q] = cmul(src[j + q * nR], t);
+      }
+    }
+    butterfly<R>(v, SIGN);
+    const int d0 = (j / NS) * NS * R + jm;
+#pragma unroll
+    for (int q = 0; q < R; ++q) dst[d0 + q * NS] = v[q];
+  }
+}
+
+template <int N, int NS, int SIGN, int R, int... Rest, typename V>
+__device__ __forceinline__ V* fft_stages_c(V* a, V* b, int ld, int batch, const V* tw) {
+  fft_stage_c<R, N, NS, SIGN>(a, b, ld, batch, tw);
+  __syncthreads();
+  if constexpr (sizeof...(Rest) == 0) {
+    return b;
+  } else {
+    return fft_stages_c<N, NS * R, SIGN, Rest...>(b, a, ld, batch, tw);
+  }
+}
+
+// Lengths with a compiled plan (others use block_fft).
+__host__ __device__ constexpr bool fft_length_compiled(int n) {
+  return n == 48 || n == 72 || n == 96 || n == 192 || n == 384;
+}
+
+template <int N, int SIGN, typename V>
+__device__ __forceinline__ V* block_fft_c(V* a, V* b, int batch, int ld, const V* tw) {
+  static_assert(fft_length_compiled(N), "no compiled plan for this length");
+  if constexpr (N == 48) return fft_stages_c<48, 1, SIGN, 4, 4, 3>(a, b, ld, batch, tw);
+  else if constexpr (N == 72) return fft_stages_c<72, 1, SIGN, 8, 3, 3>(a, b, ld, batch, tw);
+  else if constexpr (N == 96) return fft_stages_c<96, 1, SIGN, 8, 4, 3>(a, b, ld, batch, tw);
+  else if constexpr (N == 192) return fft_stages_c<192, 1, SIGN, 8, 8, 3>(a, b, ld, batch, tw);
+  else return fft_stages_c<384, 1, SIGN, 8, 4, 4, 3>(a, b, ld, batch, tw);
+}
+
+// Calls f(std::integral_constant<int, n>) for a compiled length n, else
+// f(std::integral_constant<int, 0>) (runtime plan).
+template <class F>
+inline void with_fft_length(int n, F&& f) {
+  switch (n) {
+    case 48: f(std::integral_constant<int, 48>{}); break;
+    case 72: f(std::integral_constant<int, 72>{}); break;
+    case 96: f(std::integral_constant<int, 96>{}); break;
+    case 192: f(std::integral_constant<int, 192>{}); break;
+    case 384: f(std::integral_constant<int, 384>{}); break;
+    default: f(std::integral_constant<int, 0>{}); break;
+  }
 }
 
 }  // namespace opf

@@ -66,6 +66,8 @@ struct DevSetup {
   double2* tw_th = nullptr;  // e^{+2 pi i t / nth}
   float2* tw_z32 = nullptr;
   float2* tw_th32 = nullptr;
+  double* r = nullptr;    // radial points (null where the split curl is not used)
+  float* d1f = nullptr;   // d1 in FP32, then 1/r in FP32 ([2][N][9] + [N])
 };
 
 // Spectral fields are stored [field][m][n][kk] (kk = k + K - 1 fastest).

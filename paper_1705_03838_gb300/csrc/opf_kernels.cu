@@ -76,107 +76,161 @@ void launch_internal_to_abi(const Dims& d, const double2* U, double2* abi, int, 
 }
 
 // ------------------------------------------------------------------ curl (A1)
-// SPLIT: the laminar base flow U = (1 - r^2) z, Omega = 2r theta is removed
-// in FP64 (W6 then holds u', w'), and the terms linear in the perturbation,
-// U x w' + u' x Omega (+ U x Omega on (0,0)), are evaluated here per mode in
-// FP64 -- they are diagonal in r -- and written to Nlin in +- form.
+// A block takes kCurlKC consecutive kk of one m over all N radial points: the
+// block reads and combines each u+-, u_z value once (u_r, u_theta formed in
+// FP64) into shared memory, and the 9-point radial stencils read their
+// neighbours from there.
+//
+// SPLIT (mixed precision): the laminar base flow U = (1 - r^2) z,
+// Omega = 2r theta is removed in FP64 (W6 then holds u', w' in FP32), and the
+// terms linear in the perturbation, U x w' + u' x Omega (+ U x Omega on
+// (0,0)), are evaluated here per mode in FP64 -- they are diagonal in r -- and
+// written to Nlin in +- form.  FP64 arithmetic is kept to what Nlin needs (the
+// u_z derivative, w_r, w_theta); the u_theta derivative feeds only w_z, which
+// goes to the FP32 product, and is taken in FP32 from an FP32 copy of the
+// u_theta tile.  Without SPLIT everything is FP64.
+constexpr int kCurlKC = 4;
+
+size_t curl_smem(const Dims& d) { return (size_t)d.N * kCurlKC * (3 * sizeof(double2) + sizeof(float2)); }
+
 template <typename V, bool SPLIT>
-__global__ void __launch_bounds__(256) k_curl(Dims d, const double* __restrict__ d1,
+__global__ void __launch_bounds__(128) k_curl(Dims d, const double* __restrict__ d1,
+                                              const float* __restrict__ d1f, const double* __restrict__ rr,
                                               const double* __restrict__ rinv,
                                               const double2* __restrict__ U, V* __restrict__ W6,
                                               double2* __restrict__ Nlin) {
   using T = typename Scalar<V>::T;
-  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= d.F) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int KC = kCurlKC;
+  const int N = d.N, nk = d.nk;
+  double2* s_uz = (double2*)smraw;              // [N][KC] u_z
+  double2* s_ur = s_uz + N * KC;                // [N][KC] u_r
+  double2* s_ut = s_ur + N * KC;                // [N][KC] u_theta
+  float2* s_ut32 = (float2*)(s_ut + N * KC);    // [N][KC] u_theta in FP32 (SPLIT)
   d1 = bofs(d1, d.ps);
+  d1f = bofs(d1f, d.ps);
+  rr = bofs(rr, d.ps);
   rinv = bofs(rinv, d.ps);
   U = bofs(U, d.ss);
   W6 = bofs(W6, d.ss);
   Nlin = bofs(Nlin, d.ss);
-  const int kk = idx % d.nk;
-  const long t = idx / d.nk;
-  const int n = t % d.N;
-  const int m = t / d.N;
-  const int N = d.N, nk = d.nk;
+  const int m = blockIdx.y, kk0 = blockIdx.x * KC;
   const long fs = d.F;
+  const double2* up = U + (long)m * N * nk;
+  for (int e = threadIdx.x; e < N * KC; e += blockDim.x) {
+    const int c = e % KC, n = e / KC, kk = kk0 + c;
+    if (kk >= nk) continue;  // columns past nk are never read
+    const long o = (long)n * nk + kk;
+    const double2 a = up[o], b = up[fs + o];
+    s_uz[e] = up[2 * fs + o];
+    s_ur[e] = double2{0.5 * (a.x + b.x), 0.5 * (a.y + b.y)};
+    const double2 ut = double2{0.5 * (a.y - b.y), -0.5 * (a.x - b.x)};
+    s_ut[e] = ut;
+    if constexpr (SPLIT) s_ut32[e] = float2{(float)ut.x, (float)ut.y};
+  }
+  __syncthreads();
   const int mt = d.m_p * m;
-  const double ak = d.alpha * (kk - (d.K - 1));
   const int ps = mt & 1, pv = ps ^ 1;
-  const double2* up = U + ((long)m * N) * nk + kk;
-  const double2* um = up + fs;
-  const double2* uz = up + 2 * fs;
-  const int lo = row_lo_d(n, N);
-  const double* wv = d1 + ((long)pv * N + n) * 9;
-  const double* ws = d1 + ((long)ps * N + n) * 9;
-  double dtx = 0, dty = 0, dzx = 0, dzy = 0;  // d/dr of u_theta and u_z
+  for (int e = threadIdx.x; e < N * KC; e += blockDim.x) {
+    const int c = e % KC, n = e / KC, kk = kk0 + c;
+    if (kk >= nk) continue;
+    const int lo = row_lo_d(n, N);
+    const double* ws = d1 + ((long)ps * N + n) * 9;
+    double dzx = 0, dzy = 0;  // d/dr of u_z (FP64)
+    T dtx = 0, dty = 0;       // d/dr of u_theta
+    if constexpr (SPLIT) {
+      const float* wv = d1f + ((long)pv * N + n) * 9;
 #pragma unroll
-  for (int q = 0; q < 9; ++q) {
-    const long o = (long)(lo + q) * nk;
-    const double2 a = up[o], b = um[o], c = uz[o];
-    dtx += wv[q] * 0.5 * (a.y - b.y);
-    dty -= wv[q] * 0.5 * (a.x - b.x);
-    dzx += ws[q] * c.x;
-    dzy += ws[q] * c.y;
-  }
-  const long o = (long)n * nk;
-  const double2 a = up[o], b = um[o], c = uz[o];
-  const double urx = 0.5 * (a.x + b.x), ury = 0.5 * (a.y + b.y);
-  const double utx = 0.5 * (a.y - b.y), uty = -0.5 * (a.x - b.x);
-  const double ri = rinv[n];
-  // w_r = i (m~ u_z / r - ak u_theta)
-  const double xr = mt * ri * c.x - ak * utx, xi = mt * ri * c.y - ak * uty;
-  // w_theta = i ak u_r - d_r u_z
-  const double wtx = -ak * ury - dzx, wty = ak * urx - dzy;
-  // w_z = d_r u_theta + u_theta / r - i m~ u_r / r
-  const double wzx = dtx + ri * utx + mt * ri * ury, wzy = dty + ri * uty - mt * ri * urx;
-  const long w = ((long)m * N + n) * nk + kk;
-  double uzx = c.x, uzy = c.y, wtx2 = wtx, wty2 = wty;
-  if constexpr (SPLIT) {
-    const double r = 1.0 / ri, Ub = 1.0 - r * r, Ob = 2.0 * r;
-    const bool mean = (m == 0 && kk == d.K - 1);
-    if (mean) {
-      uzx -= Ub;
-      wtx2 -= Ob;
+      for (int q = 0; q < 9; ++q) {
+        const int o = (lo + q) * KC + c;
+        const double2 z = s_uz[o];
+        const float2 t = s_ut32[o];
+        dzx = fma(ws[q], z.x, dzx);
+        dzy = fma(ws[q], z.y, dzy);
+        dtx = fmaf(wv[q], t.x, dtx);
+        dty = fmaf(wv[q], t.y, dty);
+      }
+    } else {
+      const double* wv = d1 + ((long)pv * N + n) * 9;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const int o = (lo + q) * KC + c;
+        const double2 z = s_uz[o], t = s_ut[o];
+        dzx = fma(ws[q], z.x, dzx);
+        dzy = fma(ws[q], z.y, dzy);
+        dtx = fma(wv[q], t.x, dtx);
+        dty = fma(wv[q], t.y, dty);
+      }
     }
-    // N_r = -U w'_t - Omega u'_z, N_t = U w'_r, N_z = Omega u'_r
-    double nrx = -Ub * wtx2 - Ob * uzx, nry = -Ub * wty2 - Ob * uzy;
-    if (mean) nrx -= Ub * Ob;
-    const double ntx = Ub * (-xi), nty = Ub * xr;
-    Nlin[w] = double2{nrx - nty, nry + ntx};
-    double2 nminus = double2{nrx + nty, nry - ntx};
-    if (d.rotate && mt == 1 && kk == d.K - 1) {  // Coriolis force of U z: N- = -2 U (Omega_y + i Omega_x)
-      nminus.x -= 2.0 * Ub * d.rot_y;
-      nminus.y -= 2.0 * Ub * d.rot_x;
+    const double2 ur = s_ur[e], ut = s_ut[e], uz = s_uz[e];
+    const double ri = rinv[n];
+    const double ak = d.alpha * (kk - (d.K - 1));
+    const double mri = mt * ri;
+    // w_r = i (m~ u_z / r - ak u_theta)
+    const double xr = mri * uz.x - ak * ut.x, xi = mri * uz.y - ak * ut.y;
+    // w_theta = i ak u_r - d_r u_z
+    double wtx = -ak * ur.y - dzx, wty = ak * ur.x - dzy;
+    const long w = ((long)m * N + n) * nk + kk;
+    double uzx = uz.x;
+    if constexpr (SPLIT) {
+      const double r = rr[n], Ub = 1.0 - r * r, Ob = 2.0 * r;
+      const bool mean = (m == 0 && kk == d.K - 1);
+      if (mean) {
+        uzx -= Ub;
+        wtx -= Ob;
+      }
+      // N_r = -U w'_t - Omega u'_z, N_t = U w'_r, N_z = Omega u'_r
+      double nrx = -Ub * wtx - Ob * uzx, nry = -Ub * wty - Ob * uz.y;
+      if (mean) nrx -= Ub * Ob;
+      const double ntx = Ub * (-xi), nty = Ub * xr;
+      Nlin[w] = double2{nrx - nty, nry + ntx};
+      double2 nminus = double2{nrx + nty, nry - ntx};
+      if (d.rotate && mt == 1 && kk == d.K - 1) {  // Coriolis force of U z: N- = -2 U (Omega_y + i Omega_x)
+        nminus.x -= 2.0 * Ub * d.rot_y;
+        nminus.y -= 2.0 * Ub * d.rot_x;
+      }
+      Nlin[fs + w] = nminus;
+      Nlin[2 * fs + w] = double2{Ob * ur.x, Ob * ur.y};
+      // w_z = d_r u_theta + u_theta / r - i m~ u_r / r, in FP32
+      const float ri32 = d1f[2 * 9 * N + n], mri32 = (float)mt * ri32;
+      const float2 ut32 = s_ut32[e];
+      const float urx = (float)ur.x, ury = (float)ur.y;
+      W6[0 * fs + w] = float2{urx, ury};
+      W6[1 * fs + w] = ut32;
+      W6[2 * fs + w] = float2{(float)uzx, (float)uz.y};
+      W6[3 * fs + w] = float2{(float)(-xi), (float)xr};
+      W6[4 * fs + w] = float2{(float)wtx, (float)wty};
+      W6[5 * fs + w] = float2{fmaf(mri32, ury, fmaf(ri32, ut32.x, dtx)), fmaf(-mri32, urx, fmaf(ri32, ut32.y, dty))};
+    } else {
+      W6[0 * fs + w] = ur;
+      W6[1 * fs + w] = ut;
+      W6[2 * fs + w] = uz;
+      W6[3 * fs + w] = V{-xi, xr};
+      W6[4 * fs + w] = V{wtx, wty};
+      W6[5 * fs + w] = V{dtx + ri * ut.x + mri * ur.y, dty + ri * ut.y - mri * ur.x};
     }
-    Nlin[fs + w] = nminus;
-    Nlin[2 * fs + w] = double2{Ob * urx, Ob * ury};
   }
-  W6[0 * fs + w] = V{(T)urx, (T)ury};
-  W6[1 * fs + w] = V{(T)utx, (T)uty};
-  W6[2 * fs + w] = V{(T)uzx, (T)uzy};
-  W6[3 * fs + w] = V{(T)(-xi), (T)xr};
-  W6[4 * fs + w] = V{(T)wtx2, (T)wty2};
-  W6[5 * fs + w] = V{(T)wzx, (T)wzy};
 }
 
 void launch_curl(const Dims& d, const DevSetup& s, const double2* U, double2* W6, cudaStream_t st) {
-  dim3 g((unsigned)((d.F + 255) / 256), 1, d.B);
-  k_curl<double2, false><<<g, 256, 0, st>>>(d, s.d1, s.rinv, U, W6, nullptr);
+  dim3 g((unsigned)((d.nk + kCurlKC - 1) / kCurlKC), d.M, d.B);
+  k_curl<double2, false><<<g, 128, curl_smem(d), st>>>(d, s.d1, nullptr, nullptr, s.rinv, U, W6, nullptr);
 }
 
 void launch_curl_split32(const Dims& d, const DevSetup& s, const double2* U, float2* W6,
                          double2* Nlin, cudaStream_t st) {
-  dim3 g((unsigned)((d.F + 255) / 256), 1, d.B);
-  k_curl<float2, true><<<g, 256, 0, st>>>(d, s.d1, s.rinv, U, W6, Nlin);
+  dim3 g((unsigned)((d.nk + kCurlKC - 1) / kCurlKC), d.M, d.B);
+  k_curl<float2, true><<<g, 128, curl_smem(d), st>>>(d, s.d1, s.d1f, s.r, s.rinv, U, W6, Nlin);
 }
 
 // ------------------------------------------------------------------ z synthesis (A2)
 
-template <typename V>
+// NZ > 0: the z length 3K is the compile-time constant NZ (compiled plan).
+template <typename V, int NZ>
 __global__ void __launch_bounds__(128) k_zsynth(Dims d, FftPlan pz, const V* __restrict__ twz,
                                                 const V* __restrict__ W6, V* __restrict__ Z6) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int nz = d.nz, ld = nz + 1, MC = d.mcz;
+  const int nz = NZ > 0 ? NZ : d.nz, ld = nz + 1, MC = d.mcz;
   V* A = (V*)smraw;
   V* B = A + MC * ld;
   V* tw = B + MC * ld;
@@ -195,7 +249,9 @@ __global__ void __launch_bounds__(128) k_zsynth(Dims d, FftPlan pz, const V* __r
     A[mc * ld + z] = v;
   }
   __syncthreads();
-  const V* res = block_fft(A, B, MC, ld, pz, tw, +1);
+  const V* res;
+  if constexpr (NZ > 0) res = block_fft_c<NZ, +1>(A, B, MC, ld, tw);
+  else res = block_fft(A, B, MC, ld, pz, tw, +1);
   const int mcn = min(MC, d.M - m0);
   for (int e = threadIdx.x; e < mcn * nz; e += blockDim.x) {
     const int mc = e % mcn, z = e / mcn;
@@ -208,13 +264,19 @@ size_t zsynth_smem(const Dims& d, int mc, size_t vb) { return (2 * (size_t)mc * 
 void launch_zsynth32(const Dims& d, const DevSetup& s, const FftPlan& pz, const float2* W6,
                      float2* Z6, cudaStream_t st) {
   dim3 g((d.M + d.mcz - 1) / d.mcz, d.N * 6, d.B);
-  k_zsynth<float2><<<g, 128, zsynth_smem(d, d.mcz, sizeof(float2)), st>>>(d, pz, s.tw_z32, W6, Z6);
+  const size_t sm = zsynth_smem(d, d.mcz, sizeof(float2));
+  with_fft_length(d.nz, [&](auto n) {
+    k_zsynth<float2, decltype(n)::value><<<g, 128, sm, st>>>(d, pz, s.tw_z32, W6, Z6);
+  });
 }
 
 void launch_zsynth(const Dims& d, const DevSetup& s, const FftPlan& pz, const double2* W6,
                    double2* Z6, cudaStream_t st) {
   dim3 g((d.M + d.mcz - 1) / d.mcz, d.N * 6, d.B);
-  k_zsynth<double2><<<g, 128, zsynth_smem(d, d.mcz, sizeof(double2)), st>>>(d, pz, s.tw_z, W6, Z6);
+  const size_t sm = zsynth_smem(d, d.mcz, sizeof(double2));
+  with_fft_length(d.nz, [&](auto n) {
+    k_zsynth<double2, decltype(n)::value><<<g, 128, sm, st>>>(d, pz, s.tw_z, W6, Z6);
+  });
 }
 
 // ------------------------------------------------------------------ product (A3)
@@ -222,12 +284,13 @@ void launch_zsynth(const Dims& d, const DevSetup& s, const FftPlan& pz, const do
 __device__ __forceinline__ void sincos_pi(double x, double* s, double* c) { sincospi(x, s, c); }
 __device__ __forceinline__ void sincos_pi(float x, float* s, float* c) { sincospif(x, s, c); }
 
-template <typename V>
+// NTH > 0: the theta length 3M is the compile-time constant NTH.
+template <typename V, int NTH>
 __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* __restrict__ twth,
                                                  const V* __restrict__ Z6, V* __restrict__ ZN) {
   using T = typename Scalar<V>::T;
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int nth = d.nth, ld = nth, M = d.M;
+  const int nth = NTH > 0 ? NTH : d.nth, ld = nth, M = d.M;
   const int ZC = d.zc;
   V* A = (V*)smraw;            // 3 * ZC sequences
   V* B = A + 3 * ZC * ld;      // 3 * ZC sequences
@@ -256,7 +319,9 @@ __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* _
     A[(zr * 3 + pr) * ld + q] = v;
   }
   __syncthreads();
-  V* res = block_fft(A, B, 3 * zc, ld, pth, tw, +1);
+  V* res;
+  if constexpr (NTH > 0) res = block_fft_c<NTH, +1>(A, B, 3 * zc, ld, tw);
+  else res = block_fft(A, B, 3 * zc, ld, pth, tw, +1);
   V* C = (res == A) ? B : A;
   // CFL number of this radial plane (optional): max over the grid of
   // |u_r|/dr, |u_t|/(r dtheta), |u_z|/dz for the TOTAL velocity (the FP32
@@ -301,7 +366,9 @@ __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* _
   }
   __syncthreads();
   V* D = (C == A) ? B : A;
-  const V* out = block_fft(C, D, 2 * zc, ld, pth, tw, -1);
+  const V* out;
+  if constexpr (NTH > 0) out = block_fft_c<NTH, -1>(C, D, 2 * zc, ld, tw);
+  else out = block_fft(C, D, 2 * zc, ld, pth, tw, -1);
   for (int e = threadIdx.x; e < zc * M; e += blockDim.x) {
     const int m = e % M, zr = e / M;
     const V y = out[(zr * 2 + 0) * ld + m];
@@ -320,22 +387,28 @@ size_t product_smem(const Dims& d, int zc, size_t vb) { return (2 * 3 * (size_t)
 void launch_product32(const Dims& d, const DevSetup& s, const FftPlan& pth, const float2* Z6,
                       float2* ZN, cudaStream_t st) {
   dim3 g((d.nz + d.zc - 1) / d.zc, d.N, d.B);
-  k_product<float2><<<g, 128, product_smem(d, d.zc, sizeof(float2)), st>>>(d, pth, s.tw_th32, Z6, ZN);
+  const size_t sm = product_smem(d, d.zc, sizeof(float2));
+  with_fft_length(d.nth, [&](auto n) {
+    k_product<float2, decltype(n)::value><<<g, 128, sm, st>>>(d, pth, s.tw_th32, Z6, ZN);
+  });
 }
 
 void launch_product(const Dims& d, const DevSetup& s, const FftPlan& pth, const double2* Z6,
                     double2* ZN, cudaStream_t st) {
   dim3 g((d.nz + d.zc - 1) / d.zc, d.N, d.B);
-  k_product<double2><<<g, 128, product_smem(d, d.zc, sizeof(double2)), st>>>(d, pth, s.tw_th, Z6, ZN);
+  const size_t sm = product_smem(d, d.zc, sizeof(double2));
+  with_fft_length(d.nth, [&](auto n) {
+    k_product<double2, decltype(n)::value><<<g, 128, sm, st>>>(d, pth, s.tw_th, Z6, ZN);
+  });
 }
 
 // ------------------------------------------------------------------ z analysis (A4)
-template <typename V>
+template <typename V, int NZ>
 __global__ void __launch_bounds__(128) k_zanalysis(Dims d, FftPlan pz, const V* __restrict__ twz,
                                                    const V* __restrict__ ZN, const double2* __restrict__ Nlin,
                                                    double2* __restrict__ Nout) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int nz = d.nz, ld = nz + 1, M = d.M, K = d.K, nk = d.nk;
+  const int nz = NZ > 0 ? NZ : d.nz, ld = nz + 1, M = d.M, K = d.K, nk = d.nk;
   const int MC = d.mca;
   V* A = (V*)smraw;
   V* B = A + 3 * MC * ld;
@@ -356,7 +429,9 @@ __global__ void __launch_bounds__(128) k_zanalysis(Dims d, FftPlan pz, const V* 
     A[(f * MC + mc) * ld + z] = v;
   }
   __syncthreads();
-  const V* res = block_fft(A, B, 3 * MC, ld, pz, tw, -1);
+  const V* res;
+  if constexpr (NZ > 0) res = block_fft_c<NZ, -1>(A, B, 3 * MC, ld, tw);
+  else res = block_fft(A, B, 3 * MC, ld, pz, tw, -1);
   const double sc = 1.0 / ((double)nz * d.nth);
   const long fs = d.F;
   for (int e = threadIdx.x; e < mcn * nk; e += blockDim.x) {
@@ -402,15 +477,19 @@ size_t zanalysis_smem(const Dims& d, int mc, size_t vb) {
 void launch_zanalysis(const Dims& d, const DevSetup& s, const FftPlan& pz, const double2* ZN,
                       double2* Nout, cudaStream_t st) {
   dim3 g((d.M + d.mca - 1) / d.mca, d.N, d.B);
-  k_zanalysis<double2><<<g, 128, zanalysis_smem(d, d.mca, sizeof(double2)), st>>>(d, pz, s.tw_z, ZN, nullptr,
-                                                                                  Nout);
+  const size_t sm = zanalysis_smem(d, d.mca, sizeof(double2));
+  with_fft_length(d.nz, [&](auto n) {
+    k_zanalysis<double2, decltype(n)::value><<<g, 128, sm, st>>>(d, pz, s.tw_z, ZN, nullptr, Nout);
+  });
 }
 
 void launch_zanalysis32(const Dims& d, const DevSetup& s, const FftPlan& pz, const float2* ZN,
                         const double2* Nlin, double2* Nout, cudaStream_t st) {
   dim3 g((d.M + d.mca - 1) / d.mca, d.N, d.B);
-  k_zanalysis<float2><<<g, 128, zanalysis_smem(d, d.mca, sizeof(float2)), st>>>(d, pz, s.tw_z32, ZN, Nlin,
-                                                                                Nout);
+  const size_t sm = zanalysis_smem(d, d.mca, sizeof(float2));
+  with_fft_length(d.nz, [&](auto n) {
+    k_zanalysis<float2, decltype(n)::value><<<g, 128, sm, st>>>(d, pz, s.tw_z32, ZN, Nlin, Nout);
+  });
 }
 
 // ------------------------------------------------------------------ linear solve (A5-A7)
@@ -833,16 +912,24 @@ bool prepare_kernel_attrs(const Dims& d) {
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return false;
   const size_t lim = (size_t)optin;
-  if (zsynth_smem(d, d.mcz, vb) > lim || zanalysis_smem(d, d.mca, vb) > lim ||
+  if (zsynth_smem(d, d.mcz, vb) > lim || zanalysis_smem(d, d.mca, vb) > lim || curl_smem(d) > lim ||
       product_smem(d, d.zc, vb) > lim || solve_smem(d.N, solve_tile(d)) > lim)
     return false;
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  bool ok = cudaFuncSetAttribute(k_zsynth<double2>, a, optin) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(k_zanalysis<double2>, a, optin) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(k_product<double2>, a, optin) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(k_zsynth<float2>, a, optin) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(k_zanalysis<float2>, a, optin) == cudaSuccess;
-  ok = ok && cudaFuncSetAttribute(k_product<float2>, a, optin) == cudaSuccess;
+  bool ok = cudaFuncSetAttribute(k_curl<double2, false>, a, optin) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_curl<float2, true>, a, optin) == cudaSuccess;
+  with_fft_length(d.nz, [&](auto n) {
+    constexpr int L = decltype(n)::value;
+    ok = ok && cudaFuncSetAttribute(k_zsynth<double2, L>, a, optin) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_zanalysis<double2, L>, a, optin) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_zsynth<float2, L>, a, optin) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_zanalysis<float2, L>, a, optin) == cudaSuccess;
+  });
+  with_fft_length(d.nth, [&](auto n) {
+    constexpr int L = decltype(n)::value;
+    ok = ok && cudaFuncSetAttribute(k_product<double2, L>, a, optin) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_product<float2, L>, a, optin) == cudaSuccess;
+  });
   ok = ok && cudaFuncSetAttribute(k_solve<16>, a, optin) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(k_solve<8>, a, optin) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(k_solve<4>, a, optin) == cudaSuccess;
