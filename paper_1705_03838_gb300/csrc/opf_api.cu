@@ -259,6 +259,7 @@ int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, con
   d.nk = 2 * K - 1;
   d.nz = 3 * K;
   d.nth = 3 * M;
+  d.inv_grid = 1.0 / ((double)d.nz * d.nth);
   d.alpha = alpha;
   d.Re = Re[0];
   d.dt = dt[0];

@@ -74,6 +74,7 @@ struct DevSetup {
 // Physical-in-z intermediates are stored [field][n][z][m] (m fastest).
 struct Dims {
   int N, K, M, m_p, nk, nz, nth;
+  double inv_grid;  // 1 / (nz nth): scaling of the forward transforms
   double alpha, Re, dt, c;  // host copies (trajectory 0); kernels read DevSetup::prm
   long F;         // complex values per spectral field = M * N * nk
   int mcz, mca;   // m columns per block: z synthesis, z analysis

@@ -91,7 +91,9 @@ void launch_internal_to_abi(const Dims& d, const double2* U, double2* abi, int, 
 // u_theta tile.  Without SPLIT everything is FP64.
 constexpr int kCurlKC = 4;
 
-size_t curl_smem(const Dims& d) { return (size_t)d.N * kCurlKC * (3 * sizeof(double2) + sizeof(float2)); }
+size_t curl_smem(const Dims& d) {
+  return (size_t)d.N * kCurlKC * (3 * sizeof(double2) + sizeof(float2)) + kCurlKC * sizeof(double);
+}
 
 template <typename V, bool SPLIT>
 __global__ void __launch_bounds__(128) k_curl(Dims d, const double* __restrict__ d1,
@@ -107,6 +109,7 @@ __global__ void __launch_bounds__(128) k_curl(Dims d, const double* __restrict__
   double2* s_ur = s_uz + N * KC;                // [N][KC] u_r
   double2* s_ut = s_ur + N * KC;                // [N][KC] u_theta
   float2* s_ut32 = (float2*)(s_ut + N * KC);    // [N][KC] u_theta in FP32 (SPLIT)
+  double* s_ak = (double*)(s_ut32 + N * KC);    // [KC] alpha k of the block's columns
   d1 = bofs(d1, d.ps);
   d1f = bofs(d1f, d.ps);
   rr = bofs(rr, d.ps);
@@ -117,6 +120,7 @@ __global__ void __launch_bounds__(128) k_curl(Dims d, const double* __restrict__
   const int m = blockIdx.y, kk0 = blockIdx.x * KC;
   const long fs = d.F;
   const double2* up = U + (long)m * N * nk;
+  if (threadIdx.x < KC) s_ak[threadIdx.x] = d.alpha * (kk0 + (int)threadIdx.x - (d.K - 1));
   for (int e = threadIdx.x; e < N * KC; e += blockDim.x) {
     const int c = e % KC, n = e / KC, kk = kk0 + c;
     if (kk >= nk) continue;  // columns past nk are never read
@@ -164,7 +168,7 @@ __global__ void __launch_bounds__(128) k_curl(Dims d, const double* __restrict__
     }
     const double2 ur = s_ur[e], ut = s_ut[e], uz = s_uz[e];
     const double ri = rinv[n];
-    const double ak = d.alpha * (kk - (d.K - 1));
+    const double ak = s_ak[c];
     const double mri = mt * ri;
     // w_r = i (m~ u_z / r - ak u_theta)
     const double xr = mri * uz.x - ak * ut.x, xi = mri * uz.y - ak * ut.y;
@@ -326,19 +330,21 @@ __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* _
   // CFL number of this radial plane (optional): max over the grid of
   // |u_r|/dr, |u_t|/(r dtheta), |u_z|/dz for the TOTAL velocity (the FP32
   // path carries the perturbation only, so the laminar 1 - r^2 is added back)
+  // (taken in the transform precision T)
   double* cfl = bofs(d.cfl, d.ss);
-  double rn = 0.0, inv_dr = 0.0, inv_rdt = 0.0, inv_dz = 0.0, Ubase = 0.0;
+  T inv_dr = 0, inv_rdt = 0, inv_dz = 0, Ubase = 0;
   if (cfl) {
     const double* rinv = bofs(d.rinv_cfl, d.ps);
-    rn = 1.0 / rinv[n];
-    const double rm = n > 0 ? 1.0 / rinv[n - 1] : -rn;
-    const double rp = n < d.N - 1 ? 1.0 / rinv[n + 1] : 1.0 + (1.0 - rm);
-    inv_dr = 1.0 / fmin(rn - rm, rp - rn);
-    inv_rdt = d.m_p * nth / (6.283185307179586 * rn);
-    inv_dz = d.alpha * nz / 6.283185307179586;
-    if constexpr (sizeof(T) == 4) Ubase = 1.0 - rn * rn;
+    const T one = 1, rn = one / (T)rinv[n];
+    const T rm = n > 0 ? one / (T)rinv[n - 1] : -rn;
+    const T rp = n < d.N - 1 ? one / (T)rinv[n + 1] : one + (one - rm);
+    const T twopi = (T)6.283185307179586;
+    inv_dr = one / fmin(rn - rm, rp - rn);
+    inv_rdt = (T)(d.m_p * nth) / (twopi * rn);
+    inv_dz = (T)d.alpha * (T)nz / twopi;
+    if constexpr (sizeof(T) == 4) Ubase = one - rn * rn;
   }
-  double cmax = 0.0;
+  T cmax = 0;
   for (int e = threadIdx.x; e < zc * nth; e += blockDim.x) {
     const int q = e % nth, zr = e / nth;
     const V x0 = res[(zr * 3 + 0) * ld + q], x1 = res[(zr * 3 + 1) * ld + q], x2 = res[(zr * 3 + 2) * ld + q];
@@ -347,7 +353,8 @@ __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* _
     if (d.rotate) {  // Coriolis -2 Omega x u, Omega in cylindrical components at theta_q
       T sn, cs;
       sincos_pi((T)(2 * q) / (T)(d.m_p * nth), &sn, &cs);
-      const T o_r = (T)d.rot_x * cs + (T)d.rot_y * sn, o_t = -(T)d.rot_x * sn + (T)d.rot_y * cs;
+      const T rx = (T)d.rot_x, ry = (T)d.rot_y;
+      const T o_r = rx * cs + ry * sn, o_t = -rx * sn + ry * cs;
       const T o_z = (T)d.rot_z;
       nr -= (T)2 * (o_t * uz - o_z * ut);
       nt -= (T)2 * (o_z * ur - o_r * uz);
@@ -355,14 +362,13 @@ __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* _
     }
     C[(zr * 2 + 0) * ld + q] = V{nr, nt};
     C[(zr * 2 + 1) * ld + q] = V{nz, (T)0};
-    if (cfl)
-      cmax = fmax(cmax, fmax(fabs((double)ur) * inv_dr,
-                             fmax(fabs((double)ut) * inv_rdt, fabs((double)uz + Ubase) * inv_dz)));
+    if (cfl) cmax = fmax(cmax, fmax(fabs(ur) * inv_dr, fmax(fabs(ut) * inv_rdt, fabs(uz + Ubase) * inv_dz)));
   }
-  if (cfl) {  // block max, then one atomic per block (non-negative doubles order as integers)
+  if (cfl) {  // warp max, then one atomic per warp (non-negative doubles order as integers)
     for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
-    if ((threadIdx.x & 31) == 0 && cmax > 0.0)
-      atomicMax((unsigned long long*)cfl, (unsigned long long)__double_as_longlong(cmax));
+    const double cm = (double)cmax;
+    if ((threadIdx.x & 31) == 0 && cm > 0.0)
+      atomicMax((unsigned long long*)cfl, (unsigned long long)__double_as_longlong(cm));
   }
   __syncthreads();
   V* D = (C == A) ? B : A;
@@ -421,6 +427,31 @@ __global__ void __launch_bounds__(128) k_zanalysis(Dims d, FftPlan pz, const V* 
   Nout = bofs(Nout, d.ss);
   const double Re = bofs(d.prm, d.ps)[kPrmRe];
   for (int e = threadIdx.x; e < nz; e += blockDim.x) tw[e] = twz[e];
+  const long fs = d.F;
+  // FP64 addends of an output point (linear terms, body force); a thread's
+  // first point has them loaded before the transform, so that their latency
+  // overlaps it
+  auto addends = [&](long o, double2* ap, double2* am, double2* az) {
+    *ap = *am = *az = double2{0.0, 0.0};
+    if (d.forcing) {  // constant body force (shared by the trajectories of a group)
+      *ap = d.forcing[o];
+      *am = d.forcing[fs + o];
+      *az = d.forcing[2 * fs + o];
+    }
+    if (Nlin) {  // terms linear in the perturbation, evaluated in FP64
+      const double2 a = Nlin[o], b = Nlin[fs + o], c = Nlin[2 * fs + o];
+      *ap = double2{ap->x + a.x, ap->y + a.y};
+      *am = double2{am->x + b.x, am->y + b.y};
+      *az = double2{az->x + c.x, az->y + c.y};
+    }
+  };
+  auto out_index = [&](int e) {
+    const int kk = e % nk, mc = e / nk;
+    return ((long)(m0 + mc) * d.N + n) * nk + kk;
+  };
+  double2 pp, pm, pz0;
+  const bool have0 = threadIdx.x < mcn * nk;
+  if (have0 && (Nlin || d.forcing)) addends(out_index(threadIdx.x), &pp, &pm, &pz0);
   const long fstride = (long)d.N * nz * M;
   for (int e = threadIdx.x; e < 3 * MC * nz; e += blockDim.x) {
     const int mc = e % MC, z = (e / MC) % nz, f = e / (MC * nz);
@@ -432,37 +463,35 @@ __global__ void __launch_bounds__(128) k_zanalysis(Dims d, FftPlan pz, const V* 
   const V* res;
   if constexpr (NZ > 0) res = block_fft_c<NZ, -1>(A, B, 3 * MC, ld, tw);
   else res = block_fft(A, B, 3 * MC, ld, pz, tw, -1);
-  const double sc = 1.0 / ((double)nz * d.nth);
-  const long fs = d.F;
+  // scaling and the +- combination in the transform's precision, then FP64
+  using T = typename Scalar<V>::T;
+  const T sc = (T)d.inv_grid;
   for (int e = threadIdx.x; e < mcn * nk; e += blockDim.x) {
     const int kk = e % nk, mc = e / nk, m = m0 + mc;
     const int k = kk - (K - 1);
     const int zp = k < 0 ? k + nz : k;
     const V r_ = res[(0 * MC + mc) * ld + zp], t_ = res[(1 * MC + mc) * ld + zp];
     const V z_ = res[(2 * MC + mc) * ld + zp];
-    const double nrx = sc * r_.x, nry = sc * r_.y, ntx = sc * t_.x, nty = sc * t_.y;
-    double2 nz2 = double2{sc * z_.x, sc * z_.y};
+    double2 np = double2{(double)(sc * (r_.x - t_.y)), (double)(sc * (r_.y + t_.x))};  // N+ = N_r + i N_theta
+    double2 nm = double2{(double)(sc * (r_.x + t_.y)), (double)(sc * (r_.y - t_.x))};  // N- = N_r - i N_theta
+    double2 nz2 = double2{(double)(sc * z_.x), (double)(sc * z_.y)};
     if (k == 0 && m == 0) nz2.x += 4.0 / Re;  // base driving force (laminar balance)
     const long o = ((long)m * d.N + n) * nk + kk;
-    double2 np = double2{nrx - nty, nry + ntx};        // N+ = N_r + i N_theta
-    double2 nm = double2{nrx + nty, nry - ntx};        // N- = N_r - i N_theta
-    if (d.forcing) {  // constant body force (shared by the trajectories of a group)
-      const double2 a = d.forcing[o], b = d.forcing[fs + o], c = d.forcing[2 * fs + o];
-      np.x += a.x;
-      np.y += a.y;
-      nm.x += b.x;
-      nm.y += b.y;
-      nz2.x += c.x;
-      nz2.y += c.y;
-    }
-    if (Nlin) {  // terms linear in the perturbation, evaluated in FP64
-      const double2 a = Nlin[o], b = Nlin[fs + o], c = Nlin[2 * fs + o];
-      np.x += a.x;
-      np.y += a.y;
-      nm.x += b.x;
-      nm.y += b.y;
-      nz2.x += c.x;
-      nz2.y += c.y;
+    if (Nlin || d.forcing) {
+      double2 ap, am, az;
+      if (e == (int)threadIdx.x) {
+        ap = pp;
+        am = pm;
+        az = pz0;
+      } else {
+        addends(o, &ap, &am, &az);
+      }
+      np.x += ap.x;
+      np.y += ap.y;
+      nm.x += am.x;
+      nm.y += am.y;
+      nz2.x += az.x;
+      nz2.y += az.y;
     }
     Nout[o] = np;
     Nout[fs + o] = nm;

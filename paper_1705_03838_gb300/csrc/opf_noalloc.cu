@@ -126,6 +126,7 @@ extern "C" int opf_nonlinear_noalloc(int N, int K, int M, int m_p, double alpha,
   d.nk = 2 * K - 1;
   d.nz = 3 * K;
   d.nth = 3 * M;
+  d.inv_grid = 1.0 / ((double)d.nz * d.nth);
   d.alpha = alpha;
   d.Re = Re;
   d.dt = 1.0;
