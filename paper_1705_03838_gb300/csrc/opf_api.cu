@@ -348,6 +348,14 @@ struct Runner {
   double cfl_C = 0.0;   // > 0: CFL-controlled time step (single trajectory)
   double dt_max = 0.0;  // upper bound of the controlled time step
   cudaGraphExec_t gexec = nullptr;
+  // groups after the first run on side streams, forked from and joined back
+  // into `stream` (graph branches when captured); cur: the stream the group
+  // being enqueued runs on (null: stream)
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join_ev;
+  cudaEvent_t fork_ev = nullptr;
+  cudaStream_t cur = nullptr;
+  cudaStream_t st() const { return cur ? cur : stream; }
   cudaEvent_t ev[kMaxSlots][2];
   int slot_name[kMaxSlots];
   int nslots = 0, graph_nslots = 0;
@@ -364,11 +372,11 @@ struct Runner {
     if (!timed(name) || nslots >= kMaxSlots) return;
     slot_name[nslots] = name;
     // external: inside stream capture this becomes an event-record node
-    cudaEventRecordWithFlags(ev[nslots][0], stream, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(ev[nslots][0], st(), cudaEventRecordExternal);
   }
   void end() {
     if (!timed(open_name) || nslots >= kMaxSlots) return;
-    cudaEventRecordWithFlags(ev[nslots][1], stream, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(ev[nslots][1], st(), cudaEventRecordExternal);
     ++nslots;
   }
   void drop_graph() {
@@ -396,13 +404,19 @@ void runner_free(Runner* r) {
       cudaEventDestroy(r->ev[i][1]);
     }
   r->events_made = false;
+  for (cudaStream_t s : r->side) cudaStreamDestroy(s);
+  for (cudaEvent_t e : r->join_ev) cudaEventDestroy(e);
+  if (r->fork_ev) cudaEventDestroy(r->fork_ev);
+  r->side.clear();
+  r->join_ev.clear();
+  r->fork_ev = nullptr;
   if (r->own) cudaStreamDestroy(r->own);
   r->own = nullptr;
 }
 
 void enqueue_nonlinear(Runner* r, const Group& g, const double2* U, double2* Nout) {
   const opf::Dims& d = g.d;
-  cudaStream_t st = r->stream;
+  cudaStream_t st = r->st();
   if (r->precision == 1) {
     r->begin(0);
     opf::launch_curl_split32(d, g.ds, U, g.W6f, g.Nlin, st);
@@ -436,24 +450,62 @@ void enqueue_solve(Runner* r, const Group& g, const double2* Na, const double2* 
                    double wb, double2* Uout) {
   opf::SolveArgs a{g.U, Na, Nb, wa, wb, Uout, g.beta_p};
   r->begin(4);
-  opf::launch_solve(g.d, g.ds, a, g.nJ, r->stream);
+  opf::launch_solve(g.d, g.ds, a, g.nJ, r->st());
   r->end();
+}
+
+// Side streams and fork/join events for groups 1..n-1 (created once).
+bool ensure_side_streams(Runner* r) {
+  const size_t need = r->groups.size() - 1;
+  if (!r->fork_ev && cudaEventCreateWithFlags(&r->fork_ev, cudaEventDisableTiming) != cudaSuccess) {
+    r->fork_ev = nullptr;
+    return false;
+  }
+  while (r->side.size() < need) {
+    cudaStream_t s;
+    cudaEvent_t e;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaStreamDestroy(s);
+      return false;
+    }
+    r->side.push_back(s);
+    r->join_ev.push_back(e);
+  }
+  return true;
 }
 
 // One predictor-corrector step (section 2) of every trajectory of every
 // group: predictor with N_j, then n_corr corrector passes with
-// c N^q + (1 - c) N_j, each solved from u_j.
+// c N^q + (1 - c) N_j, each solved from u_j.  The groups are independent:
+// with more than one, groups 1.. run on side streams forked from the main
+// stream and joined back (parallel graph branches), so that one group's
+// FP64-bound solves overlap another's transforms.  Per-kernel timing
+// (timing 1) keeps them in one stream.
 void enqueue_step(Runner* r) {
-  for (Group* g : r->groups) {
+  const size_t ng = r->groups.size();
+  const bool fork = ng > 1 && r->timing != 1 && ensure_side_streams(r);
+  if (fork) cudaEventRecord(r->fork_ev, r->stream);
+  for (size_t i = 0; i < ng; ++i) {
+    Group* g = r->groups[i];
+    r->cur = nullptr;
+    if (fork && i > 0) {
+      r->cur = r->side[i - 1];
+      cudaStreamWaitEvent(r->cur, r->fork_ev, 0);
+    }
     const double c = g->d.c;
-    if (g->d.cfl) cudaMemsetAsync(g->cfl, 0, sizeof(double), r->stream);
+    if (g->d.cfl) cudaMemsetAsync(g->cfl, 0, sizeof(double), r->st());
     enqueue_nonlinear(r, *g, g->U, g->Nj);
     enqueue_solve(r, *g, g->Nj, nullptr, 1.0, 0.0, g->U1);
     for (int q = 0; q < r->n_corr; ++q) {
       enqueue_nonlinear(r, *g, g->U1, g->Nq);
       enqueue_solve(r, *g, g->Nq, g->Nj, c, 1.0 - c, q == r->n_corr - 1 ? g->U : g->U1);
     }
+    if (fork && i > 0) cudaEventRecord(r->join_ev[i - 1], r->cur);
   }
+  r->cur = nullptr;
+  if (fork)
+    for (size_t i = 1; i < ng; ++i) cudaStreamWaitEvent(r->stream, r->join_ev[i - 1], 0);
 }
 
 int harvest_timing(Runner* r) {
