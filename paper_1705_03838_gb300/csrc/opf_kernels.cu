@@ -650,10 +650,14 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   double2* S = NE + 3 * N * T;          // [N][T]     N+ + N-, later d_r p
   double2* P = S + N * T;               // [N][T]     pressure
   double2* coef = P + N * T;            // [T][4]     influence coefficients
-  double* X = (double*)(coef + 4 * T);  // [N][6T]    velocity chains
+  double2* UW = coef + 4 * T;           // [T][19]    u_j near the wall (influence step)
+  double2* AI = UW + 19 * T;            // [T][16]    inverse influence matrices
+  double* X = (double*)(AI + 16 * T);   // [N][6T]    velocity chains
   double* W1 = X + N * NT;              // [2][N][9]  first-derivative stencils
   double* RI = W1 + 2 * N * 9;          // [N]        1/r
-  double* misc = RI + N;                // [2]        flux correction
+  double* RIp = RI + N;                 // [N]        (1 + m~) / (2r)
+  double* RIm = RIp + N;                // [N]        (1 - m~) / (2r)
+  double* misc = RIm + N;               // [2]        flux correction
   const int m = blockIdx.y, kk0 = blockIdx.x * T, tid = threadIdx.x;
   const int mt = d.m_p * m, ps = mt & 1, pv = ps ^ 1;
   s.d1 = bofs(s.d1, d.ps);
@@ -700,7 +704,12 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   // ---- N_eff = wa N_a + wb N_b, and N+ + N- for the divergence
 #pragma unroll 9
   for (int e = tid; e < 2 * N * 9; e += NB) W1[e] = s.d1[e];
-  for (int e = tid; e < N; e += NB) RI[e] = s.rinv[e];
+  for (int e = tid; e < N; e += NB) {
+    const double ri = s.rinv[e];
+    RI[e] = ri;
+    RIp[e] = 0.5 * (1 + mt) * ri;
+    RIm[e] = 0.5 * (1 - mt) * ri;
+  }
 #pragma unroll 4
   for (int e = tid; e < 3 * N * T; e += NB) {
     const int mi = e % T, i = (e / T) % N, f = e / (T * N);
@@ -721,28 +730,29 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   }
   __syncthreads();
 
+  // Row-parallel phases over (mode, row) give each thread one fixed mode
+  // mi_t = tid % T and the rows tid / T, tid / T + NB / T, ...
+  const int mi_t = tid % T;
+  const double ak_t = d.alpha * (min(kk0 + mi_t, nk - 1) - (K - 1));
+
   // ---- pressure right-hand side: div N_eff (rows < N-1), 0 at the wall
-  for (int e = tid; e < N * T; e += NB) {
-    const int mi = e % T, i = e / T;
-    const int k = min(kk0 + mi, nk - 1) - (K - 1);
-    const double ak = d.alpha * k;
+  for (int i = tid / T; i < N; i += NB / T) {
     double2 b = double2{0.0, 0.0};
     if (i < N - 1) {
       const int lo = row_lo_d(i, N);
       double ax = 0.0, ay = 0.0;
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
-        const double2 sv = S[(lo + q) * T + mi];
+        const double2 sv = S[(lo + q) * T + mi_t];
         const double w = wv[i * 9 + q];
-        ax += w * sv.x;
-        ay += w * sv.y;
+        ax = fma(w, sv.x, ax);
+        ay = fma(w, sv.y, ay);
       }
-      const double2 np = NE[i * T + mi], nm = NE[(N + i) * T + mi], nz = NE[(2 * N + i) * T + mi];
-      const double ri = 0.5 * RI[i];
-      b.x = 0.5 * ax + ri * ((1 + mt) * np.x + (1 - mt) * nm.x) - ak * nz.y;
-      b.y = 0.5 * ay + ri * ((1 + mt) * np.y + (1 - mt) * nm.y) + ak * nz.x;
+      const double2 np = NE[i * T + mi_t], nm = NE[(N + i) * T + mi_t], nz = NE[(2 * N + i) * T + mi_t];
+      b.x = fma(0.5, ax, fma(RIp[i], np.x, fma(RIm[i], nm.x, -ak_t * nz.y)));
+      b.y = fma(0.5, ay, fma(RIp[i], np.y, fma(RIm[i], nm.y, ak_t * nz.x)));
     }
-    P[i * T + mi] = b;
+    P[i * T + mi_t] = b;
   }
   __syncthreads();
 
@@ -765,39 +775,43 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
       }
       X[i * NT + c] = b;
     }
+    // u_j near the wall and the inverse influence matrices of the tile, for
+    // the influence step (rows N-9..N-1 of u+, u-; row N-1 of u_z)
+    for (int e = tid - NP; e < 35 * T; e += NB - NP) {
+      const int mi = e % T, w = e / T;
+      if (w < 19) {
+        const int f = w < 18 ? w / 9 : 2, i = w < 18 ? N - 9 + w % 9 : N - 1;
+        UW[mi * 19 + w] = uj(f, i, mi);
+      } else {
+        AI[mi * 16 + (w - 19)] = s.ainv[((long)m * nk + min(kk0 + mi, nk - 1)) * 16 + (w - 19)];
+      }
+    }
   }
   __syncthreads();
 
-  // ---- d_r p once per (mode, row), then subtract grad p from the right-hand sides
-  for (int e = tid; e < N * T; e += NB) {
-    const int mi = e % T, i = e / T;
+  // ---- d_r p per (mode, row), subtracted at once from the right-hand sides of
+  //      the three fields (rows < N-1):
+  //      (grad p)+- = d_r p -+ m~ p / r,  (grad p)_z = i ak p
+  for (int i = tid / T; i < N - 1; i += NB / T) {
     const int lo = row_lo_d(i, N);
     double ax = 0.0, ay = 0.0;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-      const double2 pv2 = P[(lo + q) * T + mi];
+      const double2 pv2 = P[(lo + q) * T + mi_t];
       const double w = ws[i * 9 + q];
-      ax += w * pv2.x;
-      ay += w * pv2.y;
+      ax = fma(w, pv2.x, ax);
+      ay = fma(w, pv2.y, ay);
     }
-    S[i * T + mi] = double2{ax, ay};
-  }
-  __syncthreads();
-#pragma unroll 4
-  for (int e = tid; e < (N - 1) * NT; e += NB) {
-    const int c = e % NT, i = e / NT;
-    const int part = c & 1, mi = (c >> 1) % T, f = (c >> 1) / T;
-    // rhs -= grad p:  (grad p)+- = d_r p -+ m~ p / r,  (grad p)_z = i ak p
-    const double2 pp = P[i * T + mi];
-    double& xv = X[i * NT + c];
-    if (f < 2) {
-      const double2 dp = S[i * T + mi];
-      const double mr = (f == 0 ? mt : -mt) * RI[i];
-      xv = fma(mr, part ? pp.y : pp.x, xv - (part ? dp.y : dp.x));
-    } else {
-      const double ak = d.alpha * (min(kk0 + mi, nk - 1) - (K - 1));
-      xv = part == 0 ? fma(ak, pp.y, xv) : fma(-ak, pp.x, xv);
-    }
+    const double2 pp = P[i * T + mi_t];
+    const double mr = mt * RI[i];
+    double* xr = X + i * NT;
+    const int c0 = mi_t << 1, c1 = (T + mi_t) << 1, c2 = (2 * T + mi_t) << 1;
+    xr[c0] = fma(mr, pp.x, xr[c0] - ax);
+    xr[c0 + 1] = fma(mr, pp.y, xr[c0 + 1] - ay);
+    xr[c1] = fma(-mr, pp.x, xr[c1] - ax);
+    xr[c1 + 1] = fma(-mr, pp.y, xr[c1 + 1] - ay);
+    xr[c2] = fma(ak_t, pp.y, xr[c2]);
+    xr[c2 + 1] = fma(-ak_t, pp.x, xr[c2 + 1]);
   }
   __syncthreads();
 
@@ -816,9 +830,9 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   if (tid < 4 * T && kk0 + (tid >> 2) < nk) {
     const int mj = tid >> 2, r = tid & 3, kj = kk0 + mj;
     const double akj = d.alpha * (kj - (K - 1));
-    auto uv = [&](int ff, int i) {
+    auto uv = [&](int ff, int i) {  // rows N-9.. of u+-, row N-1 of u_z
       const int c = (ff * T + mj) << 1;
-      const double2 w = uj(ff, i, mj);
+      const double2 w = UW[mj * 19 + (ff < 2 ? ff * 9 + i - (N - 9) : 18)];
       return double2{X[i * NT + c] - cu * w.x, X[i * NT + c + 1] - cu * w.y};
     };
     const double2 g0 = uv(0, N - 1), g1 = uv(1, N - 1), g2 = uv(2, N - 1);
@@ -835,7 +849,7 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
     const double2 g[4] = {g0, g1, g2,
                           double2{0.5 * ax + ri * ((1 + mt) * g0.x + (1 - mt) * g1.x) - akj * g2.y,
                                   0.5 * ay + ri * ((1 + mt) * g0.y + (1 - mt) * g1.y) + akj * g2.x}};
-    const double2* Ai = s.ainv + ((long)m * nk + kj) * 16 + r * 4;
+    const double2* Ai = AI + mj * 16 + r * 4;
     double sx = 0.0, sy = 0.0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -908,7 +922,7 @@ static int solve_tile(const Dims& d) {
 size_t solve_smem_bytes(int N, int T) { return solve_smem(N, T); }
 
 static size_t solve_smem(int N, int T) {
-  return (size_t)(5 * N * T + 4 * T) * 16 + (size_t)6 * N * T * 8 + (size_t)(2 * N * 9 + N + 2) * 8;
+  return (size_t)(5 * N * T + 39 * T) * 16 + (size_t)6 * N * T * 8 + (size_t)(2 * N * 9 + 3 * N + 2) * 8;
 }
 
 // Chunk sizes keep every transform block within ~96 KB of shared memory (two
