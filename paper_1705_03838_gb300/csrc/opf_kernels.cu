@@ -715,7 +715,8 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
     const int mi = e % T, i = (e / T) % N, f = e / (T * N);
     const long g = f * fs + base + (long)i * nk + min(kk0 + mi, nk - 1);
     const double2 u = a.Na[g];
-    double2 v = double2{a.wa * u.x, a.wa * u.y};
+    double2 v = u;
+    if (a.wa != 1.0) v = double2{a.wa * u.x, a.wa * u.y};  // (the predictor takes N_a as it is)
     if (a.Nb) {
       const double2 w = a.Nb[g];
       v.x += a.wb * w.x;
@@ -826,40 +827,59 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   __syncthreads();
 
   // ---- influence matrix on u = v - ((1-c)/c) u_j:
-  //      g = (u+(1), u-(1), u_z(1), div u(1)),  a = -A^{-1} g  (thread: mode, row of A^{-1})
-  if (tid < 4 * T && kk0 + (tid >> 2) < nk) {
-    const int mj = tid >> 2, r = tid & 3, kj = kk0 + mj;
-    const double akj = d.alpha * (kj - (K - 1));
-    auto uv = [&](int ff, int i) {  // rows N-9.. of u+-, row N-1 of u_z
+  //      g = (u+(1), u-(1), u_z(1), div u(1)),  a = -A^{-1} g.
+  //      A warp issues one FP64 instruction per ~64 cycles on GB300 whatever
+  //      its active lanes, so the work is spread: step 1, one thread per
+  //      (mode, tap) of the wall divergence stencil and per (mode, field) of
+  //      u(1); step 2, one thread per (mode, row of A^{-1}, re/im part), the
+  //      tap sum reduced over the mode's 8 lanes.  (NE is free by now.)
+  {
+    double2* Dt = NE;          // [T][9] w_q (u+ + u-)(N-9+q)
+    double2* Gw = NE + 9 * T;  // [T][3] u+-, u_z at the wall
+    auto uv = [&](int ff, int i, int mj) {  // rows N-9.. of u+-, row N-1 of u_z
       const int c = (ff * T + mj) << 1;
       const double2 w = UW[mj * 19 + (ff < 2 ? ff * 9 + i - (N - 9) : 18)];
       return double2{X[i * NT + c] - cu * w.x, X[i * NT + c + 1] - cu * w.y};
     };
-    const double2 g0 = uv(0, N - 1), g1 = uv(1, N - 1), g2 = uv(2, N - 1);
-    const int lo = N - 9;
-    double ax = 0.0, ay = 0.0;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
+    if (tid < 9 * T) {
+      const int mj = tid / 9, q = tid % 9, i = N - 9 + q;
+      const double2 p = uv(0, i, mj), mm = uv(1, i, mj);
       const double w = wv[(N - 1) * 9 + q];
-      const double2 p = uv(0, lo + q), mm = uv(1, lo + q);
-      ax += w * (p.x + mm.x);
-      ay += w * (p.y + mm.y);
+      Dt[tid] = double2{w * (p.x + mm.x), w * (p.y + mm.y)};
+    } else if (tid < 12 * T) {
+      const int e = tid - 9 * T, mj = e / 3, f = e % 3;
+      Gw[e] = uv(f, N - 1, mj);
     }
-    const double ri = 0.5 * RI[N - 1];
-    const double2 g[4] = {g0, g1, g2,
-                          double2{0.5 * ax + ri * ((1 + mt) * g0.x + (1 - mt) * g1.x) - akj * g2.y,
-                                  0.5 * ay + ri * ((1 + mt) * g0.y + (1 - mt) * g1.y) + akj * g2.x}};
-    const double2* Ai = AI + mj * 16 + r * 4;
-    double sx = 0.0, sy = 0.0;
+    __syncthreads();
+    if (tid < 8 * T) {  // whole warps (T >= 4)
+      const int mj = tid >> 3, l = tid & 7, r = (tid >> 1) & 3, part = tid & 1;
+      double2 sum = Dt[mj * 9 + l];
+      if (l == 0) {
+        const double2 t8 = Dt[mj * 9 + 8];
+        sum = double2{sum.x + t8.x, sum.y + t8.y};
+      }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const double2 A = Ai[c];
-      sx += A.x * g[c].x - A.y * g[c].y;
-      sy += A.x * g[c].y + A.y * g[c].x;
+      for (int o = 4; o > 0; o >>= 1) {
+        sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o, 8);
+        sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o, 8);
+      }
+      const double2 g0 = Gw[mj * 3], g1 = Gw[mj * 3 + 1], g2 = Gw[mj * 3 + 2];
+      const double akj = d.alpha * (min(kk0 + mj, nk - 1) - (K - 1));
+      const double rp = RIp[N - 1], rm = RIm[N - 1];
+      const double2 g[4] = {g0, g1, g2,
+                            double2{fma(0.5, sum.x, fma(rp, g0.x, fma(rm, g1.x, -akj * g2.y))),
+                                    fma(0.5, sum.y, fma(rp, g0.y, fma(rm, g1.y, akj * g2.x)))}};
+      const double2* Ai = AI + mj * 16 + r * 4;
+      double acc = 0.0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const double2 A = Ai[c];
+        acc = part ? fma(A.x, g[c].y, fma(A.y, g[c].x, acc)) : fma(A.x, g[c].x, fma(-A.y, g[c].y, acc));
+      }
+      ((double*)coef)[(mj * 4 + r) * 2 + part] = -acc;
     }
-    coef[mj * 4 + r] = double2{-sx, -sy};
+    __syncthreads();
   }
-  __syncthreads();
 
   // final value of chain c at row i: v - ((1-c)/c) u_j + basis responses
   auto final_value = [&](int i, int c) {
@@ -867,8 +887,9 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
     const int kk = min(kk0 + mi, nk - 1), k = kk - (K - 1);
     const double* Bv = s.basis + (long)(abs(k) * M + m) * 6 * N;
     const double2 a0 = coef[mi * 4 + 0], ax = coef[mi * 4 + 1 + f];
-    const double sk = k > 0 ? 1.0 : (k < 0 ? -1.0 : 0.0);
-    const double c0 = f == 2 ? (part ? sk * a0.x : -sk * a0.y) : (part ? a0.y : a0.x);
+    // u_z responses carry i sign(k): coefficient sign(k) (a0.x, -a0.y) swapped
+    const double az = part ? a0.x : -a0.y;
+    const double c0 = f == 2 ? (k > 0 ? az : (k < 0 ? -az : 0.0)) : (part ? a0.y : a0.x);
     const double c1 = part ? ax.y : ax.x;
     const double2 w = a.Uj[f * fs + base + (long)i * nk + kk];
     return X[i * NT + c] - cu * (part ? w.y : w.x) + c0 * Bv[f * N + i] + c1 * Bv[(3 + f) * N + i];
