@@ -541,6 +541,31 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void* p, unsigned bytes) 
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Asynchronous global -> shared copies (8 or 16 bytes, both addresses aligned
+// to the size); completion by commit groups, visibility by a block barrier.
+__device__ __forceinline__ void cp_async8(void* sm, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(sm)), "l"(g)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* sm, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(sm)), "l"(g)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int G>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(G) : "memory"); }
+
+// Shared memory of a solve block: the working arrays, then (when they fit in
+// ~100 KB, i.e. for moderate N) u_j and the influence responses of the tile,
+// staged by asynchronous copies at the start so that the right-hand sides,
+// the influence step and the write-out read them from shared memory.
+__host__ __device__ constexpr size_t solve_smem_base(int N, int T) {
+  return (size_t)(5 * N * T + 39 * T) * 16 + (size_t)6 * N * T * 8 + (size_t)(2 * N * 9 + 3 * N + 2) * 8;
+}
+__host__ __device__ constexpr bool solve_stage(int N, int T) {
+  return solve_smem_base(N, T) + 16 + (size_t)96 * N * T <= 100 * 1024;
+}
+
 // Banded substitution on one real right-hand side held in shared memory at
 // x[i * st], i < N, by a group of 4 consecutive lanes (column-oriented):
 // lane t keeps the partial sum of row c+1+t (and of row c+5+t for the wall
@@ -658,6 +683,9 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   double* RIp = RI + N;                 // [N]        (1 + m~) / (2r)
   double* RIm = RIp + N;                // [N]        (1 - m~) / (2r)
   double* misc = RIm + N;               // [2]        flux correction
+  const bool stage = solve_stage(N, T);
+  double2* UJ = (double2*)(((size_t)(misc + 2) + 15) & ~(size_t)15);  // [3][N][T] u_j (stage)
+  double* BS = (double*)(UJ + 3 * N * T);                             // [T][6N]   responses (stage)
   const int m = blockIdx.y, kk0 = blockIdx.x * T, tid = threadIdx.x;
   const int mt = d.m_p * m, ps = mt & 1, pv = ps ^ 1;
   s.d1 = bofs(s.d1, d.ps);
@@ -694,16 +722,18 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
     const int mi = tid % T, which = tid / T;
     const int ik = abs(min(kk0 + mi, nk - 1) - (K - 1));
     if (which == 4) {
-      prefetch_l2_bulk(s.basis + (long)(ik * M + m) * 6 * N, 48u * N);
+      if (!stage) prefetch_l2_bulk(s.basis + (long)(ik * M + m) * 6 * N, 48u * N);
     } else if (!(N & 1)) {
       const long op = which == 0 ? ((ik == 0 && m == 0) ? K * M : ik * M + m) : ik * s.nJ + s.hop[3 * m + which - 1];
       prefetch_l2_bulk((which == 0 ? s.luP : s.luH) + op * N * kLuSlots, (unsigned)N * kLuSlots * 8u);
     }
   }
 
+  // The stencils by asynchronous copies, waited for at the first barrier.
+  for (int e = tid; e < 2 * N * 9; e += NB) cp_async8(W1 + e, s.d1 + e);
+  cp_async_commit();
+
   // ---- N_eff = wa N_a + wb N_b, and N+ + N- for the divergence
-#pragma unroll 9
-  for (int e = tid; e < 2 * N * 9; e += NB) W1[e] = s.d1[e];
   for (int e = tid; e < N; e += NB) {
     const double ri = s.rinv[e];
     RI[e] = ri;
@@ -724,6 +754,7 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
     }
     NE[(f * N + i) * T + mi] = v;
   }
+  cp_async_wait<0>();
   __syncthreads();
   for (int e = tid; e < N * T; e += NB) {
     const double2 p = NE[e], q = NE[N * T + e];
@@ -771,6 +802,7 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
       double b = 0.0;
       if (i < N - 1) {
         const double2 u = uj(f, i, mi);
+        if (stage && part == 0) UJ[(f * N + i) * T + mi] = u;
         const double2 ne = NE[(f * N + i) * T + mi];
         b = ci * (part ? u.y : u.x) + (part ? ne.y : ne.x);
       }
@@ -778,9 +810,25 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
     }
     // u_j near the wall and the inverse influence matrices of the tile, for
     // the influence step (rows N-9..N-1 of u+, u-; row N-1 of u_z)
+    // (staged: u_j of the wall row and the influence responses of the tile
+    // into shared memory instead, for the influence step and the write-out)
+    if (stage) {
+      for (int e = tid - NP; e < 3 * T; e += NB - NP) {
+        const int mi = e % T, f = e / T;
+        UJ[(f * N + N - 1) * T + mi] = uj(f, N - 1, mi);
+      }
+      for (int e = tid - NP; e < 3 * N * T; e += NB - NP) {  // 16-byte chunks, 3N per mode
+        const int mi = e / (3 * N), ch = e % (3 * N);
+        const int ik = abs(min(kk0 + mi, nk - 1) - (K - 1));
+        cp_async16(BS + (long)mi * 6 * N + 2 * ch, s.basis + (long)(ik * M + m) * 6 * N + 2 * ch);
+      }
+      cp_async_commit();
+      cp_async_wait<0>();
+    }
     for (int e = tid - NP; e < 35 * T; e += NB - NP) {
       const int mi = e % T, w = e / T;
       if (w < 19) {
+        if (stage) continue;  // read from the staged u_j
         const int f = w < 18 ? w / 9 : 2, i = w < 18 ? N - 9 + w % 9 : N - 1;
         UW[mi * 19 + w] = uj(f, i, mi);
       } else {
@@ -838,7 +886,7 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
     double2* Gw = NE + 9 * T;  // [T][3] u+-, u_z at the wall
     auto uv = [&](int ff, int i, int mj) {  // rows N-9.. of u+-, row N-1 of u_z
       const int c = (ff * T + mj) << 1;
-      const double2 w = UW[mj * 19 + (ff < 2 ? ff * 9 + i - (N - 9) : 18)];
+      const double2 w = stage ? UJ[(ff * N + i) * T + mj] : UW[mj * 19 + (ff < 2 ? ff * 9 + i - (N - 9) : 18)];
       return double2{X[i * NT + c] - cu * w.x, X[i * NT + c + 1] - cu * w.y};
     };
     if (tid < 9 * T) {
@@ -891,8 +939,9 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
     const double az = part ? a0.x : -a0.y;
     const double c0 = f == 2 ? (k > 0 ? az : (k < 0 ? -az : 0.0)) : (part ? a0.y : a0.x);
     const double c1 = part ? ax.y : ax.x;
-    const double2 w = a.Uj[f * fs + base + (long)i * nk + kk];
-    return X[i * NT + c] - cu * (part ? w.y : w.x) + c0 * Bv[f * N + i] + c1 * Bv[(3 + f) * N + i];
+    const double2 w = stage ? UJ[(f * N + i) * T + mi] : a.Uj[f * fs + base + (long)i * nk + kk];
+    const double* B = stage ? BS + (long)mi * 6 * N : Bv;
+    return X[i * NT + c] - cu * (part ? w.y : w.x) + c0 * B[f * N + i] + c1 * B[(3 + f) * N + i];
   };
 
   // ---- fixed flux on (0,0): beta' so that 2 pi int u_z r dr = pi/2
@@ -943,7 +992,7 @@ static int solve_tile(const Dims& d) {
 size_t solve_smem_bytes(int N, int T) { return solve_smem(N, T); }
 
 static size_t solve_smem(int N, int T) {
-  return (size_t)(5 * N * T + 39 * T) * 16 + (size_t)6 * N * T * 8 + (size_t)(2 * N * 9 + 3 * N + 2) * 8;
+  return solve_smem_base(N, T) + (solve_stage(N, T) ? 16 + (size_t)96 * N * T : 0);
 }
 
 // Chunk sizes keep every transform block within ~96 KB of shared memory (two
