@@ -87,8 +87,8 @@ def kernel_costs(w):
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the current
 # kernels on the medium workload (one ncu capture each, summarised in the
 # named profile), keyed by (kernel, precision of the step)
-PROFILED_DRAM_BYTES = {("solve", 0): 22.5e6, ("solve", 1): 22.5e6, ("product", 0): 10.66e6}
-PROFILE_FILES = {"solve": "profiles/k_solve_medium.md", "product": "profiles/k_zsynth_k_product_fp64_medium.md"}
+PROFILED_DRAM_BYTES = {("solve", 0): 24.25e6, ("solve", 1): 20.77e6, ("product", 0): 10.66e6}
+PROFILE_FILES = {"solve": "profiles/k_solve_medium.md", "product": "profiles/transforms_medium.md"}
 
 
 # which arithmetic bounds each kernel: FP64 for the solve and the curl (both

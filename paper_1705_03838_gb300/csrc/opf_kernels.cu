@@ -9,6 +9,7 @@
 //               (N_r, N_theta) -> N+-, base forcing 4/Re on the (0,0) mode
 // Linear part (section 2.2, banded LU per Fourier mode; section 2 influence
 // matrix): k_solve, one block per tile of T modes at fixed m.
+#include <algorithm>
 #include <cstdio>
 
 #include "opf_fft.cuh"
@@ -534,6 +535,7 @@ struct SolveDev {
   const double* G;
   const double* prm;
   int nJ;
+  int stage;  // u_j and the influence responses staged in shared memory
 };
 
 // Bulk L2 prefetch by the TMA unit: p 16-byte aligned, bytes a multiple of 16.
@@ -559,12 +561,15 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // ~100 KB, i.e. for moderate N) u_j and the influence responses of the tile,
 // staged by asynchronous copies at the start so that the right-hand sides,
 // the influence step and the write-out read them from shared memory.
+// The host stages only where that costs no resident blocks (see
+// launch_solve); the launch gives the staged size then, the base size else.
 __host__ __device__ constexpr size_t solve_smem_base(int N, int T) {
-  return (size_t)(5 * N * T + 39 * T) * 16 + (size_t)6 * N * T * 8 + (size_t)(2 * N * 9 + 3 * N + 2) * 8;
+  return (size_t)(5 * N * T + 4 * T) * 16 + (size_t)6 * N * T * 8 + (size_t)(2 * N * 9 + 3 * N + 2) * 8;
 }
-__host__ __device__ constexpr bool solve_stage(int N, int T) {
-  return solve_smem_base(N, T) + 16 + (size_t)96 * N * T <= 100 * 1024;
+__host__ __device__ constexpr size_t solve_smem_staged(int N, int T) {
+  return solve_smem_base(N, T) + 16 + (size_t)96 * N * T;
 }
+__host__ __device__ constexpr bool solve_stage_fits(int N, int T) { return solve_smem_staged(N, T) <= 100 * 1024; }
 
 // Banded substitution on one real right-hand side held in shared memory at
 // x[i * st], i < N, by a group of 4 consecutive lanes (column-oriented):
@@ -675,15 +680,17 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   double2* S = NE + 3 * N * T;          // [N][T]     N+ + N-, later d_r p
   double2* P = S + N * T;               // [N][T]     pressure
   double2* coef = P + N * T;            // [T][4]     influence coefficients
-  double2* UW = coef + 4 * T;           // [T][19]    u_j near the wall (influence step)
-  double2* AI = UW + 19 * T;            // [T][16]    inverse influence matrices
-  double* X = (double*)(AI + 16 * T);   // [N][6T]    velocity chains
+  double* X = (double*)(coef + 4 * T);  // [N][6T]    velocity chains
   double* W1 = X + N * NT;              // [2][N][9]  first-derivative stencils
   double* RI = W1 + 2 * N * 9;          // [N]        1/r
   double* RIp = RI + N;                 // [N]        (1 + m~) / (2r)
   double* RIm = RIp + N;                // [N]        (1 - m~) / (2r)
   double* misc = RIm + N;               // [2]        flux correction
-  const bool stage = solve_stage(N, T);
+  const bool stage = s.stage;
+  // u_j near the wall for the influence step, when not staged: in S (free
+  // after the pressure right-hand side) if it holds [T][19], else from global
+  double2* UW = S;
+  const bool uw_in_s = !stage && N >= 19;
   double2* UJ = (double2*)(((size_t)(misc + 2) + 15) & ~(size_t)15);  // [3][N][T] u_j (stage)
   double* BS = (double*)(UJ + 3 * N * T);                             // [T][6N]   responses (stage)
   const int m = blockIdx.y, kk0 = blockIdx.x * T, tid = threadIdx.x;
@@ -825,14 +832,11 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
       cp_async_commit();
       cp_async_wait<0>();
     }
-    for (int e = tid - NP; e < 35 * T; e += NB - NP) {
-      const int mi = e % T, w = e / T;
-      if (w < 19) {
-        if (stage) continue;  // read from the staged u_j
+    if (uw_in_s) {
+      for (int e = tid - NP; e < 19 * T; e += NB - NP) {
+        const int mi = e % T, w = e / T;
         const int f = w < 18 ? w / 9 : 2, i = w < 18 ? N - 9 + w % 9 : N - 1;
         UW[mi * 19 + w] = uj(f, i, mi);
-      } else {
-        AI[mi * 16 + (w - 19)] = s.ainv[((long)m * nk + min(kk0 + mi, nk - 1)) * 16 + (w - 19)];
       }
     }
   }
@@ -886,9 +890,19 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
     double2* Gw = NE + 9 * T;  // [T][3] u+-, u_z at the wall
     auto uv = [&](int ff, int i, int mj) {  // rows N-9.. of u+-, row N-1 of u_z
       const int c = (ff * T + mj) << 1;
-      const double2 w = stage ? UJ[(ff * N + i) * T + mj] : UW[mj * 19 + (ff < 2 ? ff * 9 + i - (N - 9) : 18)];
+      const double2 w = stage     ? UJ[(ff * N + i) * T + mj]
+                        : uw_in_s ? UW[mj * 19 + (ff < 2 ? ff * 9 + i - (N - 9) : 18)]
+                                  : uj(ff, i, mj);
       return double2{X[i * NT + c] - cu * w.x, X[i * NT + c + 1] - cu * w.y};
     };
+    // row r of A^{-1} for the step-2 threads, loaded while step 1 runs
+    double2 Ar[4];
+    if (tid < 8 * T) {
+      const int mj = tid >> 3, r = (tid >> 1) & 3;
+      const double2* Ag = s.ainv + ((long)m * nk + min(kk0 + mj, nk - 1)) * 16 + r * 4;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) Ar[c] = Ag[c];
+    }
     if (tid < 9 * T) {
       const int mj = tid / 9, q = tid % 9, i = N - 9 + q;
       const double2 p = uv(0, i, mj), mm = uv(1, i, mj);
@@ -917,11 +931,10 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
       const double2 g[4] = {g0, g1, g2,
                             double2{fma(0.5, sum.x, fma(rp, g0.x, fma(rm, g1.x, -akj * g2.y))),
                                     fma(0.5, sum.y, fma(rp, g0.y, fma(rm, g1.y, akj * g2.x)))}};
-      const double2* Ai = AI + mj * 16 + r * 4;
       double acc = 0.0;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const double2 A = Ai[c];
+        const double2 A = Ar[c];
         acc = part ? fma(A.x, g[c].y, fma(A.y, g[c].x, acc)) : fma(A.x, g[c].x, fma(-A.y, g[c].y, acc));
       }
       ((double*)coef)[(mj * 4 + r) * 2 + part] = -acc;
@@ -992,7 +1005,26 @@ static int solve_tile(const Dims& d) {
 size_t solve_smem_bytes(int N, int T) { return solve_smem(N, T); }
 
 static size_t solve_smem(int N, int T) {
-  return solve_smem_base(N, T) + (solve_stage(N, T) ? 16 + (size_t)96 * N * T : 0);
+  return solve_stage_fits(N, T) ? solve_smem_staged(N, T) : solve_smem_base(N, T);
+}
+
+// Stage u_j and the responses when the staged block fits and the SM still
+// holds as many blocks as the grid can use (so staging never costs occupancy).
+static bool solve_use_stage(const Dims& d, int T, long blocks) {
+  if (!solve_stage_fits(d.N, T)) return false;
+  static int sms = 0, smem_sm = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const size_t reserve = 1024;  // per-block shared memory the system keeps
+  const long with = (long)(smem_sm / (solve_smem_staged(d.N, T) + reserve));
+  const long without = (long)(smem_sm / (solve_smem_base(d.N, T) + reserve));
+  const long need = (blocks + sms - 1) / sms;
+  return with >= std::min(need, without);
 }
 
 // Chunk sizes keep every transform block within ~96 KB of shared memory (two
@@ -1050,12 +1082,14 @@ bool prepare_kernel_attrs(const Dims& d) {
 }
 
 void launch_solve(const Dims& d, const DevSetup& s, const SolveArgs& a, int nJ, cudaStream_t st) {
-  SolveDev sd{s.d1, s.rinv, s.wq, s.hop, s.luH, s.luP, s.basis, s.ainv, s.G, s.prm, nJ};
   const int T = solve_tile(d);
   dim3 g((d.nk + T - 1) / T, d.M, d.B);
-  if (T == 16) k_solve<16><<<g, 24 * 16, solve_smem(d.N, 16), st>>>(d, sd, a);
-  else if (T == 8) k_solve<8><<<g, 24 * 8, solve_smem(d.N, 8), st>>>(d, sd, a);
-  else k_solve<4><<<g, 24 * 4, solve_smem(d.N, 4), st>>>(d, sd, a);
+  const bool stage = solve_use_stage(d, T, (long)g.x * g.y * g.z);
+  SolveDev sd{s.d1, s.rinv, s.wq, s.hop, s.luH, s.luP, s.basis, s.ainv, s.G, s.prm, nJ, stage ? 1 : 0};
+  const size_t sm = stage ? solve_smem_staged(d.N, T) : solve_smem_base(d.N, T);
+  if (T == 16) k_solve<16><<<g, 24 * 16, sm, st>>>(d, sd, a);
+  else if (T == 8) k_solve<8><<<g, 24 * 8, sm, st>>>(d, sd, a);
+  else k_solve<4><<<g, 24 * 4, sm, st>>>(d, sd, a);
 }
 
 // ------------------------------------------------------------------ diagnostics
