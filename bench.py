@@ -57,14 +57,16 @@ def config_dict(w, precision):
 
 
 # ------------------------------------------------------------------ algorithmic costs
-def kernel_costs(w):
+def kernel_costs(w, precision=1):
     """Algorithmic flops and bytes per launch, per kernel.
 
     FFT flops use 2.5 n log2 n per real 2-D transform of n = 9KM points,
     split between z (log2 3K) and theta (log2 3M) parts.  The solve counts,
     per mode and radial row: div N_eff (48), d_r p (36), right-hand sides (30),
     final update and influence correction (36), and 8 real banded
-    substitutions (2 nl + 2 nu + 1 each, nl/nu the row's band widths)."""
+    substitutions (2 nl + 2 nu + 1 each, nl/nu the row's band widths).  In FP64
+    steps the solve launches also take the curl of their output (A1) for the
+    next nonlinear evaluation, so their cost includes the curl's."""
     N, K, M = w["N"], w["K"], w["M"]
     nz, nth, nk = 3 * K, 3 * M, 2 * K - 1
     n = nz * nth
@@ -80,14 +82,15 @@ def kernel_costs(w):
         "zsynth": {"flops": 6 * N * 2.5 * n * lz, "bytes": 16 * (6 * F + 6 * P)},
         "product": {"flops": 9 * N * 2.5 * n * lt + 9 * N * n, "bytes": 16 * (6 * P + 3 * P)},
         "zanalysis": {"flops": 3 * N * 2.5 * n * lz, "bytes": 16 * (3 * P + 3 * F)},
-        "solve": {"flops": solve, "bytes": 16 * (3 * F * 3 + 3 * F)},
+        "solve": {"flops": solve + (F * (2 * 9 * 4 + 30) if precision == 0 else 0),
+                  "bytes": 16 * (3 * F * 3 + 3 * F + (6 * F if precision == 0 else 0))},
     }
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the current
 # kernels on the medium workload (one ncu capture each, summarised in the
 # named profile), keyed by (kernel, precision of the step)
-PROFILED_DRAM_BYTES = {("solve", 0): 24.25e6, ("solve", 1): 20.77e6, ("product", 0): 10.66e6}
+PROFILED_DRAM_BYTES = {("product", 0): 10.66e6}
 PROFILE_FILES = {"solve": "profiles/k_solve_medium.md", "product": "profiles/transforms_medium.md"}
 
 
@@ -666,9 +669,8 @@ def run_gpu(args, w):
 
     value = args.steps * world / (total_ms / 1000.0)
     peaks, peak_kind = load_peaks()
-    costs = kernel_costs(w)
-
     def roofline(kt, precision):
+        costs = kernel_costs(w, precision)
         dom = max(kt, key=lambda k: kt[k][0])
         dom_ms = kt[dom][0] / max(1, kt[dom][1])
         pk, src = kernel_peak(dom, precision)
@@ -692,7 +694,9 @@ def run_gpu(args, w):
         cpu = {"value": sps, "unit": "timesteps/s", "cores": 1, "kind": "oracle",
                "sample": f"{n} full oracle steps of the same workload after 1 setup step "
                          f"({setup:.1f} s), {secs:.1f} s, single thread"}
-    launches_per_step = 5 * 2  # 4 nonlinear-term kernels + 1 solve, predictor + corrector
+    # per pass: curl + 3 transform kernels + solve (mixed); FP64 steps take
+    # the curl inside the solve
+    launches_per_step = (5 if args.precision == 1 else 4) * 2
     line = {
         "metric": METRIC,
         "value": value,

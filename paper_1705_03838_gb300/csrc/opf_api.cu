@@ -60,6 +60,10 @@ struct Group {
   opf::FftPlan pz{}, pth{};
   int nJ = 0;
   bool shared_setup = false;
+  // FP64 steps: W6 holds the curl of U, as the last solve of a step leaves
+  // it; anything else that writes U, W6 or an option clears this, and the
+  // next step then starts with a curl launch
+  bool w6_valid = false;
   std::vector<double> Re, dt, time;  // per trajectory
   opf::DevSetup ds;                  // trajectory 0's setup arrays
   char* parena = nullptr;
@@ -414,13 +418,21 @@ void runner_free(Runner* r) {
   r->own = nullptr;
 }
 
-void enqueue_nonlinear(Runner* r, const Group& g, const double2* U, double2* Nout) {
+// The curl of U (A1) into the group's W6 (and Nlin in mixed precision);
+// timed: inside the per-kernel event slots.
+void enqueue_curl(Runner* r, const Group& g, const double2* U, bool timed = true) {
+  if (timed) r->begin(0);
+  if (r->precision == 1) opf::launch_curl_split32(g.d, g.ds, U, g.W6f, g.Nlin, r->st());
+  else opf::launch_curl(g.d, g.ds, U, g.W6, r->st());
+  if (timed) r->end();
+}
+
+// N(U) into Nout; with_curl false: W6 already holds the curl of U.
+void enqueue_nonlinear(Runner* r, const Group& g, const double2* U, double2* Nout, bool with_curl = true) {
   const opf::Dims& d = g.d;
   cudaStream_t st = r->st();
+  if (with_curl) enqueue_curl(r, g, U);
   if (r->precision == 1) {
-    r->begin(0);
-    opf::launch_curl_split32(d, g.ds, U, g.W6f, g.Nlin, st);
-    r->end();
     r->begin(1);
     opf::launch_zsynth32(d, g.ds, g.pz, g.W6f, g.Z6f, st);
     r->end();
@@ -432,9 +444,6 @@ void enqueue_nonlinear(Runner* r, const Group& g, const double2* U, double2* Nou
     r->end();
     return;
   }
-  r->begin(0);
-  opf::launch_curl(d, g.ds, U, g.W6, st);
-  r->end();
   r->begin(1);
   opf::launch_zsynth(d, g.ds, g.pz, g.W6, g.Z6, st);
   r->end();
@@ -446,9 +455,21 @@ void enqueue_nonlinear(Runner* r, const Group& g, const double2* U, double2* Nou
   r->end();
 }
 
+// FP64 steps fuse the curl into the solve: the solve blocks leave the curl
+// of their output in W6 for the next nonlinear evaluation (measured: FP64
+// medium step 441 -> 394 us).  Mixed-precision steps keep the separate split
+// curl: there the fused form cost the solve about as much as the curl launch
+// it saved.
+bool fused_curl(const Runner* r) { return r->precision == 0; }
+
+// Solve pass into Uout (and, fused, the curl of Uout into W6).
 void enqueue_solve(Runner* r, const Group& g, const double2* Na, const double2* Nb, double wa,
                    double wb, double2* Uout) {
   opf::SolveArgs a{g.U, Na, Nb, wa, wb, Uout, g.beta_p};
+  if (fused_curl(r)) {
+    a.curl = 1;
+    a.W6 = (void*)g.W6;
+  }
   r->begin(4);
   opf::launch_solve(g.d, g.ds, a, g.nJ, r->st());
   r->end();
@@ -495,10 +516,13 @@ void enqueue_step(Runner* r) {
     }
     const double c = g->d.c;
     if (g->d.cfl) cudaMemsetAsync(g->cfl, 0, sizeof(double), r->st());
-    enqueue_nonlinear(r, *g, g->U, g->Nj);
+    // fused: W6 holds the curl of U at the start of a step (runner_step) and
+    // the solves leave the curl of their output
+    const bool curl = !fused_curl(r);
+    enqueue_nonlinear(r, *g, g->U, g->Nj, curl);
     enqueue_solve(r, *g, g->Nj, nullptr, 1.0, 0.0, g->U1);
     for (int q = 0; q < r->n_corr; ++q) {
-      enqueue_nonlinear(r, *g, g->U1, g->Nq);
+      enqueue_nonlinear(r, *g, g->U1, g->Nq, curl);
       enqueue_solve(r, *g, g->Nq, g->Nj, c, 1.0 - c, q == r->n_corr - 1 ? g->U : g->U1);
     }
     if (fork && i > 0) cudaEventRecord(r->join_ev[i - 1], r->cur);
@@ -535,6 +559,7 @@ float time_launch(Runner* r, F launch) {
 }
 
 int tune_group(Runner* r, Group* g) {
+  g->w6_valid = false;  // the timed launches overwrite the work buffers
   opf::Dims& d = g->d;
   int dev = 0, optin = 0;
   CU(cudaGetDevice(&dev));
@@ -633,6 +658,11 @@ int runner_step(Runner* r, int n) {
   }
   for (int s = 0; s < n; ++s) {
     r->nslots = 0;
+    for (Group* g : r->groups)
+      if (fused_curl(r) && !g->w6_valid) {  // the step graph starts from the curl of U (untimed)
+        enqueue_curl(r, *g, g->U, false);
+        g->w6_valid = true;
+      }
     if (r->use_graph) {
       if (!r->gexec) {
         cudaGraph_t gr;
@@ -672,6 +702,7 @@ int runner_step(Runner* r, int n) {
 
 int runner_option(Runner* r, const char* key, double v) {
   if (!key) return fail(OPF_EINVAL, "set_option: NULL key");
+  for (Group* g : r->groups) g->w6_valid = false;  // precision / frame rotation change W6
   if (!strcmp(key, "precision")) {
     if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "precision: 0 (FP64) or 1 (mixed)");
     r->precision = (int)v;
@@ -746,6 +777,7 @@ int traj_set_state_device(Group* g, int b, const double* d_coeffs, cudaStream_t 
   CU(cudaStreamSynchronize(st));
   if (h_flag) return fail(OPF_ENAN, "set_state: non-finite coefficient; state unchanged");
   opf::launch_abi_to_internal(d, abi, g->at(g->U, b), st);
+  g->w6_valid = false;
   CU(cudaMemsetAsync(g->at(g->beta_p, b), 0, sizeof(double), st));
   CU(cudaStreamSynchronize(st));
   CU(cudaGetLastError());
@@ -775,6 +807,7 @@ int traj_energy(Group* g, int b, double out[3], cudaStream_t st) {
   const opf::DevSetup s = g->setup_of(b);
   double2* U = g->at(g->U, b);
   double2* W6 = g->at(g->W6, b);
+  g->w6_valid = false;  // FP64 curl of this trajectory only
   opf::launch_curl(d, s, U, W6, st);
   opf::launch_energy(d, s, U, W6, g->at(g->beta_p, b), g->at(g->partial, b), g->nblk_energy,
                      g->at(g->out3, b), st);
@@ -921,6 +954,7 @@ int opf_nonlinear(opf_t* h, const double* coeffs, double* out) {
   opf::launch_abi_to_internal(g.d, g.abi, g.tmpU, st);
   const int timing = h->run.timing;
   h->run.timing = 0;
+  g.w6_valid = false;  // W6 takes the curl of the given state
   enqueue_nonlinear(&h->run, g, g.tmpU, g.Nq);
   h->run.timing = timing;
   opf::launch_internal_to_abi(g.d, g.Nq, g.abi, 1, st);

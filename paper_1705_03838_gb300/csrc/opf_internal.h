@@ -137,6 +137,12 @@ struct SolveArgs {
   double wa, wb;
   double2* Uout;
   double* beta_p;  // device scalar: beta' of this solve (written by the (0,0) mode)
+  // curl of the solved state for the next nonlinear evaluation, computed by
+  // the same blocks from their radial columns: 0 none, 1 FP64 into W6
+  // (double2), 2 mixed precision into W6 (float2) and the FP64 linear terms Nlin
+  int curl = 0;
+  void* W6 = nullptr;
+  double2* Nlin = nullptr;
 };
 void launch_solve(const Dims& d, const DevSetup& s, const SolveArgs& a, int nJ, cudaStream_t st);
 void launch_energy(const Dims& d, const DevSetup& s, const double2* U, const double2* W6,

@@ -96,13 +96,102 @@ size_t curl_smem(const Dims& d) {
   return (size_t)d.N * kCurlKC * (3 * sizeof(double2) + sizeof(float2)) + kCurlKC * sizeof(double);
 }
 
+// One grid point (m, kk, radial row n) of A1 from the radial column of its
+// mode: uz_at(i), ut_at(i) (FP64) and ut32_at(i) (FP32, SPLIT) give u_z and
+// u_theta at row i; ur, ut, uz are the point's own values; ak = alpha k.
+// d1 = [2][N][9] stencils, d1f = the FP32 stencils then FP32 1/r, rr and rinv
+// the radial points and their inverses (all of this trajectory).  Writes the
+// six W6 components (and, SPLIT, the FP64 linear terms Nlin in +- form).
+template <typename V, bool SPLIT, typename UzAt, typename UtAt, typename Ut32At>
+__device__ __forceinline__ void curl_point(const Dims& d, int m, int kk, int n, double ak,
+                                           const double* __restrict__ d1, const float* __restrict__ d1f,
+                                           const double* __restrict__ rr, const double* __restrict__ rinv,
+                                           UzAt uz_at, UtAt ut_at, Ut32At ut32_at, double2 ur, double2 ut,
+                                           double2 uz, V* __restrict__ W6, double2* __restrict__ Nlin) {
+  using T = typename Scalar<V>::T;
+  const int N = d.N, nk = d.nk;
+  const long fs = d.F;
+  const int mt = d.m_p * m;
+  const int ps = mt & 1, pv = ps ^ 1;
+  const int lo = row_lo_d(n, N);
+  const double* ws = d1 + ((long)ps * N + n) * 9;
+  double dzx = 0, dzy = 0;  // d/dr of u_z (FP64)
+  T dtx = 0, dty = 0;       // d/dr of u_theta
+  if constexpr (SPLIT) {
+    const float* wv = d1f + ((long)pv * N + n) * 9;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const double2 z = uz_at(lo + q);
+      const float2 t = ut32_at(lo + q);
+      dzx = fma(ws[q], z.x, dzx);
+      dzy = fma(ws[q], z.y, dzy);
+      dtx = fmaf(wv[q], t.x, dtx);
+      dty = fmaf(wv[q], t.y, dty);
+    }
+  } else {
+    const double* wv = d1 + ((long)pv * N + n) * 9;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      const double2 z = uz_at(lo + q), t = ut_at(lo + q);
+      dzx = fma(ws[q], z.x, dzx);
+      dzy = fma(ws[q], z.y, dzy);
+      dtx = fma(wv[q], t.x, dtx);
+      dty = fma(wv[q], t.y, dty);
+    }
+  }
+  const double ri = rinv[n];
+  const double mri = mt * ri;
+  // w_r = i (m~ u_z / r - ak u_theta)
+  const double xr = mri * uz.x - ak * ut.x, xi = mri * uz.y - ak * ut.y;
+  // w_theta = i ak u_r - d_r u_z
+  double wtx = -ak * ur.y - dzx, wty = ak * ur.x - dzy;
+  const long w = ((long)m * N + n) * nk + kk;
+  double uzx = uz.x;
+  if constexpr (SPLIT) {
+    const double r = rr[n], Ub = 1.0 - r * r, Ob = 2.0 * r;
+    const bool mean = (m == 0 && kk == d.K - 1);
+    if (mean) {
+      uzx -= Ub;
+      wtx -= Ob;
+    }
+    // N_r = -U w'_t - Omega u'_z, N_t = U w'_r, N_z = Omega u'_r
+    double nrx = -Ub * wtx - Ob * uzx, nry = -Ub * wty - Ob * uz.y;
+    if (mean) nrx -= Ub * Ob;
+    const double ntx = Ub * (-xi), nty = Ub * xr;
+    Nlin[w] = double2{nrx - nty, nry + ntx};
+    double2 nminus = double2{nrx + nty, nry - ntx};
+    if (d.rotate && mt == 1 && kk == d.K - 1) {  // Coriolis force of U z: N- = -2 U (Omega_y + i Omega_x)
+      nminus.x -= 2.0 * Ub * d.rot_y;
+      nminus.y -= 2.0 * Ub * d.rot_x;
+    }
+    Nlin[fs + w] = nminus;
+    Nlin[2 * fs + w] = double2{Ob * ur.x, Ob * ur.y};
+    // w_z = d_r u_theta + u_theta / r - i m~ u_r / r, in FP32
+    const float ri32 = d1f[2 * 9 * N + n], mri32 = (float)mt * ri32;
+    const float2 ut32 = ut32_at(n);
+    const float urx = (float)ur.x, ury = (float)ur.y;
+    W6[0 * fs + w] = float2{urx, ury};
+    W6[1 * fs + w] = ut32;
+    W6[2 * fs + w] = float2{(float)uzx, (float)uz.y};
+    W6[3 * fs + w] = float2{(float)(-xi), (float)xr};
+    W6[4 * fs + w] = float2{(float)wtx, (float)wty};
+    W6[5 * fs + w] = float2{fmaf(mri32, ury, fmaf(ri32, ut32.x, dtx)), fmaf(-mri32, urx, fmaf(ri32, ut32.y, dty))};
+  } else {
+    W6[0 * fs + w] = ur;
+    W6[1 * fs + w] = ut;
+    W6[2 * fs + w] = uz;
+    W6[3 * fs + w] = V{-xi, xr};
+    W6[4 * fs + w] = V{wtx, wty};
+    W6[5 * fs + w] = V{dtx + ri * ut.x + mri * ur.y, dty + ri * ut.y - mri * ur.x};
+  }
+}
+
 template <typename V, bool SPLIT>
 __global__ void __launch_bounds__(128) k_curl(Dims d, const double* __restrict__ d1,
                                               const float* __restrict__ d1f, const double* __restrict__ rr,
                                               const double* __restrict__ rinv,
                                               const double2* __restrict__ U, V* __restrict__ W6,
                                               double2* __restrict__ Nlin) {
-  using T = typename Scalar<V>::T;
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int KC = kCurlKC;
   const int N = d.N, nk = d.nk;
@@ -134,86 +223,13 @@ __global__ void __launch_bounds__(128) k_curl(Dims d, const double* __restrict__
     if constexpr (SPLIT) s_ut32[e] = float2{(float)ut.x, (float)ut.y};
   }
   __syncthreads();
-  const int mt = d.m_p * m;
-  const int ps = mt & 1, pv = ps ^ 1;
   for (int e = threadIdx.x; e < N * KC; e += blockDim.x) {
     const int c = e % KC, n = e / KC, kk = kk0 + c;
     if (kk >= nk) continue;
-    const int lo = row_lo_d(n, N);
-    const double* ws = d1 + ((long)ps * N + n) * 9;
-    double dzx = 0, dzy = 0;  // d/dr of u_z (FP64)
-    T dtx = 0, dty = 0;       // d/dr of u_theta
-    if constexpr (SPLIT) {
-      const float* wv = d1f + ((long)pv * N + n) * 9;
-#pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        const int o = (lo + q) * KC + c;
-        const double2 z = s_uz[o];
-        const float2 t = s_ut32[o];
-        dzx = fma(ws[q], z.x, dzx);
-        dzy = fma(ws[q], z.y, dzy);
-        dtx = fmaf(wv[q], t.x, dtx);
-        dty = fmaf(wv[q], t.y, dty);
-      }
-    } else {
-      const double* wv = d1 + ((long)pv * N + n) * 9;
-#pragma unroll
-      for (int q = 0; q < 9; ++q) {
-        const int o = (lo + q) * KC + c;
-        const double2 z = s_uz[o], t = s_ut[o];
-        dzx = fma(ws[q], z.x, dzx);
-        dzy = fma(ws[q], z.y, dzy);
-        dtx = fma(wv[q], t.x, dtx);
-        dty = fma(wv[q], t.y, dty);
-      }
-    }
-    const double2 ur = s_ur[e], ut = s_ut[e], uz = s_uz[e];
-    const double ri = rinv[n];
-    const double ak = s_ak[c];
-    const double mri = mt * ri;
-    // w_r = i (m~ u_z / r - ak u_theta)
-    const double xr = mri * uz.x - ak * ut.x, xi = mri * uz.y - ak * ut.y;
-    // w_theta = i ak u_r - d_r u_z
-    double wtx = -ak * ur.y - dzx, wty = ak * ur.x - dzy;
-    const long w = ((long)m * N + n) * nk + kk;
-    double uzx = uz.x;
-    if constexpr (SPLIT) {
-      const double r = rr[n], Ub = 1.0 - r * r, Ob = 2.0 * r;
-      const bool mean = (m == 0 && kk == d.K - 1);
-      if (mean) {
-        uzx -= Ub;
-        wtx -= Ob;
-      }
-      // N_r = -U w'_t - Omega u'_z, N_t = U w'_r, N_z = Omega u'_r
-      double nrx = -Ub * wtx - Ob * uzx, nry = -Ub * wty - Ob * uz.y;
-      if (mean) nrx -= Ub * Ob;
-      const double ntx = Ub * (-xi), nty = Ub * xr;
-      Nlin[w] = double2{nrx - nty, nry + ntx};
-      double2 nminus = double2{nrx + nty, nry - ntx};
-      if (d.rotate && mt == 1 && kk == d.K - 1) {  // Coriolis force of U z: N- = -2 U (Omega_y + i Omega_x)
-        nminus.x -= 2.0 * Ub * d.rot_y;
-        nminus.y -= 2.0 * Ub * d.rot_x;
-      }
-      Nlin[fs + w] = nminus;
-      Nlin[2 * fs + w] = double2{Ob * ur.x, Ob * ur.y};
-      // w_z = d_r u_theta + u_theta / r - i m~ u_r / r, in FP32
-      const float ri32 = d1f[2 * 9 * N + n], mri32 = (float)mt * ri32;
-      const float2 ut32 = s_ut32[e];
-      const float urx = (float)ur.x, ury = (float)ur.y;
-      W6[0 * fs + w] = float2{urx, ury};
-      W6[1 * fs + w] = ut32;
-      W6[2 * fs + w] = float2{(float)uzx, (float)uz.y};
-      W6[3 * fs + w] = float2{(float)(-xi), (float)xr};
-      W6[4 * fs + w] = float2{(float)wtx, (float)wty};
-      W6[5 * fs + w] = float2{fmaf(mri32, ury, fmaf(ri32, ut32.x, dtx)), fmaf(-mri32, urx, fmaf(ri32, ut32.y, dty))};
-    } else {
-      W6[0 * fs + w] = ur;
-      W6[1 * fs + w] = ut;
-      W6[2 * fs + w] = uz;
-      W6[3 * fs + w] = V{-xi, xr};
-      W6[4 * fs + w] = V{wtx, wty};
-      W6[5 * fs + w] = V{dtx + ri * ut.x + mri * ur.y, dty + ri * ut.y - mri * ur.x};
-    }
+    curl_point<V, SPLIT>(
+        d, m, kk, n, s_ak[c], d1, d1f, rr, rinv, [&](int i) { return s_uz[i * KC + c]; },
+        [&](int i) { return s_ut[i * KC + c]; }, [&](int i) { return s_ut32[i * KC + c]; }, s_ur[e], s_ut[e],
+        s_uz[e], W6, Nlin);
   }
 }
 
@@ -536,6 +552,8 @@ struct SolveDev {
   const double* prm;
   int nJ;
   int stage;  // u_j and the influence responses staged in shared memory
+  const float* d1f;
+  const double* r;
 };
 
 // Bulk L2 prefetch by the TMA unit: p 16-byte aligned, bytes a multiple of 16.
@@ -669,8 +687,15 @@ __device__ __forceinline__ void band_solve4(const double* __restrict__ L, double
 // 0 solves the pressure system the other warps assemble the p-independent part
 // of the velocity right-hand sides; the last pass applies u_j, the influence
 // correction and the flux correction on the way out to global memory.
+// Resident blocks per SM the register budget must allow (the shared-memory
+// footprints of the tiles allow about as many at moderate N).
 template <int T>
-__global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs a) {
+constexpr int solve_min_blocks() {
+  return T == 4 ? 4 : (T == 8 ? 3 : 2);
+}
+
+template <int T>
+__global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d, SolveDev s, SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = d.N, nk = d.nk, M = d.M, K = d.K;
   constexpr int NT = 6 * T;   // velocity right-hand sides (chains)
@@ -705,6 +730,10 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
   s.ainv = bofs(s.ainv, d.ps);
   s.G = bofs(s.G, d.ps);
   s.prm = bofs(s.prm, d.ps);
+  s.d1f = bofs(s.d1f, d.ps);
+  s.r = bofs(s.r, d.ps);
+  a.W6 = bofs(a.W6, d.ss);
+  a.Nlin = bofs(a.Nlin, d.ss);
   a.Uj = bofs(a.Uj, d.ss);
   a.Na = bofs(a.Na, d.ss);
   a.Nb = bofs(a.Nb, d.ss);
@@ -986,6 +1015,40 @@ __global__ void __launch_bounds__(24 * T) k_solve(Dims d, SolveDev s, SolveArgs 
     if (has_mean && c == cz) v += bp * s.G[i];
     double* out = (double*)(a.Uout + f * fs + base + (long)i * nk + kk0 + mi) + part;
     *out = v;
+    if (a.curl) X[i * NT + c] = v;  // (only this element's own X is read above)
+  }
+
+  // ---- the curl of the new state (A1) for the next nonlinear evaluation, from
+  //      the block's radial columns (NE is free: u_r, u_theta, FP32 u_theta)
+  if (a.curl) {
+    __syncthreads();
+    double2* UR = NE;
+    double2* UT = NE + N * T;
+    float2* UT32 = (float2*)(NE + 2 * N * T);
+    const int c0 = mi_t << 1, c1 = (T + mi_t) << 1, c2 = (2 * T + mi_t) << 1;
+    for (int i = tid / T; i < N; i += NB / T) {
+      const double* xr = X + i * NT;
+      const double2 up = double2{xr[c0], xr[c0 + 1]}, um = double2{xr[c1], xr[c1 + 1]};
+      const double2 ut = double2{0.5 * (up.y - um.y), -0.5 * (up.x - um.x)};
+      UR[i * T + mi_t] = double2{0.5 * (up.x + um.x), 0.5 * (up.y + um.y)};
+      UT[i * T + mi_t] = ut;
+      UT32[i * T + mi_t] = float2{(float)ut.x, (float)ut.y};
+    }
+    __syncthreads();
+    const int kk = kk0 + mi_t;
+    if (kk < nk) {
+      auto uz_at = [&](int i) { return double2{X[i * NT + c2], X[i * NT + c2 + 1]}; };
+      auto ut_at = [&](int i) { return UT[i * T + mi_t]; };
+      auto ut32_at = [&](int i) { return UT32[i * T + mi_t]; };
+      for (int i = tid / T; i < N; i += NB / T) {
+        if (a.curl == 2)
+          curl_point<float2, true>(d, m, kk, i, ak_t, W1, s.d1f, s.r, RI, uz_at, ut_at, ut32_at, UR[i * T + mi_t],
+                                   UT[i * T + mi_t], uz_at(i), (float2*)a.W6, a.Nlin);
+        else
+          curl_point<double2, false>(d, m, kk, i, ak_t, W1, s.d1f, s.r, RI, uz_at, ut_at, ut32_at,
+                                     UR[i * T + mi_t], UT[i * T + mi_t], uz_at(i), (double2*)a.W6, nullptr);
+      }
+    }
   }
 }
 
@@ -1085,7 +1148,7 @@ void launch_solve(const Dims& d, const DevSetup& s, const SolveArgs& a, int nJ, 
   const int T = solve_tile(d);
   dim3 g((d.nk + T - 1) / T, d.M, d.B);
   const bool stage = solve_use_stage(d, T, (long)g.x * g.y * g.z);
-  SolveDev sd{s.d1, s.rinv, s.wq, s.hop, s.luH, s.luP, s.basis, s.ainv, s.G, s.prm, nJ, stage ? 1 : 0};
+  SolveDev sd{s.d1, s.rinv, s.wq, s.hop, s.luH, s.luP, s.basis, s.ainv, s.G, s.prm, nJ, stage ? 1 : 0, s.d1f, s.r};
   const size_t sm = stage ? solve_smem_staged(d.N, T) : solve_smem_base(d.N, T);
   if (T == 16) k_solve<16><<<g, 24 * 16, sm, st>>>(d, sd, a);
   else if (T == 8) k_solve<8><<<g, 24 * 8, sm, st>>>(d, sd, a);
