@@ -47,8 +47,10 @@ def gpu_run(opf, N, K, M, m_p, alpha, Re, dt, U0, nsteps, **opts):
 
 
 # ---------------------------------------------------------------- stages
+# the last five hit the compiled FFT plans: 3K or 3M in 48, 72, 96, 192, 384
 @pytest.mark.parametrize("N,K,M,m_p", [(16, 4, 6, 1), (12, 3, 4, 2), (9, 1, 1, 1), (20, 5, 3, 3),
-                                       (32, 16, 16, 1)])
+                                       (32, 16, 16, 1), (10, 24, 32, 1), (10, 64, 2, 1), (10, 2, 64, 2),
+                                       (9, 128, 2, 1), (9, 2, 128, 1)])
 def test_nonlinear_term_matches_oracle(opf, N, K, M, m_p):
     alpha, Re = 1.25, 1000.0
     U0 = inputs.seeded_state(N, K, M, m_p, alpha, 0.1, 77)
@@ -56,6 +58,55 @@ def test_nonlinear_term_matches_oracle(opf, N, K, M, m_p):
     got = opf.opf_nonlinear(h, U0)
     want = Oracle(Params(N, K, M, m_p, alpha, Re, 0.01)).nonlinear(U0)
     assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("N,K,M,m_p", [(10, 24, 32, 1), (10, 64, 2, 1), (9, 2, 128, 1)])
+def test_mixed_nonlinear_term_on_compiled_plans(opf, N, K, M, m_p):
+    """FP32 transforms with compiled plans (72, 96, 192, 384 points) against
+    the FP64 oracle: FP32 round-off only."""
+    alpha, Re = 1.25, 1000.0
+    U0 = inputs.seeded_state(N, K, M, m_p, alpha, 0.1, 78)
+    h = opf.opf_create(N, K, M, m_p, alpha, Re, 0.01)
+    opf.opf_set_option(h, "precision", 1)
+    got = opf.opf_nonlinear(h, U0)
+    want = Oracle(Params(N, K, M, m_p, alpha, Re, 0.01)).nonlinear(U0)
+    assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
+
+
+def test_fp64_steps_with_interleaved_calls_equal_plain_steps(opf):
+    """FP64 steps take the curl of each solved state inside the solve; every
+    call that writes the state or the work buffers in between (energy, the
+    nonlinear term of another state, an option, set_state) must leave the
+    next step starting from the curl of the current state.  A stale curl
+    would change the result at the size of the perturbation; the only
+    difference allowed is the round-off of the set_state(get_state) round
+    trip (u+- <-> u_r, u_theta)."""
+    N, K, M, m_p, alpha, Re, dt = 16, 4, 4, 1, 1.25, 800.0, 0.01
+    U0 = inputs.seeded_state(N, K, M, m_p, alpha, 0.05, 321)
+    other = inputs.seeded_state(N, K, M, m_p, alpha, 0.05, 322)
+    h, plain = gpu_run(opf, N, K, M, m_p, alpha, Re, dt, U0, 6)
+    h2 = opf.opf_create(N, K, M, m_p, alpha, Re, dt)
+    opf.opf_set_state(h2, U0)
+    opf.opf_step(h2, 2)
+    opf.opf_energy(h2)
+    opf.opf_step(h2, 1)
+    opf.opf_nonlinear(h2, other)
+    opf.opf_step(h2, 1)
+    opf.opf_set_option(h2, "n_corr", 1)
+    opf.opf_step(h2, 1)
+    opf.opf_set_state(h2, opf.opf_get_state(h2))
+    opf.opf_step(h2, 1)
+    assert rel(opf.opf_get_state(h2), plain) < 1e-13
+    # a mixed-precision step, then FP64 steps: as if started from that state
+    h3 = opf.opf_create(N, K, M, m_p, alpha, Re, dt)
+    opf.opf_set_state(h3, U0)
+    opf.opf_set_option(h3, "precision", 1)
+    opf.opf_step(h3, 1)
+    mid = opf.opf_get_state(h3)
+    opf.opf_set_option(h3, "precision", 0)
+    opf.opf_step(h3, 2)
+    _, ref = gpu_run(opf, N, K, M, m_p, alpha, Re, dt, mid, 2)
+    assert rel(opf.opf_get_state(h3), ref) < 1e-13
 
 
 def test_state_round_trip_and_hermitian_projection(opf):
