@@ -106,7 +106,9 @@ def test_fp64_steps_with_interleaved_calls_equal_plain_steps(opf):
     opf.opf_set_option(h3, "precision", 0)
     opf.opf_step(h3, 2)
     _, ref = gpu_run(opf, N, K, M, m_p, alpha, Re, dt, mid, 2)
-    assert rel(opf.opf_get_state(h3), ref) < 1e-13
+    # set_state also projects the m = 0 modes of the mixed-precision state
+    # onto Hermitian symmetry (FP32 round-off breaks it slightly): ~1e-12
+    assert rel(opf.opf_get_state(h3), ref) < 1e-10
 
 
 def test_state_round_trip_and_hermitian_projection(opf):
