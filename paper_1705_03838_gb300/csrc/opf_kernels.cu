@@ -1075,14 +1075,19 @@ static size_t solve_smem(int N, int T) {
 // holds as many blocks as the grid can use (so staging never costs occupancy).
 static bool solve_use_stage(const Dims& d, int T, long blocks) {
   if (!solve_stage_fits(d.N, T)) return false;
-  static int sms = 0, smem_sm = 0;
-  if (!sms) {
+  struct SmInfo {
+    int sms = 1, smem_sm = 0;
+  };
+  static const SmInfo info = [] {  // (thread-safe one-time initialisation)
+    SmInfo i;
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&i.sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&i.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (i.sms <= 0) i.sms = 1;
+    return i;
+  }();
+  const int sms = info.sms, smem_sm = info.smem_sm;
   const size_t reserve = 1024;  // per-block shared memory the system keeps
   const long with = (long)(smem_sm / (solve_smem_staged(d.N, T) + reserve));
   const long without = (long)(smem_sm / (solve_smem_base(d.N, T) + reserve));
