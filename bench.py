@@ -108,6 +108,24 @@ def step_algorithmic_bytes(w, precision):
     return (528 if precision == 0 else 432) * F
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest per-rank value over the ranks of the process group (x
+    itself without one): the job's time is its slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (each rank processes the same number of units)."""
+    return units_per_rank * world / seconds
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -630,10 +648,7 @@ def run_gpu(args, w):
         kt = {k: (v[0] / max(1, v[1]), 1) for k, v in kt_all.items()}
         kt[dom] = (kt_live[dom][0] / max(1, kt_live[dom][1]), 1)
         energy = opf.opf_energy(h)
-        if world > 1:
-            t = torch.tensor([total], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+        total = max_over_ranks(total, dist, "cuda")
         return total, kt, clk, wall, energy
 
     res = {}
@@ -656,18 +671,14 @@ def run_gpu(args, w):
         E = opf.opf_energy(h)
     torch.cuda.synchronize()
     e2e_s = time.time() - t0
-    e2e_rate = e2e_steps / e2e_s
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_rate = e2e_steps * world / float(t.item())
+    e2e_rate = job_rate(e2e_steps, world, max_over_ranks(e2e_s, dist, "cuda"))
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
 
-    value = args.steps * world / (total_ms / 1000.0)
+    value = job_rate(args.steps, world, total_ms / 1000.0)
     peaks, peak_kind = load_peaks()
     def roofline(kt, precision):
         costs = kernel_costs(w, precision)
@@ -684,8 +695,8 @@ def run_gpu(args, w):
                 "share": {k: v[0] / tot for k, v in kt.items()}}
 
     roof = roofline(ktimes, args.precision)
-    fp64_value = args.steps * world / (res[0][0] / 1000.0)
-    mixed_value = args.steps * world / (res[1][0] / 1000.0)
+    fp64_value = job_rate(args.steps, world, res[0][0] / 1000.0)
+    mixed_value = job_rate(args.steps, world, res[1][0] / 1000.0)
     hbm_frac = step_algorithmic_bytes(w, args.precision) * value / world / (peaks["hbm_gbs"] * 1e9)
 
     cpu = None
