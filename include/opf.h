@@ -139,7 +139,10 @@ int opf_set_stream(opf_t* h, void* stream);
 
 /* Per-kernel device time of the steps run since the last call with reset=1:
  * names[i] (library-owned) and total_ms[i], launches[i] for i < *count
- * (capacity cap).  Collected only while option "timing" = 1. */
+ * (capacity cap).  Collected only while option "timing" = 1.  In FP64 steps
+ * the curl is taken inside the solve launches (its own kernel runs only when
+ * a step starts after the state, the work buffers or an option changed, and
+ * is not timed then), so "curl" reports no launches there. */
 int opf_kernel_times(opf_t* h, int cap, int* count, const char** names,
                      double* total_ms, int* launches, int reset);
 
