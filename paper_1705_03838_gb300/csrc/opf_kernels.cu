@@ -685,8 +685,11 @@ __device__ __forceinline__ void band_solve4(const double* __restrict__ L, double
 // sequential in r, with 4 lanes per real right-hand side (2T pressure chains,
 // then 6T velocity chains = (u+, u-, u_z) x T modes x (re, im)).  While warp
 // 0 solves the pressure system the other warps assemble the p-independent part
-// of the velocity right-hand sides; the last pass applies u_j, the influence
-// correction and the flux correction on the way out to global memory.
+// of the velocity right-hand sides (and stage u_j and the influence
+// responses); the last pass applies u_j, the influence correction and the
+// flux correction on the way out to global memory, and with a.curl the block
+// then takes the curl of its new state for the next nonlinear evaluation.
+//
 // Resident blocks per SM the register budget must allow (the shared-memory
 // footprints of the tiles allow about as many at moderate N).
 template <int T>
