@@ -259,6 +259,44 @@ def test_bessel_swirl_decays_at_exact_rate():
     assert 3.5 < errs[0] / errs[1] < 4.5
 
 
+def test_linear_limit_is_quadratic_in_the_amplitude():
+    """Hagen-Poiseuille is a fixed point of the step and u x w is quadratic,
+    so a step from u_lam + eps v gives (S - u_lam)/eps = A v + eps B(v) +
+    O(eps^2): halving eps halves the difference of successive quotients.  A
+    stray constant term (a wrong driving force) or a cubic one breaks the
+    ratio 2."""
+    N, K, M, m_p, alpha, Re, dt = 16, 3, 3, 1, 1.25, 500.0, 0.01
+    lam = inputs.laminar_state(N, K, M)
+    v = inputs.seeded_state(N, K, M, m_p, alpha, 1.0, 5, laminar=False)
+    o = Oracle(Params(N, K, M, m_p, alpha, Re, dt))
+    q = [(o.step(lam + eps * v, 3) - lam) / eps for eps in (1e-2, 5e-3, 2.5e-3, 1.25e-3)]
+    d = [np.linalg.norm(q[i] - q[i + 1]) for i in range(3)]
+    assert d[0] > 1e-6 * np.linalg.norm(q[0])  # the nonlinear term is there
+    assert abs(d[0] / d[1] - 2.0) < 2e-3 and abs(d[1] / d[2] - 2.0) < 2e-3
+
+
+def test_radial_refinement_of_the_step():
+    """Two steps from one smooth field on N = 16 ... 40 radial points (the
+    field and the results moved between meshes by the 9-point interpolation,
+    itself exact on polynomials) against N = 64: the error falls
+    monotonically and reaches the order of the 9-point stencils (section 2:
+    orders 8 and 7) by N = 32 ... 40."""
+    from oracle.opf_oracle import change_resolution
+
+    K, M, alpha, Re, dt, NF = 3, 3, 1.25, 500.0, 0.01, 64
+    U0 = inputs.seeded_state(NF, K, M, 1, alpha, 0.05, 9)
+    ref = Oracle(Params(NF, K, M, 1, alpha, Re, dt)).step(U0, 2)
+    scale = np.linalg.norm(ref - inputs.laminar_state(NF, K, M))
+    Ns = (16, 24, 32, 40)
+    errs = []
+    for n in Ns:
+        U = Oracle(Params(n, K, M, 1, alpha, Re, dt)).step(change_resolution(U0, n, K, M, 1), 2)
+        errs.append(np.linalg.norm(change_resolution(U, NF, K, M, 1) - ref) / scale)
+    assert all(errs[i + 1] < errs[i] for i in range(3))
+    order = math.log(errs[2] / errs[3]) / math.log(Ns[3] / Ns[2])
+    assert order > 5.5, (errs, order)
+
+
 def test_wall_conditions_at_round_off():
     """||g|| (no-slip and wall divergence) at machine epsilon (section 2)."""
     N, K, M = 16, 4, 4
