@@ -259,6 +259,94 @@ def test_bessel_swirl_decays_at_exact_rate():
     assert 3.5 < errs[0] / errs[1] < 4.5
 
 
+def test_swirl_amplitude_per_step_follows_the_theta_method_at_c_not_half():
+    """Implicitness c != 1/2 with two correctors: u x omega of the swirl is a
+    pure radial gradient, so every corrector leaves the viscous update alone
+    and each step multiplies the swirl by the theta-method factor
+    g = (1 + (1-c) lambda dt) / (1 - c lambda dt), lambda = -j^2/Re
+    (section 2: c weights the implicit viscous term).  At c = 0.6 g^n differs
+    from exp(lambda t) by ~(c - 1/2) lambda^2 dt t = 4e-5; the closed form
+    holds to the spatial truncation level (~1e-9 at N = 24)."""
+    j1 = sps.jn_zeros(1, 1)[0]
+    N, K, M, Re, dt, n, c = 24, 2, 2, 50.0, 0.01, 50, 0.6
+    o = Oracle(Params(N, K, M, 1, 1.25, Re, dt, c=c, n_corr=2))
+    U = o.step(_swirl(N, K, M, 1e-2, j1), n)
+    lam = -j1 ** 2 / Re
+    g = (1 + (1 - c) * lam * dt) / (1 - c * lam * dt)
+    shape = 1e-2 * sps.j1(j1 * o.r)
+    err_theta = np.abs(U[1, 0, K - 1] - g ** n * shape).max() / 1e-2
+    err_exp = np.abs(U[1, 0, K - 1] - math.exp(lam * n * dt) * shape).max() / 1e-2
+    assert err_theta < 2e-8
+    assert err_exp > 1e-5  # the c = 0.6 scheme is not second order
+
+
+def _time_refinement(c, n_corr, dts, ref, U0, T, args):
+    errs = []
+    lam = inputs.laminar_state(args[0], args[1], args[2])
+    for dt in dts:
+        U = Oracle(Params(*args, dt, c=c, n_corr=n_corr)).step(U0, int(round(T / dt)))
+        errs.append(np.linalg.norm(U - ref) / np.linalg.norm(ref - lam))
+    return errs
+
+
+@pytest.fixture(scope="module")
+def refinement_case():
+    """A nonlinear run (amplitude 0.3, Re = 5000, N = 12) to T = 0.4, and a
+    reference at dt = 0.05/64 shared by every scheme below."""
+    args = (12, 3, 3, 1, 1.25, 5000.0)
+    U0 = inputs.seeded_state(12, 3, 3, 1, 1.25, 0.3, 31)
+    T, dtr = 0.4, 0.05 / 64
+    ref = Oracle(Params(*args, dtr, n_corr=3)).step(U0, int(round(T / dtr)))
+    return args, U0, T, ref
+
+
+@pytest.mark.parametrize("c,n_corr,lo,hi", [(0.5, 1, 1.7, 2.5), (0.5, 2, 1.7, 2.5),
+                                            (0.6, 1, 0.8, 1.25), (0.6, 2, 0.8, 1.25)])
+def test_time_refinement_order_of_the_predictor_corrector(refinement_case, c, n_corr, lo, hi):
+    """Section 2's predictor-corrector: second order at c = 1/2 with one or
+    two corrector iterations, first order at c = 0.6 (weights c, 1 - c on
+    both the viscous and the nonlinear term).  Every scheme converges to the
+    same limit, so the weights of each term sum to one.  A corrector that
+    took N from u_j instead of from the latest iterate would fall to first
+    order at n_corr = 2; a nonlinear weight pair that did not sum to one
+    would stall against the common reference."""
+    args, U0, T, ref = refinement_case
+    errs = _time_refinement(c, n_corr, (0.025, 0.0125, 0.00625), ref, U0, T, args)
+    order = math.log2(errs[1] / errs[2])
+    assert lo < order < hi, (errs, order)
+    assert errs[2] < (5e-5 if c == 0.5 else 5e-4)
+
+
+@pytest.mark.parametrize("c,n_corr", [(0.6, 1), (0.4, 2)])
+def test_first_order_error_constant_of_the_theta_weights(c, n_corr):
+    """With both the viscous and the nonlinear term weighted c (new level) and
+    1 - c (old level), the local error of a step is (c - 1/2) dt^2 u'' + O(dt^3),
+    so over a short time T the global error is (c - 1/2) dt (u'(T) - u'(0))
+    to leading order.  u' comes from a fine reference trajectory by one-sided
+    differences, the O(dt^2) part of the error is removed by Richardson
+    extrapolation over dt and dt/2.  Swapping the two nonlinear weights keeps
+    the scheme consistent and first order but flips the sign of the
+    (dominant) advective part of this error: the cosine goes to ~ -0.9."""
+    args = (12, 3, 3, 1, 1.25, 5000.0)
+    U0 = inputs.seeded_state(12, 3, 3, 1, 1.25, 0.3, 31)
+    T, dtr = 0.05, 0.05 / 400
+    o = Oracle(Params(*args, dtr, n_corr=3))
+    traj = [U0]
+    for _ in range(int(round(T / dtr))):
+        traj.append(o.step(traj[-1], 1))
+    ud0 = (-3 * traj[0] + 4 * traj[1] - traj[2]) / (2 * dtr)
+    udT = (3 * traj[-1] - 4 * traj[-2] + traj[-3]) / (2 * dtr)
+    pred = (c - 0.5) * (udT - ud0)
+    es = []
+    for dt in (0.005, 0.0025):
+        V = Oracle(Params(*args, dt, c=c, n_corr=n_corr)).step(U0, int(round(T / dt)))
+        es.append((V - traj[-1]) / dt)
+    e = 2 * es[1] - es[0]
+    cos = np.real(np.vdot(e, pred)) / (np.linalg.norm(e) * np.linalg.norm(pred))
+    ratio = np.linalg.norm(e) / np.linalg.norm(pred)
+    assert cos > 0.7 and 0.8 < ratio < 1.25, (cos, ratio)
+
+
 def test_linear_limit_is_quadratic_in_the_amplitude():
     """Hagen-Poiseuille is a fixed point of the step and u x w is quadratic,
     so a step from u_lam + eps v gives (S - u_lam)/eps = A v + eps B(v) +
