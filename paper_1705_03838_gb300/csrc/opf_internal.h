@@ -102,6 +102,7 @@ struct Dims {
 
 void choose_chunks(Dims* d);
 bool prepare_kernel_attrs(const Dims& d);
+bool prepare_nonlinear_attrs(const Dims& d);  // FP64 nonlinear-term kernels only
 // Shared memory a launch shape needs (autotuner candidates must fit).
 size_t zsynth_smem(const Dims& d, int mc, size_t vb);
 size_t zanalysis_smem(const Dims& d, int mc, size_t vb);

@@ -1152,6 +1152,34 @@ bool prepare_kernel_attrs(const Dims& d) {
   return ok;
 }
 
+// Shared-memory limits of the FP64 nonlinear-term kernels only (curl, z
+// synthesis, theta product, z analysis) for the allocation-free entry point:
+// checks their footprints against the opt-in limit and raises their dynamic
+// shared-memory limit to it.
+bool prepare_nonlinear_attrs(const Dims& d) {
+  const size_t vb = sizeof(double2);
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return false;
+  const size_t lim = (size_t)optin;
+  if (zsynth_smem(d, d.mcz, vb) > lim || zanalysis_smem(d, d.mca, vb) > lim || curl_smem(d) > lim ||
+      product_smem(d, d.zc, vb) > lim)
+    return false;
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  bool ok = cudaFuncSetAttribute(k_curl<double2, false>, a, optin) == cudaSuccess;
+  with_fft_length(d.nz, [&](auto n) {
+    constexpr int L = decltype(n)::value;
+    ok = ok && cudaFuncSetAttribute(k_zsynth<double2, L>, a, optin) == cudaSuccess;
+    ok = ok && cudaFuncSetAttribute(k_zanalysis<double2, L>, a, optin) == cudaSuccess;
+  });
+  with_fft_length(d.nth, [&](auto n) {
+    constexpr int L = decltype(n)::value;
+    ok = ok && cudaFuncSetAttribute(k_product<double2, L>, a, optin) == cudaSuccess;
+  });
+  return ok;
+}
+
 void launch_solve(const Dims& d, const DevSetup& s, const SolveArgs& a, int nJ, cudaStream_t st) {
   const int T = solve_tile(d);
   dim3 g((d.nk + T - 1) / T, d.M, d.B);

@@ -18,9 +18,17 @@
 //    to start at zero.  Calls whose GPU work overlaps (different streams or
 //    threads without ordering) race on the array.
 //  * The first call on a device looks up the array's device address there
-//    (cudaGetSymbolAddress); make that first call before any stream capture.
+//    (cudaGetSymbolAddress) and sets the kernels' shared-memory limits; make
+//    that first call before any stream capture.  CUDA loads modules lazily,
+//    so it is also that first call (not loading the library) that places the
+//    16 MiB array and the kernels' code on the device: make it at start-up,
+//    before the caller's own pool takes the device memory.
+//  * The call waits for its result (it synchronises the stream) before it
+//    returns, so it refuses, with OPF_EINVAL and before launching anything,
+//    a stream that is being captured.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 
 #include "opf_internal.h"
@@ -35,6 +43,15 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 void* g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Transform lengths (3K, 3M) whose kernels already have their shared-memory
+// limit raised, per device, in a fixed table (no host allocation either); the
+// attributes are set once per device and shape (every call, once the table
+// is full).
+constexpr int kAttrSlots = 32;
+std::mutex g_attr_mutex;
+long g_attr_done[kMaxDevices][kAttrSlots] = {};
+int g_attr_count[kMaxDevices] = {};
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -159,6 +176,16 @@ extern "C" int opf_nonlinear_noalloc(int N, int K, int M, int m_p, double alpha,
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return fail(OPF_ECUDA, "opf_nonlinear_noalloc: no usable CUDA device");
+  cudaStream_t st = (cudaStream_t)stream;
+  {  // the call ends with a stream synchronisation, which a capture forbids
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+      if (e != cudaSuccess) cudaGetLastError();  // leave no sticky status behind
+      return fail(OPF_EINVAL, "opf_nonlinear_noalloc: the stream is being captured (or its capture state "
+                              "cannot be read); this call synchronises its stream and cannot run inside a capture");
+    }
+  }
   if (!g_scratch_addr[dev]) {  // once per device, with that device current
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -167,8 +194,17 @@ extern "C" int opf_nonlinear_noalloc(int N, int K, int M, int m_p, double alpha,
                                  cudaGetErrorString(e));
     g_scratch_addr[dev] = p;
   }
-  if (!opf::prepare_kernel_attrs(d))
-    return fail(OPF_EINVAL, "opf_nonlinear_noalloc: resolution needs more shared memory than a block has");
+  {
+    const long key = (long)d.nz << 20 | d.nth;
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    long* done = g_attr_done[dev];
+    int& count = g_attr_count[dev];
+    if (std::find(done, done + count, key) == done + count) {
+      if (!opf::prepare_nonlinear_attrs(d))
+        return fail(OPF_EINVAL, "opf_nonlinear_noalloc: resolution needs more shared memory than a block has");
+      if (count < kAttrSlots) done[count++] = key;
+    }
+  }
   unsigned char* base = (unsigned char*)g_scratch_addr[dev];
   opf::DevSetup s{};
   s.prm = (double*)(base + o_prm);
@@ -182,7 +218,6 @@ extern "C" int opf_nonlinear_noalloc(int N, int K, int M, int m_p, double alpha,
   double2* Z6 = (double2*)(base + o_Z6);
   double2* ZN = (double2*)(base + o_ZN);
   double2* Nn = (double2*)(base + o_N);
-  cudaStream_t st = (cudaStream_t)stream;
 
   const int nc = std::max(N, std::max(d.nz, d.nth));
   k_noalloc_consts<<<(nc + 127) / 128, 128, 0, st>>>(N, d.nz, d.nth, Re, s.prm, s.d1, s.rinv, s.tw_z,

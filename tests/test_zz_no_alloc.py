@@ -61,3 +61,43 @@ def test_noalloc_second_shape_and_rejections(env):
     with pytest.raises(opf.OpfError) as e:
         opf.opf_nonlinear_noalloc(48, 32, 24, 2, 1.25, 2400.0, d_in.data_ptr(), d_out.data_ptr())
     assert e.value.code == opf.OPF_EINVAL and "scratch" in str(e.value)
+
+
+def test_noalloc_calls_after_the_first_take_no_device_memory(env):
+    """The contract itself: once the first call on the device has placed the
+    array and the kernels there, further calls leave free device memory as
+    it was (torch's caching allocator holds the buffers made beforehand)."""
+    torch, opf = env
+    N, K, M, m_p, alpha, Re = 16, 4, 6, 1, 1.25, 800.0
+    d_in = _device(torch, inputs.seeded_state(N, K, M, m_p, alpha, 0.1, 21))
+    d_out = torch.empty_like(d_in)
+    st = torch.cuda.current_stream().cuda_stream
+    opf.opf_nonlinear_noalloc(N, K, M, m_p, alpha, Re, d_in.data_ptr(), d_out.data_ptr(), st)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(5):
+        opf.opf_nonlinear_noalloc(N, K, M, m_p, alpha, Re, d_in.data_ptr(), d_out.data_ptr(), st)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
+def test_noalloc_refuses_a_capturing_stream_without_breaking_the_capture(env):
+    """The call synchronises its stream, so under capture it must return the
+    documented error before launching anything, leaving the capture valid."""
+    torch, opf = env
+    N, K, M, m_p, alpha, Re = 12, 3, 4, 2, 1.0, 500.0
+    d_in = _device(torch, inputs.seeded_state(N, K, M, m_p, alpha, 0.1, 6))
+    d_out = torch.empty_like(d_in)
+    opf.opf_nonlinear_noalloc(N, K, M, m_p, alpha, Re, d_in.data_ptr(), d_out.data_ptr())  # first call
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        y = d_in * 2.0
+        with pytest.raises(opf.OpfError) as e:
+            opf.opf_nonlinear_noalloc(N, K, M, m_p, alpha, Re, d_in.data_ptr(), d_out.data_ptr(),
+                                      side.cuda_stream)
+    assert e.value.code == opf.OPF_EINVAL and "captur" in str(e.value)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y, d_in * 2.0)
