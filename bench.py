@@ -229,6 +229,78 @@ print(json.dumps({{"steps": n, "seconds": el, "setup": setup}}))
     return res["steps"] / res["seconds"], res["steps"], res["setup"], res["seconds"]
 
 
+def oracle_timing_all_cores(seconds_budget=10.0):
+    """The oracle on all host cores: one single-threaded oracle process per
+    core (memory permitting), each stepping its own seeded trajectory of the
+    same workload; returns (aggregate steps/s, processes, total steps)."""
+    nproc = os.cpu_count() or 1
+    try:  # ~1.2 GB per medium oracle process (LU factors of 1512 modes)
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        nproc = max(1, min(nproc, int(avail // (1.5 * 2 ** 30))))
+    except (ValueError, OSError, AttributeError):
+        pass
+    code = f"""
+import sys, time, json
+sys.path.insert(0, {ROOT!r})
+from oracle.opf_oracle import Oracle, Params
+from paper_1705_03838_gb300 import inputs
+w = inputs.WORKLOADS[{WORKLOAD!r}]
+rank = int(sys.argv[1])
+o = Oracle(Params(w['N'], w['K'], w['M'], w['m_p'], w['alpha'], w['Re'], w['dt']))
+U = inputs.seeded_state(w['N'], w['K'], w['M'], w['m_p'], w['alpha'], w['amplitude'], w['seed'] + rank,
+                        w['envelope'])
+U = o.step(U, 1)
+n = 0; t0 = time.time()
+while True:
+    U = o.step(U, 1); n += 1
+    el = time.time() - t0
+    if el > {seconds_budget}:
+        break
+print(json.dumps({{"steps": n, "seconds": el}}))
+"""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    procs = [subprocess.Popen([sys.executable, "-c", code, str(i)], stdout=subprocess.PIPE,
+                              stderr=subprocess.PIPE, text=True, env=env) for i in range(nproc)]
+    rate, steps = 0.0, 0
+    for p in procs:
+        out, err = p.communicate()
+        if p.returncode != 0:
+            raise RuntimeError("oracle timing failed: " + err[-2000:])
+        res = json.loads(out.strip().splitlines()[-1])
+        rate += res["steps"] / res["seconds"]
+        steps += res["steps"]
+    return rate, nproc, steps
+
+
+def oracle_small_full():
+    """The small workload in full (100 steps, N=32, |k|<16, m<16) on one core."""
+    code = f"""
+import sys, time, json
+sys.path.insert(0, {ROOT!r})
+from oracle.opf_oracle import Oracle, Params
+from paper_1705_03838_gb300 import inputs
+w = inputs.WORKLOADS['small']
+o = Oracle(Params(w['N'], w['K'], w['M'], w['m_p'], w['alpha'], w['Re'], w['dt']))
+U = inputs.workload_state('small')
+t0 = time.time(); U = o.step(U, 100); el = time.time() - t0
+print(json.dumps({{"steps": 100, "seconds": el, "energy": [float(x) for x in o.energy(U)]}}))
+"""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+LARGE_ORACLE_NOTE = ("large workload (N=128, |k|<128, m<128) not stepped on the host: the oracle's dense "
+                     "solve factors 32,640 complex systems of order 513 per dt (~47 TFLOP of LU), hours "
+                     "per step; it is checked instead on its nonlinear term and sampled-mode solves")
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -366,6 +438,46 @@ def run_ensemble(args):
     print(json.dumps(line), flush=True)
 
 
+def large_oracle_check(opf, w):
+    """Errors of the large grid against the FP64 oracle where the oracle can
+    follow: the nonlinear term of the start (FP64 and mixed precision), and
+    one FP64 predictor-only step (n_corr = 0) on sampled modes, whose dense
+    solves the oracle affords one by one."""
+    import numpy as np
+
+    from oracle.opf_oracle import Oracle, Params
+    from paper_1705_03838_gb300 import inputs
+
+    args_h = (w["N"], w["K"], w["M"], w["m_p"], w["alpha"], w["Re"], 2e-5)
+    U0 = inputs.workload_state("large")
+    t0 = time.time()
+    o = Oracle(Params(*args_h))
+    Nref = o.nonlinear(U0)
+    K = w["K"]
+    modes = [(0, K - 1), (0, K), (1, K - 2), (17, K - 34), (64, K + 90), (100, K - 121), (127, 2 * K - 2)]
+    sub = o.solve_modes(U0, Nref, modes)
+    host_s = time.time() - t0
+    h = opf.opf_create(*args_h)
+    out = {}
+    for prec, name in ((0, "fp64"), (1, "mixed")):
+        opf.opf_set_option(h, "precision", prec)
+        got = opf.opf_nonlinear(h, U0)
+        out[f"nonlinear_{name}_rel_l2"] = float(np.linalg.norm(got - Nref) / np.linalg.norm(Nref))
+    opf.opf_set_option(h, "precision", 0)
+    opf.opf_set_option(h, "n_corr", 0)
+    opf.opf_set_state(h, U0)
+    opf.opf_step(h, 1)
+    U1 = opf.opf_get_state(h)
+    got = np.stack([U1[:, m, kk] for m, kk in modes])
+    want = np.stack([sub[mk][0] for mk in modes])
+    out["predictor_solve_fp64_rel_l2_on_sampled_modes"] = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+    out["sampled_modes_m_kk"] = modes
+    out["oracle_host_seconds"] = host_s
+    out["note"] = LARGE_ORACLE_NOTE
+    opf.opf_destroy(h)
+    return out
+
+
 def run_large(args):
     """Large turbulent-start run, mixed precision: Re=5300, alpha=0.4
     (L = 5 pi R), N=128, |k|<128, m<128, m_p=1, broadband perturbation of
@@ -423,6 +535,23 @@ def run_large(args):
     torch.cuda.synchronize()
     res[1] = {"ms_per_step": ev0.elapsed_time(ev1) / args.steps, "steps": args.steps,
               "dt_min": min(dts), "dt_max": max(dts), "E": E50}
+    # kernel shares and the dominant kernel's rate from two instrumented steps
+    opf.opf_set_option(h, "timing", 1)
+    opf.opf_kernel_times(h, reset=True)
+    opf.opf_step(h, 2)
+    kt = opf.opf_kernel_times(h, reset=True)
+    opf.opf_set_option(h, "timing", 0)
+    costs = kernel_costs(w, 1)
+    per = {k: v[0] / max(1, v[1]) for k, v in kt.items() if v[1] > 0}
+    dom = max(per, key=per.get)
+    pk, src = kernel_peak(dom, 1)
+    ach = costs[dom]["flops"] / (per[dom] * 1e-3) / 1e12
+    tot = sum(v[0] for v in kt.values())
+    roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+            "traffic": None, "peak_source": src, "launch_ms": per[dom],
+            "share": {k: v[0] / tot for k, v in kt.items() if v[1] > 0}}
+    opf.opf_destroy(h)
+    oracle_err = large_oracle_check(opf, w)
     dof = 3 * w["N"] * (2 * w["K"] - 1) * (2 * w["M"] - 1)
     line = {
         "metric": "large run timesteps/s (CFL-controlled dt, includes per-step dt control)",
@@ -438,6 +567,10 @@ def run_large(args):
         "dt_range_mixed": [res[1]["dt_min"], res[1]["dt_max"]],
         "device_footprint_gb": (free0 - free1) / 1e9,
         "energy_rel_diff_mixed_vs_fp64_after_50_steps": float(abs(res[1]["E"][0] - res[0]["E"][0]) / res[0]["E"][0]),
+        "roofline": roof,
+        "oracle_error": oracle_err,
+        "hbm_roofline_frac": step_algorithmic_bytes(w, 1) * (1000.0 / res[1]["ms_per_step"])
+        / (load_peaks()[0]["hbm_gbs"] * 1e9),
     }
     print(json.dumps(line), flush=True)
 
@@ -563,6 +696,69 @@ def run_floquet(args):
     print(json.dumps(line), flush=True)
 
 
+def run_kernels(args):
+    """Per-kernel device times of the time step of one workload (option
+    timing 1: a CUDA event pair around every kernel of the step graph), after
+    two untimed steps: microseconds per launch and launches per kernel, and
+    the wall time per step with the events in place.  Small enough to run
+    under a profiler (--steps few)."""
+    import torch
+
+    from paper_1705_03838_gb300 import build as _build, inputs, opf
+
+    torch.cuda.set_device(0)
+    _build.build()
+    wl = args.kernels_workload
+    w = inputs.WORKLOADS[wl]
+    h = opf.opf_create(w["N"], w["K"], w["M"], w["m_p"], w["alpha"], w["Re"], w["dt"])
+    opf.opf_set_option(h, "precision", args.precision)
+    opf.opf_set_state(h, inputs.workload_state(wl))
+    opf.opf_step(h, 2)
+    torch.cuda.synchronize()
+    opf.opf_set_option(h, "timing", 1)
+    opf.opf_kernel_times(h, reset=True)
+    t0 = time.time()
+    opf.opf_step(h, args.steps)
+    torch.cuda.synchronize()
+    wall = (time.time() - t0) / args.steps
+    kt = opf.opf_kernel_times(h, reset=True)
+    line = {
+        "metric": "per-kernel device time of the time step (events around every kernel)",
+        "unit": "us per launch", "n_gpus": 1, "steps": args.steps, "dtype": "f64" if args.precision == 0 else "f32+f64",
+        "data": "synthetic", "config": {"workload": wl, "precision": args.precision},
+        "kernels": {k: {"us_per_launch": ms * 1e3 / max(n, 1), "launches": n} for k, (ms, n) in kt.items()},
+        "wall_ms_per_step_with_events": wall * 1e3,
+        "energy_EID": [float(x) for x in opf.opf_energy(h)],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_peaks(args):
+    """FP64 and FP32 FMA throughput of this GPU (the library's probe kernel:
+    independent FMA recurrences over every SM), best of three each, beside
+    the unit-count peaks the ALU rooflines use."""
+    import torch
+
+    from paper_1705_03838_gb300 import build as _build, opf
+
+    torch.cuda.set_device(0)
+    _build.build()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    f64 = max(opf.opf_fma_rate(0) for _ in range(3))
+    f32 = max(opf.opf_fma_rate(1) for _ in range(3))
+    clk = clocks.stop()
+    line = {
+        "metric": "FMA throughput (measured) vs unit-count peaks", "unit": "TFLOP/s", "n_gpus": 1,
+        "fp64_measured": f64, "fp32_measured": f32,
+        "fp64_unit_count_peak": FP64_PEAK_TFLOPS, "fp32_unit_count_peak": FP32_PEAK_TFLOPS,
+        "fp64_frac_of_unit_count": f64 / FP64_PEAK_TFLOPS, "fp32_frac_of_unit_count": f32 / FP32_PEAK_TFLOPS,
+        "clocks": clk, "gpu": torch.cuda.get_device_name(0),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_gpu(args, w):
     import numpy as np
     import torch
@@ -658,9 +854,11 @@ def run_gpu(args, w):
     E64, E32 = res[0][4], res[1][4]
 
     # end-to-end through the public API with host buffers: per step, copy the
-    # state in from pinned memory, advance one step, read E, I, D back.
+    # state in from pinned memory, advance one step, copy the new state out
+    # to pinned memory and read E, I, D back.
     opf.opf_set_option(h, "precision", args.precision)
     pinned = torch.from_numpy(U0.view(np.float64).copy()).pin_memory()
+    pinned_out = torch.empty_like(pinned).pin_memory()
     e2e_steps = max(3, min(args.steps, 50))
     opf.opf_step(h, 1)
     torch.cuda.synchronize()
@@ -668,9 +866,11 @@ def run_gpu(args, w):
     for _ in range(e2e_steps):
         opf.lib().opf_set_state(h.ptr, pinned.data_ptr())
         opf.opf_step(h, 1)
+        opf.lib().opf_get_state(h.ptr, pinned_out.data_ptr())
         E = opf.opf_energy(h)
     torch.cuda.synchronize()
     e2e_s = time.time() - t0
+    e2e_state_ok = bool(np.isfinite(pinned_out.numpy()).all())
     e2e_rate = job_rate(e2e_steps, world, max_over_ranks(e2e_s, dist, "cuda"))
 
     if rank != 0:
@@ -702,9 +902,19 @@ def run_gpu(args, w):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         sps, n, setup, secs = oracle_timing(seconds_budget=15.0)
-        cpu = {"value": sps, "unit": "timesteps/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n} full oracle steps of the same workload after 1 setup step "
-                         f"({setup:.1f} s), {secs:.1f} s, single thread"}
+        agg, nproc, nall = oracle_timing_all_cores(seconds_budget=10.0)
+        small = oracle_small_full()
+        cpu = {"value": agg, "unit": "timesteps/s", "cores": nproc, "kind": "oracle",
+               "sample": f"{nproc} single-threaded oracle processes on {nproc} host cores, each stepping its own "
+                         f"seeded trajectory of the same workload for ~10 s after 1 setup step ({nall} steps "
+                         f"in all); value = the sum of their step rates",
+               "host_cores": os.cpu_count(),
+               "single_thread": {"value": sps, "unit": "timesteps/s", "cores": 1,
+                                 "sample": f"{n} full oracle steps of the same workload after 1 setup step "
+                                           f"({setup:.1f} s), {secs:.1f} s"},
+               "small_workload_100_steps": {"seconds": small["seconds"], "cores": 1,
+                                            "timesteps_per_s": 100.0 / small["seconds"]},
+               "large_workload": LARGE_ORACLE_NOTE}
     # per pass: curl + 3 transform kernels + solve (mixed); FP64 steps take
     # the curl inside the solve
     launches_per_step = (5 if args.precision == 1 else 4) * 2
@@ -737,7 +947,9 @@ def run_gpu(args, w):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_rate, "unit": "timesteps/s",
-                "h2d_bytes_per_step": int(U0.nbytes), "d2h_bytes_per_step": 24},
+                "h2d_bytes_per_step": int(U0.nbytes), "d2h_bytes_per_step": int(U0.nbytes) + 24,
+                "per_step": "set_state from pinned host memory, one step, get_state to pinned host "
+                            "memory, energy (E, I, D)", "state_finite": e2e_state_ok},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "wall_s_timed_region": wall,
@@ -758,11 +970,14 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="medium",
-                    choices=["medium", "ensemble", "large", "learned", "net", "floquet"],
+                    choices=["medium", "ensemble", "large", "learned", "net", "floquet", "kernels", "peaks"],
                     help="medium: the default single-run line; ensemble: the batched workload; large: the "
                          "CFL-controlled large run; learned: the learned Newton-Krylov proposal pipeline; "
                          "net: the proposal network's training step; floquet: batched Arnoldi "
-                         "Floquet multipliers")
+                         "Floquet multipliers; kernels: per-kernel device times of one workload's step "
+                         "(--kernels-workload, --precision, --steps); peaks: measured FP64/FP32 FMA rates")
+    ap.add_argument("--kernels-workload", default="medium",
+                    help="workload of --workload kernels: small, medium or large")
     ap.add_argument("--autotune", type=int, default=0)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -780,6 +995,10 @@ def main():
         run_net(args)
     elif args.workload == "floquet":
         run_floquet(args)
+    elif args.workload == "kernels":
+        run_kernels(args)
+    elif args.workload == "peaks":
+        run_peaks(args)
     else:
         run_gpu(args, w)
 

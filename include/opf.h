@@ -99,7 +99,8 @@ int opf_nonlinear(opf_t* h, const double* coeffs, double* out);
 /* Options:
  *   "precision": 0 = FP64 throughout (default), 1 = mixed (FP32 transforms and
  *                product, FP64 radial solves and boundary correction)
- *   "n_corr":    corrector iterations per step (default 1)
+ *   "n_corr":    corrector iterations per step (default 1; 0 = the predictor
+ *                alone, a first-order step, e.g. to check single solves)
  *   "graph":     1 = replay the step as a CUDA graph (default), 0 = plain launches
  *   "timing":    1 = record per-kernel device times (opf_kernel_times); 2 = only
  *                the kernel named by "timed_kernel" (0 curl, 1 z synthesis,
@@ -108,11 +109,15 @@ int opf_nonlinear(opf_t* h, const double* coeffs, double* out);
  *   "autotune":  1 = on the next step, time the launch shapes of each kernel
  *                (columns/rows per block of the transforms, modes per block of
  *                the solve) on the current state and keep the fastest; reads
- *                back as 2 once done.  Read-only keys "tile", "mcz", "mca", "zc"
- *                report the shapes in use.
+ *                back as 2 once done.  Read-only keys "mcz", "mca", "zc" report
+ *                the transforms' shapes in use.
+ *   "tile":      modes per block of the solve: 0 = chosen from the grid size
+ *                (default), 4, 8 or 16 (OPF_EINVAL if that block's shared
+ *                memory does not fit); reads back the value set or the one the
+ *                autotuner chose.  Results do not depend on it.
  *   "rot_x", "rot_y", "rot_z": frame rotation Omega (Cartesian components, pipe
  *                axis z; default 0): the Coriolis force -2 Omega x u joins the
- *                nonlinear term (section 3.3's rotating pipe; a transverse axis
+ *                nonlinear term (section 3.1's rotating pipe; a transverse axis
  *                needs m_p = 1).  Single handles only.
  *   "cfl":       C > 0 switches on automatic time-step control (section 2):
  *                after every step dt = min(dt_max, C / max(|u_r|/dr,
@@ -204,6 +209,11 @@ typedef struct {
   int fix_T;         /* 1: period T fixed (no time phase condition) */
   int fix_s;         /* 1: axial shift s fixed (no axial phase condition) */
   int precision;     /* time integrations: 0 FP64, 1 mixed */
+  /* physics of the time integrations, as opf_set_forcing and the rot_x/y/z
+   * options of a handle (paper section 3.1's forcing hook and Coriolis force): */
+  const double* forcing; /* constant body force, state layout, host memory; NULL = none */
+  double rot[3];         /* frame rotation (Omega_x, Omega_y, Omega_z); a transverse
+                          * axis needs m_p = 1 */
 } opf_nk_opts;
 int opf_nk_core(int n, int count, double* x, const double* scale, opf_nk_residual F,
                 opf_nk_jv JV, void* ctx, const opf_nk_opts* opts, double* res_out,
@@ -300,14 +310,20 @@ int opf_net_train_step(opf_net_t* n, const float* d_x, const float* d_ty, const 
  * device array inside the library, held on every GPU that loads it until
  * the process exits; OPF_EINVAL if the resolution needs more (the small
  * N=32, |k|<16, m<16 case needs 6.6 MB).  The first call on a device looks
- * up that array's address there, so make it before any stream capture.
- * Calls share the array: calls whose GPU work overlaps race.  On success
- * it calls no allocator at all (no cudaMalloc, cudaFree or allocating
- * library routine); a failure only stores its message for opf_last_error. */
+ * up that array's address there and sets the kernels' shared-memory limits,
+ * so make it before any stream capture; CUDA loads modules lazily, so that
+ * first call (not loading the library) is also what places the array and the
+ * kernels' code on the device: make it at start-up, before the caller's own
+ * pool takes the device memory.  The call synchronises its stream before it
+ * returns, so on a stream that is being captured it returns OPF_EINVAL
+ * without launching anything.  Calls share the array: calls whose GPU work
+ * overlaps race.  On success it calls no allocator at all (no cudaMalloc,
+ * cudaFree or allocating library routine); a failure only stores its message
+ * for opf_last_error. */
 int opf_nonlinear_noalloc(int N, int K, int M, int m_p, double alpha, double Re,
                           const double* d_state, double* d_out, void* stream);
 
-/* Constant body force f (paper section 3.3: a user forcing hook; state layout,
+/* Constant body force f (paper section 3.1: a user forcing hook; state layout,
  * components (f_r, f_theta, f_z), host memory, copied) added to the nonlinear
  * term at every evaluation; NULL removes it.  A uniform axial force on the
  * (0,0) mode is absorbed by the fixed-flux driving (beta shifts by -f Re / 4). */
@@ -334,6 +350,15 @@ int opf_change_resolution(int N1, int K1, int M1, const double* in, int N2, int 
  * full length; OPF_EINVAL if cap is too small or what is unknown. */
 int opf_setup_query(int N, int K, int M, int m_p, double alpha, double Re, double dt,
                     const char* what, double* out, long cap, long* len);
+
+/* No counterpart in the paper (measurement support): the device's sustained
+ * fused multiply-add rate in TFLOP/s, FP64 (precision 0) or FP32 (precision
+ * 1), measured with a kernel of independent FMA recurrences over every SM.
+ * It is the denominator of the rooflines of the kernels bound by arithmetic
+ * rather than by memory (the radial solves, the transforms).  Runs on the
+ * current device; takes ~50 ms.  OPF_EINVAL for another precision or a NULL
+ * output. */
+int opf_fma_rate(int precision, double* tflops);
 
 #ifdef __cplusplus
 }

@@ -57,7 +57,7 @@ class Params:
         self.alpha, self.Re, self.dt = float(alpha), float(Re), float(dt)
         self.c, self.n_corr = float(c), int(n_corr)
         # frame rotation Omega (Cartesian, pipe axis z): Coriolis force -2 Omega x u
-        # (section 3.3 adds it through the forcing hook); forcing: a constant
+        # (section 3.1 adds it through the forcing hook); forcing: a constant
         # spectral body force (3, M, 2K-1, N) in (r, theta, z) components
         self.rotation = tuple(float(x) for x in rotation)
         self.forcing = forcing
@@ -379,6 +379,40 @@ class Oracle:
                 if mean:
                     beta_p = x[4 * N].real
         return Unew, beta_p
+
+    def solve_modes(self, Uj, Neff, modes):
+        """solve() restricted to the listed (m, kk) modes: each mode's system
+        involves only that mode's u_j and N_eff, so grids too large for a
+        dense solve of every mode can still be checked mode by mode.  Returns
+        {(m, kk): (u (3, N), beta')}, with the same right-hand side and dense
+        system as solve()."""
+        p, r = self.p, self.r
+        N, c, nu, dt = p.N, p.c, 1.0 / p.Re, p.dt
+        out = {}
+        for m, kk in modes:
+            mt, ak = self.mt(m), self.ak(kk)
+            Lv = self.scalar_laplacian(m, kk, self.par_v(m))
+            Ls = self.scalar_laplacian(m, kk, self.par_s(m))
+            ur, ut, uz = Uj[0, m, kk], Uj[1, m, kk], Uj[2, m, kk]
+            Lu = np.stack([Lv @ ur - ur / r ** 2 - 2j * mt * ut / r ** 2,
+                           Lv @ ut - ut / r ** 2 + 2j * mt * ur / r ** 2,
+                           Ls @ uz])
+            R = Uj[:, m, kk] / dt + (1.0 - c) * nu * Lu + Neff[:, m, kk]
+            D1v = self.D[self.par_v(m)][0]
+            nr, nt, nz = Neff[0, m, kk], Neff[1, m, kk], Neff[2, m, kk]
+            dN = D1v @ nr + nr / r + 1j * mt * nt / r + 1j * ak * nz
+            mean = (m == 0 and kk == p.K - 1)
+            b = np.zeros(4 * N + (1 if mean else 0), dtype=np.complex128)
+            for blk in range(3):
+                b[blk * N: (blk + 1) * N] = R[blk]
+                b[blk * N + N - 1] = 0.0
+            b[3 * N: 4 * N] = dN
+            b[4 * N - 1] = 0.0
+            if mean:
+                b[4 * N] = np.pi / 2.0
+            x = sla.lu_solve(sla.lu_factor(self._mode_matrix(m, kk)), b)
+            out[(m, kk)] = (x[:3 * N].reshape(3, N), x[4 * N].real if mean else 0.0)
+        return out
 
     def step(self, U, nsteps=1):
         """Predictor-corrector steps (section 2); returns the new state."""

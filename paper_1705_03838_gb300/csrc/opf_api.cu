@@ -521,6 +521,9 @@ void enqueue_step(Runner* r) {
     const bool curl = !fused_curl(r);
     enqueue_nonlinear(r, *g, g->U, g->Nj, curl);
     enqueue_solve(r, *g, g->Nj, nullptr, 1.0, 0.0, g->U1);
+    if (r->n_corr == 0)  // predictor only: its output (3F per trajectory) is the new state
+      cudaMemcpy2DAsync(g->U, g->sstride, g->U1, g->sstride, 3 * (size_t)g->d.F * sizeof(double2), g->d.B,
+                        cudaMemcpyDeviceToDevice, r->st());
     for (int q = 0; q < r->n_corr; ++q) {
       enqueue_nonlinear(r, *g, g->U1, g->Nq, curl);
       enqueue_solve(r, *g, g->Nq, g->Nj, c, 1.0 - c, q == r->n_corr - 1 ? g->U : g->U1);
@@ -707,7 +710,7 @@ int runner_option(Runner* r, const char* key, double v) {
     if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "precision: 0 (FP64) or 1 (mixed)");
     r->precision = (int)v;
   } else if (!strcmp(key, "n_corr")) {
-    if (!(v >= 1 && v <= 16 && v == std::floor(v))) return fail(OPF_EINVAL, "n_corr: 1..16");
+    if (!(v >= 0 && v <= 16 && v == std::floor(v))) return fail(OPF_EINVAL, "n_corr: 0..16");
     r->n_corr = (int)v;
   } else if (!strcmp(key, "graph")) {
     if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "graph: 0 or 1");
@@ -722,6 +725,16 @@ int runner_option(Runner* r, const char* key, double v) {
   } else if (!strcmp(key, "autotune")) {
     if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "autotune: 0 or 1");
     r->autotune = (int)v;
+  } else if (!strcmp(key, "tile")) {
+    if (v != 0.0 && v != 4.0 && v != 8.0 && v != 16.0)
+      return fail(OPF_EINVAL, "tile: 0 (heuristic), 4, 8 or 16 modes per solve block");
+    int dev = 0, optin = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    for (Group* g : r->groups)
+      if (v != 0.0 && opf::solve_smem_bytes(g->d.N, (int)v) > (size_t)optin)
+        return fail(OPF_EINVAL, "tile: the solve block of this size does not fit in shared memory");
+    for (Group* g : r->groups) g->d.tile = (int)v;
   } else {
     return fail(OPF_EINVAL, std::string("unknown option ") + key);
   }
@@ -1293,9 +1306,39 @@ struct NkCtx {
   std::vector<double> T, s;           // per problem: period, shift of the base point
   std::vector<std::vector<double>> phi, dphi_dt, dphi_ds, du_dt, du_dz, ubase;  // packed, base data
   std::vector<double> st;             // scratch state (interleaved complex, one trajectory)
+  double2* forcing = nullptr;         // device copy of the body force (internal layout)
   NkPack pk;
   NkCtx(int N_, int K_, int M_) : pk(N_, K_, M_) {}
+  ~NkCtx() {
+    if (forcing) cudaFree(forcing);
+  }
 };
+
+// The options' body force and frame rotation on the problems' group (shared
+// by every trajectory of it, as on a handle).
+int nk_apply_physics(NkCtx* c, const opf_nk_opts* o) {
+  opf::Dims& d = c->g.d;
+  const double x = o->rot[0], y = o->rot[1], z = o->rot[2];
+  if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z))
+    return fail(OPF_EINVAL, "nk: rotation must be finite");
+  if ((x != 0.0 || y != 0.0) && c->m_p != 1)
+    return fail(OPF_EINVAL, "nk: rotation about a transverse axis needs m_p = 1");
+  d.rot_x = x;
+  d.rot_y = y;
+  d.rot_z = z;
+  d.rotate = (x != 0.0 || y != 0.0 || z != 0.0) ? 1 : 0;
+  if (o->forcing) {
+    const size_t bytes = 3 * (size_t)d.F * sizeof(double2);
+    CU(cudaMalloc((void**)&c->forcing, bytes));
+    double2* abi = c->g.at(c->g.abi, 0);  // staging in the ABI layout
+    CU(cudaMemcpyAsync(abi, o->forcing, bytes, cudaMemcpyHostToDevice, c->run.stream));
+    opf::launch_abi_to_internal(c->g.single(0), abi, c->forcing, c->run.stream);
+    CU(cudaStreamSynchronize(c->run.stream));
+    CU(cudaGetLastError());
+    d.forcing = c->forcing;
+  }
+  return OPF_OK;
+}
 
 // multiply each axial mode k of a state by e^{i alpha k s} (shift by s) and,
 // if dz, by i alpha k (axial derivative)
@@ -1480,6 +1523,7 @@ extern "C" int opf_nk_solve(int N, int K, int M, int m_p, double alpha, double R
   // periods may diverge during the solve: every problem gets its own setup
   int rc = group_build(&c->g, N, K, M, m_p, alpha, count, Re_v.data(), dt_v.data(), true);
   if (rc == OPF_OK) rc = runner_init(&c->run);
+  if (rc == OPF_OK) rc = nk_apply_physics(c, o);
   if (rc != OPF_OK) {
     group_free(&c->g);
     runner_free(&c->run);
@@ -1724,6 +1768,7 @@ extern "C" int opf_nk_solve_ms(int N, int K, int M, int m_p, double alpha, doubl
   for (int t = 0; t < ntr; ++t) dt_v[t] = T[t / S] / (S * c->nsteps);
   int rc = group_build(&c->g, N, K, M, m_p, alpha, ntr, Re_v.data(), dt_v.data(), true);
   if (rc == OPF_OK) rc = runner_init(&c->run);
+  if (rc == OPF_OK) rc = nk_apply_physics(c, o);
   if (rc != OPF_OK) {
     group_free(&c->g);
     runner_free(&c->run);

@@ -29,13 +29,25 @@ class NkOpts(ctypes.Structure):
     _fields_ = [("max_newton", ctypes.c_int), ("max_krylov", ctypes.c_int), ("max_hook", ctypes.c_int),
                 ("tol", ctypes.c_double), ("gmres_tol", ctypes.c_double), ("delta0", ctypes.c_double),
                 ("dt", ctypes.c_double), ("eps", ctypes.c_double), ("fix_T", ctypes.c_int),
-                ("fix_s", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("fix_s", ctypes.c_int), ("precision", ctypes.c_int),
+                ("forcing", ctypes.c_void_p), ("rot", ctypes.c_double * 3)]
 
 
 def nk_opts(**kw):
+    """Newton-Krylov options; forcing= a state-layout complex array (kept alive
+    on the returned object) or None, rot= (Omega_x, Omega_y, Omega_z)."""
     o = NkOpts(max_newton=30, max_krylov=60, max_hook=12, tol=1e-10, gmres_tol=1e-3, delta0=0.0,
-               dt=0.01, eps=1e-7, fix_T=0, fix_s=0, precision=0)
+               dt=0.01, eps=1e-7, fix_T=0, fix_s=0, precision=0, forcing=None)
     for k, v in kw.items():
+        if k == "forcing":
+            if v is not None:
+                arr = np.ascontiguousarray(v, dtype=np.complex128)
+                o._forcing_keep = arr
+                o.forcing = arr.ctypes.data
+            continue
+        if k == "rot":
+            o.rot = (ctypes.c_double * 3)(*[float(x) for x in v])
+            continue
         setattr(o, k, v)
     return o
 
@@ -107,6 +119,8 @@ def lib():
         L.opf_ens_set_stream.argtypes = [vp, vp]
         L.opf_ens_kernel_times.restype = i
         L.opf_ens_kernel_times.argtypes = [vp, i, ip, ctypes.POINTER(cp), _dp, ip, i]
+        L.opf_fma_rate.restype = i
+        L.opf_fma_rate.argtypes = [i, _dp]
         L.opf_nk_core.restype = i
         L.opf_nk_core.argtypes = [i, i, _dp, _dp, NK_RESIDUAL, NK_JV, vp, ctypes.POINTER(NkOpts),
                                   _dp, ctypes.POINTER(i)]
@@ -240,6 +254,13 @@ def opf_nonlinear_noalloc(N, K, M, m_p, alpha, Re, d_state, d_out, stream=0):
     _check(lib().opf_nonlinear_noalloc(int(N), int(K), int(M), int(m_p), float(alpha), float(Re),
                                        ctypes.c_void_p(d_state), ctypes.c_void_p(d_out),
                                        ctypes.c_void_p(stream)))
+
+
+def opf_fma_rate(precision):
+    """Measured FMA throughput of the current device in TFLOP/s (0 FP64, 1 FP32)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().opf_fma_rate(int(precision), ctypes.byref(out)))
+    return out.value
 
 
 def opf_set_option(h, key, value):

@@ -184,16 +184,19 @@ def test_small_workload_100_steps(opf):
     assert abs(e[1] - e_ref[1]) < 1e-13 * w["Re"]
 
 
-def test_medium_workload_few_steps(opf):
-    """Full medium size (N=48, |k|<32, m<24, m_p=2): all coefficients after
-    3 steps against the oracle."""
+def test_medium_workload_100_steps(opf):
+    """Full medium size (N=48, |k|<32, m<24, m_p=2, Re=2400, amplitude 0.1):
+    all coefficients after 100 FP64 steps against the oracle, the same
+    bound as the small workload (relative L2 <= 1e-10)."""
     w = inputs.WORKLOADS["medium"]
     args = (w["N"], w["K"], w["M"], w["m_p"], w["alpha"], w["Re"], w["dt"])
     o = Oracle(Params(*args))
     U0 = inputs.workload_state("medium")
-    ref = o.step(U0, 3)
-    h, U = gpu_run(opf, *args, U0, 3)
-    assert rel(U, ref) < 1e-11
+    ref = o.step(U0, 100)
+    h, U = gpu_run(opf, *args, U0, 100)
+    assert rel(U, ref) < 1e-10
+    e, e_ref = opf.opf_energy(h), o.energy(ref)
+    assert abs(e[0] - e_ref[0]) < 1e-12 and abs(e[2] - e_ref[2]) < 1e-12
 
 
 def test_hagen_poiseuille_steady_on_gpu(opf):
@@ -222,6 +225,18 @@ def test_two_correctors_match_oracle(opf):
     ref = o.step(U0, 2)
     h, U = gpu_run(opf, N, K, M, 1, alpha, Re, dt, U0, 2, n_corr=2)
     assert rel(U, ref) < 1e-12
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_predictor_only_steps_match_oracle(opf, precision):
+    """n_corr = 0: each step is the predictor alone (one nonlinear term, one
+    solve), in FP64 and with the mixed-precision step (FP32 round-off)."""
+    N, K, M, alpha, Re, dt = 16, 3, 4, 1.25, 600.0, 0.01
+    U0 = inputs.seeded_state(N, K, M, 1, alpha, 0.1, 18)
+    ref = Oracle(Params(N, K, M, 1, alpha, Re, dt, n_corr=0)).step(U0, 3)
+    h, U = gpu_run(opf, N, K, M, 1, alpha, Re, dt, U0, 3, n_corr=0, precision=precision)
+    assert rel(U, ref) < (1e-12 if precision == 0 else 1e-7)
+    assert opf.opf_get_option(h, "n_corr") == 0
 
 
 def test_handles_of_different_sizes_coexist(opf):

@@ -385,6 +385,18 @@ def test_radial_refinement_of_the_step():
     assert order > 5.5, (errs, order)
 
 
+def test_solve_restricted_to_modes_equals_the_full_solve():
+    """solve_modes (used to check grids too large for the dense solve of
+    every mode) gives exactly the full solve's modes and beta'."""
+    o = Oracle(Params(12, 3, 4, 1, 1.25, 500.0, 0.01))
+    U = inputs.seeded_state(12, 3, 4, 1, 1.25, 0.1, 3)
+    Nj = o.nonlinear(U)
+    full, bp = o.solve(U, Nj)
+    for (m, kk), (u, b) in o.solve_modes(U, Nj, [(0, 2), (1, 0), (3, 4), (2, 2)]).items():
+        assert np.array_equal(u, full[:, m, kk])
+        assert b == (bp if (m, kk) == (0, 2) else 0.0)
+
+
 def test_wall_conditions_at_round_off():
     """||g|| (no-slip and wall divergence) at machine epsilon (section 2)."""
     N, K, M = 16, 4, 4
