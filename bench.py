@@ -338,6 +338,17 @@ def run_reference(args, w):
 ENSEMBLE_SHAPES = [(32, 16, 16)] * 96 + [(48, 24, 24)] * 96 + [(64, 32, 32)] * 64
 
 
+def ensemble_shapes(count):
+    """The ensemble's resolutions in its 96 : 96 : 64 proportion, count in all
+    (256 = the full workload; smaller counts for profiling)."""
+    if count >= len(ENSEMBLE_SHAPES):
+        return ENSEMBLE_SHAPES
+    a = max(1, round(count * 96 / 256))
+    c = max(1, round(count * 64 / 256))
+    b = max(1, count - a - c)
+    return [(32, 16, 16)] * a + [(48, 24, 24)] * b + [(64, 32, 32)] * c
+
+
 def run_ensemble(args):
     """Batched-ensemble workload: 256 trajectories of uneven resolution
     (96 x N=32 |k|<16 m<16, 96 x N=48 |k|<24 m<24, 64 x N=64 |k|<32 m<32),
@@ -350,12 +361,13 @@ def run_ensemble(args):
 
     torch.cuda.set_device(0)
     _build.build()
-    n = len(ENSEMBLE_SHAPES)
+    shapes = ensemble_shapes(args.ens_count)
+    n = len(shapes)
     seed = 1705038383
     U = inputs.uniforms(seed, 2 * n)
     Re = [1800.0 + 800.0 * U[2 * i] for i in range(n)]
     amp = [10.0 ** (-3.0 + 2.0 * U[2 * i + 1]) for i in range(n)]
-    Ns, Ks, Ms = zip(*ENSEMBLE_SHAPES)
+    Ns, Ks, Ms = zip(*shapes)
     alpha, dt = 1.25, 0.005
     t0 = time.time()
     e = opf.opf_ens_create(Ns, Ks, Ms, [1] * n, [alpha] * n, Re, [dt] * n)
@@ -364,7 +376,7 @@ def run_ensemble(args):
     opf.opf_ens_set_stream(e, stream.cuda_stream)
     opf.opf_ens_set_option(e, "precision", args.precision)
     t0 = time.time()
-    for i, (N, K, M) in enumerate(ENSEMBLE_SHAPES):
+    for i, (N, K, M) in enumerate(shapes):
         opf.opf_ens_set_state(e, i, inputs.seeded_state(N, K, M, 1, alpha, amp[i], seed + i))
     inputs_s = time.time() - t0
     if args.autotune:
@@ -394,19 +406,20 @@ def run_ensemble(args):
     kt_live = opf.opf_ens_kernel_times(e, reset=True)
     kt = {k: (v[0] / max(1, v[1]), 1) for k, v in kt_all.items()}  # per-launch averages
     kt["solve"] = (kt_live["solve"][0] / max(1, kt_live["solve"][1]), 1)
-    E = [opf.opf_ens_energy(e, i) for i in (0, 96, 192)]
+    firsts = [shapes.index(sh) for sh in dict.fromkeys(shapes)]
+    E = [opf.opf_ens_energy(e, i) for i in firsts]
     steps_per_s = args.steps / (total_ms / 1000.0)
-    dofs = sum(3 * N * (2 * K - 1) * (2 * M - 1) for N, K, M in ENSEMBLE_SHAPES)
-    Fsum = sum(N * (2 * K - 1) * M for N, K, M in ENSEMBLE_SHAPES)
+    dofs = sum(3 * N * (2 * K - 1) * (2 * M - 1) for N, K, M in shapes)
+    Fsum = sum(N * (2 * K - 1) * M for N, K, M in shapes)
     peaks, peak_kind = load_peaks()
     algo_bytes = (528 if args.precision == 0 else 432) * Fsum
     flops = {}
-    for (N, K, M), cnt in ((ENSEMBLE_SHAPES[0], 96), (ENSEMBLE_SHAPES[96], 96), (ENSEMBLE_SHAPES[192], 64)):
+    for (N, K, M), cnt in ((sh, shapes.count(sh)) for sh in dict.fromkeys(shapes)):
         c = kernel_costs({"N": N, "K": K, "M": M})
         for k, v in c.items():
             flops[k] = flops.get(k, 0.0) + cnt * v["flops"]
     dom = max(kt, key=lambda k: kt[k][0])
-    dom_ms = kt[dom][0] / max(1, kt[dom][1]) * 3  # three shape groups per kernel slot
+    dom_ms = kt[dom][0] / max(1, kt[dom][1]) * len(set(shapes))  # one launch per shape group per slot
     pk, src = kernel_peak(dom, args.precision)
     ach = flops[dom] / (dom_ms * 1e-3) / 1e12
     tot = sum(x[0] for x in kt.values())
@@ -421,7 +434,9 @@ def run_ensemble(args):
         "higher_is_better": True,
         "dtype": "f64" if args.precision == 0 else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": "ensemble: 96x(N32,|k|<16,m<16) + 96x(N48,|k|<24,m<24) + 64x(N64,|k|<32,m<32), "
+        "config": {"workload": f"ensemble: {shapes.count((32, 16, 16))}x(N32,|k|<16,m<16) + "
+                               f"{shapes.count((48, 24, 24))}x(N48,|k|<24,m<24) + "
+                               f"{shapes.count((64, 32, 32))}x(N64,|k|<32,m<32), "
                                "Re U[1800,2600], amp logU[1e-3,1e-1], dt=0.005",
                    "l2": "working set > L2 (no flush needed)",
                    "autotune": bool(args.autotune)},
@@ -433,7 +448,7 @@ def run_ensemble(args):
         "setup_s": setup_s,
         "inputs_s": inputs_s,
         "clocks": clk,
-        "energy_EID_members_0_96_192": [[float(x) for x in v] for v in E],
+        "energy_EID_first_member_of_each_shape": [[float(x) for x in v] for v in E],
     }
     print(json.dumps(line), flush=True)
 
@@ -979,6 +994,9 @@ def main():
     ap.add_argument("--kernels-workload", default="medium",
                     help="workload of --workload kernels: small, medium or large")
     ap.add_argument("--autotune", type=int, default=0)
+    ap.add_argument("--ens-count", type=int, default=256,
+                    help="trajectories of --workload ensemble (256 = the full workload; fewer, in the same "
+                         "proportions, for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -49,6 +49,15 @@ typedef struct opf_ctx opf_t; /* opaque; owned by the library */
  * prime factor other than 2, 3, 5.  Returns NULL on failure (opf_last_error). */
 opf_t* opf_create(int N, int K, int M, int m_p, double alpha, double Re, double dt);
 
+/* As opf_create, on a user radial mesh (paper section 2: the radial points
+ * may be supplied instead of computed): r holds N strictly increasing points
+ * in (0, 1] with r[N-1] = 1 (the wall), host memory, copied; NULL = the
+ * default points.  Stencils (9 index-nearest points of the parity-extended
+ * mesh), quadrature weights, operators and the influence data are built on
+ * these points; states on the handle are sampled there.  NULL on an invalid
+ * mesh (opf_last_error). */
+opf_t* opf_create_mesh(int N, int K, int M, int m_p, double alpha, double Re, double dt, const double* r);
+
 /* Release the handle and its device memory.  NULL is ignored. */
 void opf_destroy(opf_t* h);
 
@@ -350,6 +359,10 @@ int opf_change_resolution(int N1, int K1, int M1, const double* in, int N2, int 
  * full length; OPF_EINVAL if cap is too small or what is unknown. */
 int opf_setup_query(int N, int K, int M, int m_p, double alpha, double Re, double dt,
                     const char* what, double* out, long cap, long* len);
+/* Same, on a user radial mesh r (N points as for opf_create_mesh; NULL = the
+ * default points). */
+int opf_setup_query_mesh(int N, int K, int M, int m_p, double alpha, double Re, double dt, const double* r,
+                         const char* what, double* out, long cap, long* len);
 
 /* No counterpart in the paper (measurement support): the device's sustained
  * fused multiply-add rate in TFLOP/s, FP64 (precision 0) or FP32 (precision

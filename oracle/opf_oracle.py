@@ -52,8 +52,13 @@ __all__ = [
 class Params:
     """Run parameters (paper section 2): resolution (N, K, M), m_p, alpha, Re, dt."""
 
-    def __init__(self, N, K, M, m_p, alpha, Re, dt, c=0.5, n_corr=1, rotation=(0.0, 0.0, 0.0), forcing=None):
+    def __init__(self, N, K, M, m_p, alpha, Re, dt, c=0.5, n_corr=1, rotation=(0.0, 0.0, 0.0), forcing=None,
+                 r=None):
         self.N, self.K, self.M, self.m_p = int(N), int(K), int(M), int(m_p)
+        # r: a user radial mesh (section 2: the points may be read from a
+        # file instead of the default formula), N increasing points in (0, 1]
+        # with the wall r_N = 1; None = reading R1's points
+        self.r = None if r is None else np.array(r, dtype=np.float64)
         self.alpha, self.Re, self.dt = float(alpha), float(Re), float(dt)
         self.c, self.n_corr = float(c), int(n_corr)
         # frame rotation Omega (Cartesian, pipe axis z): Coriolis force -2 Omega x u
@@ -175,7 +180,13 @@ class Oracle:
         N = p.N
         if N < 9:
             raise ValueError("need N >= 9 for the 9-point stencil")
-        self.r = mesh(N)
+        if p.r is None:
+            self.r = mesh(N)
+        else:
+            r = p.r
+            if r.shape != (N,) or not (r[0] > 0 and r[-1] == 1.0 and np.all(np.diff(r) > 0)):
+                raise ValueError("a user mesh needs N increasing points in (0, 1] ending at the wall r = 1")
+            self.r = r.copy()
         self.D = {s: fd_matrices(self.r, s) for s in (1, -1)}
         self.w = quadrature_weights(self.r)
         self._lu = {}

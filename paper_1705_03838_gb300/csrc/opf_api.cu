@@ -69,6 +69,7 @@ struct Group {
   char* parena = nullptr;
   char* sarena = nullptr;
   size_t pstride = 0, sstride = 0;
+  std::vector<double> mesh;  // user radial mesh (empty: the default points)
   // trajectory 0's work buffers (trajectory b: + b * sstride bytes)
   double2 *U = nullptr, *U1 = nullptr, *Nj = nullptr, *Nq = nullptr, *W6 = nullptr;
   double2 *Z6 = nullptr, *ZN = nullptr, *abi = nullptr, *tmpU = nullptr, *Nlin = nullptr;
@@ -160,6 +161,7 @@ int group_fill_setups(Group* g, bool first) {
     s.Re = Re[b];
     s.dt = dt[b];
     s.c = 0.5;
+    s.r_user = g->mesh;
     ok[b] = opf::build_setup(&s, &errs[b]) ? 1 : 0;
   };
   const int nthreads = std::max(1, std::min<int>(nsetup, (int)std::thread::hardware_concurrency()));
@@ -864,7 +866,12 @@ extern "C" {
 const char* opf_last_error(void) { return g_err.c_str(); }
 
 opf_t* opf_create(int N, int K, int M, int m_p, double alpha, double Re, double dt) {
+  return opf_create_mesh(N, K, M, m_p, alpha, Re, dt, nullptr);
+}
+
+opf_t* opf_create_mesh(int N, int K, int M, int m_p, double alpha, double Re, double dt, const double* r) {
   opf_ctx* h = new opf_ctx();
+  if (r && N > 0) h->g.mesh.assign(r, r + N);
   int rc = group_build(&h->g, N, K, M, m_p, alpha, 1, &Re, &dt);
   if (rc == OPF_OK) rc = runner_init(&h->run);
   if (rc == OPF_OK) {
@@ -1219,9 +1226,15 @@ int opf_ens_kernel_times(opf_ens_t* e, int cap, int* count, const char** names, 
 // ---------------------------------------------------------------- host-only
 int opf_setup_query(int N, int K, int M, int m_p, double alpha, double Re, double dt,
                     const char* what, double* out, long cap, long* len) {
+  return opf_setup_query_mesh(N, K, M, m_p, alpha, Re, dt, nullptr, what, out, cap, len);
+}
+
+int opf_setup_query_mesh(int N, int K, int M, int m_p, double alpha, double Re, double dt, const double* r,
+                         const char* what, double* out, long cap, long* len) {
   if (N < 9 || K < 1 || M < 1 || m_p < 1 || !(alpha > 0) || !(Re > 0) || !(dt > 0) || !what || !len)
     return fail(OPF_EINVAL, "opf_setup_query: bad arguments");
   opf::Setup s;
+  if (r) s.r_user.assign(r, r + N);
   s.N = N;
   s.K = K;
   s.M = M;

@@ -29,6 +29,7 @@ bool make_plan(int n, FftPlan* p);
 struct Setup {
   int N = 0, K = 0, M = 0, m_p = 1;
   double alpha = 0, Re = 0, dt = 0, c = 0.5;
+  std::vector<double> r_user;  // a user radial mesh (N points), empty = the default points
   std::vector<double> r, rinv;
   std::vector<double> d1;     // [2 parity: 0 even, 1 odd][N][9] first derivative
   std::vector<double> d2;     // same layout, second derivative

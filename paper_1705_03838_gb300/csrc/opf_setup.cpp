@@ -297,12 +297,34 @@ bool build_setup(Setup* s, std::string* err) {
   const int nk = 2 * K - 1;
   s->r.resize(N);
   s->rinv.resize(N);
-  for (int n = 0; n < N; ++n) {  // section 2: points bunched towards the wall
-    s->r[n] = std::cos(M_PI * (double)(N - 1 - n) / (2.0 * N - 1.0));
-    s->rinv[n] = 1.0 / s->r[n];
+  if (!s->r_user.empty()) {  // section 2: the points may also come from the user
+    if ((int)s->r_user.size() != N) {
+      *err = "user mesh: need N points";
+      return false;
+    }
+    for (int n = 0; n < N; ++n) {
+      const double x = s->r_user[n];
+      if (!(x > 0.0 && x <= 1.0) || (n > 0 && !(x > s->r_user[n - 1]))) {
+        *err = "user mesh: points must increase strictly within (0, 1]";
+        return false;
+      }
+    }
+    if (s->r_user[N - 1] != 1.0) {
+      *err = "user mesh: the last point must be the wall r = 1";
+      return false;
+    }
+    for (int n = 0; n < N; ++n) {
+      s->r[n] = s->r_user[n];
+      s->rinv[n] = 1.0 / s->r[n];
+    }
+  } else {
+    for (int n = 0; n < N; ++n) {  // section 2: points bunched towards the wall
+      s->r[n] = std::cos(M_PI * (double)(N - 1 - n) / (2.0 * N - 1.0));
+      s->rinv[n] = 1.0 / s->r[n];
+    }
+    s->r[N - 1] = 1.0;
+    s->rinv[N - 1] = 1.0;
   }
-  s->r[N - 1] = 1.0;
-  s->rinv[N - 1] = 1.0;
   build_stencils(s);
   build_quadrature(s);
 

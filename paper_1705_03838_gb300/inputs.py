@@ -85,9 +85,10 @@ def envelope_broadband(k, m, K, M):
 
 
 def seeded_state(N, K, M, m_p, alpha, amplitude, seed, envelope=envelope_exp,
-                 laminar=True):
-    """Total-velocity state (3, M, 2K-1, N) complex128 following the recipe above."""
-    r = radial_points(N)
+                 laminar=True, r=None):
+    """Total-velocity state (3, M, 2K-1, N) complex128 following the recipe
+    above, sampled at the radial points r (default: radial_points(N))."""
+    r = radial_points(N) if r is None else np.asarray(r, dtype=np.float64)
     nk = 2 * K - 1
     s = (1.0 - r * r) ** 2
     ds = -4.0 * r * (1.0 - r * r)
@@ -133,9 +134,10 @@ def seeded_state(N, K, M, m_p, alpha, amplitude, seed, envelope=envelope_exp,
     return U
 
 
-def laminar_state(N, K, M):
-    """Hagen-Poiseuille flow u_z = 1 - r^2 in the host layout."""
-    r = radial_points(N)
+def laminar_state(N, K, M, r=None):
+    """Hagen-Poiseuille flow u_z = 1 - r^2 in the host layout (at the points r,
+    default radial_points(N))."""
+    r = radial_points(N) if r is None else np.asarray(r, dtype=np.float64)
     U = np.zeros((3, M, 2 * K - 1, N), dtype=np.complex128)
     U[2, 0, K - 1] = 1.0 - r * r
     return U
@@ -150,6 +152,16 @@ WORKLOADS = {
     "large": dict(N=128, K=128, M=128, m_p=1, alpha=0.4, Re=5300.0, dt=0.002,
                   amplitude=0.3, seed=1705038384, envelope=envelope_broadband),
 }
+
+
+def stretched_mesh(N, beta=1.8):
+    """A radial mesh other than the default one, for testing user meshes:
+    r_n = sinh(beta x_n) / sinh(beta), x_n = n / N (n = 1..N), clustered
+    towards the axis instead of the wall (r_N = 1)."""
+    x = np.arange(1, N + 1, dtype=np.float64) / N
+    r = np.sinh(beta * x) / math.sinh(beta)
+    r[-1] = 1.0
+    return r
 
 
 def workload_state(name):

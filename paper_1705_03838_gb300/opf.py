@@ -157,6 +157,11 @@ def lib():
         L.opf_set_forcing.argtypes = [vp, vp]
         L.opf_change_resolution.restype = i
         L.opf_change_resolution.argtypes = [i, i, i, vp, i, i, i, i, vp]
+        L.opf_create_mesh.restype = vp
+        L.opf_create_mesh.argtypes = [i, i, i, i, d, d, d, _dp]
+        L.opf_setup_query_mesh.restype = i
+        L.opf_setup_query_mesh.argtypes = [i, i, i, i, d, d, d, _dp, cp, _dp, ctypes.c_long,
+                                           ctypes.POINTER(ctypes.c_long)]
         L.opf_setup_query.restype = i
         L.opf_setup_query.argtypes = [i, i, i, i, d, d, d, cp, _dp, ctypes.c_long,
                                       ctypes.POINTER(ctypes.c_long)]
@@ -192,6 +197,17 @@ def _state_buffer(h, arr):
 
 def opf_create(N, K, M, m_p, alpha, Re, dt):
     ptr = lib().opf_create(N, K, M, m_p, alpha, Re, dt)
+    if not ptr:
+        raise OpfError(OPF_EINVAL, lib().opf_last_error().decode())
+    return Handle(ptr, N, K, M)
+
+
+def opf_create_mesh(N, K, M, m_p, alpha, Re, dt, r):
+    """opf_create on a user radial mesh r (N increasing points, r[-1] = 1)."""
+    ra = np.ascontiguousarray(r, dtype=np.float64)
+    if ra.shape != (N,):
+        raise OpfError(OPF_EINVAL, "opf_create_mesh: r must hold N points")
+    ptr = lib().opf_create_mesh(N, K, M, m_p, alpha, Re, dt, ra.ctypes.data_as(_dp))
     if not ptr:
         raise OpfError(OPF_EINVAL, lib().opf_last_error().decode())
     return Handle(ptr, N, K, M)
@@ -584,11 +600,14 @@ def opf_net_train_step(n, d_x, d_ty, d_tz, B, lam, lr):
     return loss.value
 
 
-def opf_setup_query(N, K, M, m_p, alpha, Re, dt, what):
+def opf_setup_query(N, K, M, m_p, alpha, Re, dt, what, r=None):
+    """One array of the host setup (see opf.h); r: a user radial mesh or None."""
     L = lib()
     n = ctypes.c_long()
-    _check(L.opf_setup_query(N, K, M, m_p, alpha, Re, dt, what.encode(), None, 0, ctypes.byref(n)))
+    ra = None if r is None else np.ascontiguousarray(r, dtype=np.float64)
+    rp = None if ra is None else ra.ctypes.data_as(_dp)
+    _check(L.opf_setup_query_mesh(N, K, M, m_p, alpha, Re, dt, rp, what.encode(), None, 0, ctypes.byref(n)))
     out = np.empty(n.value, dtype=np.float64)
-    _check(L.opf_setup_query(N, K, M, m_p, alpha, Re, dt, what.encode(),
-                             out.ctypes.data_as(_dp), n.value, ctypes.byref(n)))
+    _check(L.opf_setup_query_mesh(N, K, M, m_p, alpha, Re, dt, rp, what.encode(),
+                                  out.ctypes.data_as(_dp), n.value, ctypes.byref(n)))
     return out

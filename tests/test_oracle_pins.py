@@ -96,6 +96,54 @@ def test_quadrature_exact_and_convergent():
     assert e32 < 1e-12 and e16 < 1e-9
 
 
+# ------------------------------------------------------------------ user meshes
+@pytest.mark.parametrize("parity", [1, -1])
+def test_fd_and_quadrature_exact_on_a_user_mesh(parity):
+    """Section 2 lets the radial points be supplied: on a mesh clustered
+    towards the axis instead of the wall, the 9-point stencils still
+    differentiate parity-consistent polynomials of degree <= 8 exactly, and the
+    quadrature integrates r f exactly for even f of degree <= 6."""
+    N = 18
+    r = inputs.stretched_mesh(N)
+    assert np.abs(r - mesh(N)).max() > 0.1  # a genuinely different mesh
+    D1, D2 = fd_matrices(r, parity)
+    s1, s2 = np.abs(D1).sum(axis=1).max(), np.abs(D2).sum(axis=1).max()
+    for pw in range(0, 9):
+        if (-1) ** pw != parity:
+            continue
+        d1 = pw * r ** (pw - 1) if pw >= 1 else 0 * r
+        d2 = pw * (pw - 1) * r ** (pw - 2) if pw >= 2 else 0 * r
+        assert np.abs(D1 @ r ** pw - d1).max() <= 1e-13 * s1
+        assert np.abs(D2 @ r ** pw - d2).max() <= 1e-13 * s2
+    w = quadrature_weights(r)
+    for j in range(4):
+        assert abs(w @ r ** (2 * j) - 1.0 / (2 * j + 2)) < 1e-14
+
+
+def test_steady_and_swirl_solutions_on_a_user_mesh():
+    """On the user mesh: Hagen-Poiseuille flow stays steady to round-off and
+    the Bessel swirl decays at exp(-j^2 t / Re) to the time and radial
+    truncation levels; the mesh reaches every radial operator and the
+    quadrature (E = 1 for laminar flow)."""
+    N, K, M = 24, 2, 2
+    r = inputs.stretched_mesh(N)
+    o = Oracle(Params(N, K, M, 1, 1.25, 1000.0, 0.01, r=r))
+    lam = inputs.laminar_state(N, K, M, r=r)
+    U = o.step(lam, 50)
+    assert np.abs(U - lam).max() < 1e-13
+    assert np.allclose(o.energy(U), 1.0, atol=1e-13)
+    j1 = sps.jn_zeros(1, 1)[0]
+    Re, dt, n = 50.0, 0.01, 50
+    o = Oracle(Params(N, K, M, 1, 1.25, Re, dt, r=r))
+    U0 = lam.copy()
+    U0[1, 0, K - 1] = 1e-2 * sps.j1(j1 * r)
+    U = o.step(U0, n)
+    want = 1e-2 * sps.j1(j1 * r) * math.exp(-j1 ** 2 * n * dt / Re)
+    assert np.abs(U[1, 0, K - 1] - want).max() / 1e-2 < 2e-5
+    with pytest.raises(ValueError):
+        Oracle(Params(N, K, M, 1, 1.25, Re, dt, r=r[::-1]))
+
+
 # ------------------------------------------------------------------ transforms
 def test_dealiased_product_equals_truncated_convolution():
     """3/2 rule (section 2): the pseudo-spectral product of two band-limited
