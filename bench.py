@@ -811,9 +811,11 @@ def run_gpu(args, w):
 
     def timed(precision):
         """K steps at one precision from U0; per-step CUDA events, L2 flushed
-        between.  A few untimed steps with an event pair around every kernel
-        give the kernel shares and the dominant kernel; the timed steps carry
-        an event pair around the dominant kernel only."""
+        between, the step graph free of any inner event record.  A few
+        untimed steps with an event pair around every kernel give the kernel
+        shares and the dominant kernel; after the timed steps, as many steps
+        again with an event pair around the dominant kernel only give its
+        live duration."""
         opf.opf_set_option(h, "precision", precision)
         opf.opf_set_state(h, U0)
         for _ in range(args.warmup):
@@ -827,11 +829,9 @@ def run_gpu(args, w):
             opf.opf_step(h, 1)
         kt_all = opf.opf_kernel_times(h, reset=True)
         dom = max(kt_all, key=lambda k: kt_all[k][0])
-        opf.opf_set_option(h, "timing", 2)
-        opf.opf_set_option(h, "timed_kernel", names.index(dom))
-        opf.opf_step(h, 1)  # capture the timed graph outside the timed region
+        opf.opf_set_option(h, "timing", 0)
+        opf.opf_step(h, 1)  # capture the plain step graph outside the timed region
         opf.opf_set_state(h, U0)
-        opf.opf_kernel_times(h, reset=True)
         clocks = ClockSampler(local)
         clocks.start()
         time.sleep(0.3)
@@ -852,10 +852,22 @@ def run_gpu(args, w):
             dist.barrier()
         clk = clocks.stop()
         total = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+        # the dominant kernel's live duration: the same steps with an event
+        # pair around that kernel only
+        opf.opf_set_option(h, "timing", 2)
+        opf.opf_set_option(h, "timed_kernel", names.index(dom))
+        opf.opf_set_state(h, U0)
+        opf.opf_step(h, 1)
+        opf.opf_set_state(h, U0)
+        opf.opf_kernel_times(h, reset=True)
+        for _ in range(args.steps):
+            flush_l2()
+            opf.opf_step(h, 1)
         kt_live = opf.opf_kernel_times(h, reset=True)
         opf.opf_set_option(h, "timing", 0)
         # per-launch averages (every kernel launches twice per step): shares
-        # from the instrumented steps, the dominant kernel's from the timed ones
+        # from the instrumented steps, the dominant kernel's from the steps
+        # that time it alone
         kt = {k: (v[0] / max(1, v[1]), 1) for k, v in kt_all.items()}
         kt[dom] = (kt_live[dom][0] / max(1, kt_live[dom][1]), 1)
         energy = opf.opf_energy(h)

@@ -120,6 +120,10 @@ int opf_nonlinear(opf_t* h, const double* coeffs, double* out);
  *                the solve) on the current state and keep the fastest; reads
  *                back as 2 once done.  Read-only keys "mcz", "mca", "zc" report
  *                the transforms' shapes in use.
+ *   "pdl":       1 = launch the kernels of a step with programmatic dependent
+ *                launch, so that each kernel's launch and read-only prologue
+ *                overlap the end of its predecessor (default), 0 = plain
+ *                launches.  Results do not depend on it.
  *   "tile":      modes per block of the solve: 0 = chosen from the grid size
  *                (default), 4, 8 or 16 (OPF_EINVAL if that block's shared
  *                memory does not fit); reads back the value set or the one the

@@ -727,6 +727,9 @@ int runner_option(Runner* r, const char* key, double v) {
   } else if (!strcmp(key, "autotune")) {
     if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "autotune: 0 or 1");
     r->autotune = (int)v;
+  } else if (!strcmp(key, "pdl")) {
+    if (v != 0.0 && v != 1.0 && v != 2.0) return fail(OPF_EINVAL, "pdl: 0, 1 or 2");
+    for (Group* g : r->groups) g->d.pdl = (int)v;
   } else if (!strcmp(key, "tile")) {
     if (v != 0.0 && v != 4.0 && v != 8.0 && v != 16.0)
       return fail(OPF_EINVAL, "tile: 0 (heuristic), 4, 8 or 16 modes per solve block");
@@ -753,6 +756,7 @@ int runner_get_option(Runner* r, const char* key, double* v) {
   else if (!strcmp(key, "timed_kernel")) *v = r->timed_kernel;
   else if (!strcmp(key, "autotune")) *v = r->autotune;
   else if (!strcmp(key, "tile")) *v = r->groups.empty() ? 0 : r->groups[0]->d.tile;
+  else if (!strcmp(key, "pdl")) *v = r->groups.empty() ? 0 : r->groups[0]->d.pdl;
   else if (!strcmp(key, "mcz")) *v = r->groups.empty() ? 0 : r->groups[0]->d.mcz;
   else if (!strcmp(key, "mca")) *v = r->groups.empty() ? 0 : r->groups[0]->d.mca;
   else if (!strcmp(key, "zc")) *v = r->groups.empty() ? 0 : r->groups[0]->d.zc;

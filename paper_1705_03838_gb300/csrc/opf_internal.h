@@ -81,6 +81,8 @@ struct Dims {
   int mcz, mca;   // m columns per block: z synthesis, z analysis
   int zc;         // z rows per block in the theta/product kernel
   int tile = 0;   // modes per block in the solve (0: heuristic)
+  int pdl = 0;    // programmatic dependent launch of the step kernels: 0 off, 1 trigger at
+                  // the top of each block, 2 before its final store phase
   // batching: B trajectories of this shape per launch (grid z); trajectory b's
   // work buffers start b*ss bytes after trajectory 0's, its setup arrays b*ps
   // bytes after (ps = 0: one shared setup)

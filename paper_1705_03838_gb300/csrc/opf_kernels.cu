@@ -19,6 +19,40 @@ namespace opf {
 
 __device__ __forceinline__ int row_lo_d(int i, int N) { return min(max(i - 4, 0), N - 9); }
 
+// Programmatic dependent launch between the kernels of a step: each step
+// kernel lets its successor launch once all of its own blocks have reached
+// the trigger (d.pdl = 1: at the top; 2: before the final store phase), and
+// waits for its predecessor grid to complete -- with its memory visible --
+// before it reads or writes any buffer another kernel of the step touches
+// (grid_dep_wait after a prologue that reads only setup data: twiddles,
+// stencils, factors).  Every step kernel waits, so the ordering is
+// transitive along the stream.  Without a programmatic launch both are
+// no-ops.
+__device__ __forceinline__ void grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_trigger_at(const Dims& d, int where) {
+  if (d.pdl == where) grid_dep_trigger();
+}
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch with the programmatic-serialisation attribute when d.pdl is set
+// (captured into a graph, the edge to the previous kernel becomes a
+// programmatic dependency), plainly otherwise.
+template <typename... KArgs, typename... Args>
+void launch_step_kernel(const Dims& d, void (*kern)(KArgs...), dim3 g, dim3 b, size_t sm, cudaStream_t st,
+                        Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = g;
+  cfg.blockDim = b;
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = d.pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 // Batched launches: trajectory b = blockIdx.z; its buffers sit `stride` bytes
 // after trajectory b-1's (stride 0: shared).  Null stays null.
 template <typename P>
@@ -210,7 +244,9 @@ __global__ void __launch_bounds__(128) k_curl(Dims d, const double* __restrict__
   const int m = blockIdx.y, kk0 = blockIdx.x * KC;
   const long fs = d.F;
   const double2* up = U + (long)m * N * nk;
+  grid_dep_trigger_at(d, 1);
   if (threadIdx.x < KC) s_ak[threadIdx.x] = d.alpha * (kk0 + (int)threadIdx.x - (d.K - 1));
+  grid_dep_wait();
   for (int e = threadIdx.x; e < N * KC; e += blockDim.x) {
     const int c = e % KC, n = e / KC, kk = kk0 + c;
     if (kk >= nk) continue;  // columns past nk are never read
@@ -223,6 +259,7 @@ __global__ void __launch_bounds__(128) k_curl(Dims d, const double* __restrict__
     if constexpr (SPLIT) s_ut32[e] = float2{(float)ut.x, (float)ut.y};
   }
   __syncthreads();
+  grid_dep_trigger_at(d, 2);
   for (int e = threadIdx.x; e < N * KC; e += blockDim.x) {
     const int c = e % KC, n = e / KC, kk = kk0 + c;
     if (kk >= nk) continue;
@@ -235,13 +272,16 @@ __global__ void __launch_bounds__(128) k_curl(Dims d, const double* __restrict__
 
 void launch_curl(const Dims& d, const DevSetup& s, const double2* U, double2* W6, cudaStream_t st) {
   dim3 g((unsigned)((d.nk + kCurlKC - 1) / kCurlKC), d.M, d.B);
-  k_curl<double2, false><<<g, 128, curl_smem(d), st>>>(d, s.d1, nullptr, nullptr, s.rinv, U, W6, nullptr);
+  launch_step_kernel(d, k_curl<double2, false>, g, dim3(128), curl_smem(d), st, d, (const double*)s.d1,
+                     (const float*)nullptr, (const double*)nullptr, (const double*)s.rinv, U, W6,
+                     (double2*)nullptr);
 }
 
 void launch_curl_split32(const Dims& d, const DevSetup& s, const double2* U, float2* W6,
                          double2* Nlin, cudaStream_t st) {
   dim3 g((unsigned)((d.nk + kCurlKC - 1) / kCurlKC), d.M, d.B);
-  k_curl<float2, true><<<g, 128, curl_smem(d), st>>>(d, s.d1, s.d1f, s.r, s.rinv, U, W6, Nlin);
+  launch_step_kernel(d, k_curl<float2, true>, g, dim3(128), curl_smem(d), st, d, (const double*)s.d1,
+                     (const float*)s.d1f, (const double*)s.r, (const double*)s.rinv, U, W6, Nlin);
 }
 
 // ------------------------------------------------------------------ z synthesis (A2)
@@ -260,8 +300,10 @@ __global__ void __launch_bounds__(128) k_zsynth(Dims d, FftPlan pz, const V* __r
   twz = bofs(twz, d.ps);
   W6 = bofs(W6, d.ss);
   Z6 = bofs(Z6, d.ss);
+  grid_dep_trigger_at(d, 1);
   for (int e = threadIdx.x; e < nz; e += blockDim.x) tw[e] = twz[e];
   const long fs = d.F;
+  grid_dep_wait();
   for (int e = threadIdx.x; e < MC * nz; e += blockDim.x) {
     const int z = e % nz, mc = e / nz, m = m0 + mc;
     int k = z < K ? z : z - nz;
@@ -274,6 +316,7 @@ __global__ void __launch_bounds__(128) k_zsynth(Dims d, FftPlan pz, const V* __r
   if constexpr (NZ > 0) res = block_fft_c<NZ, +1>(A, B, MC, ld, tw);
   else res = block_fft(A, B, MC, ld, pz, tw, +1);
   const int mcn = min(MC, d.M - m0);
+  grid_dep_trigger_at(d, 2);
   for (int e = threadIdx.x; e < mcn * nz; e += blockDim.x) {
     const int mc = e % mcn, z = e / mcn;
     Z6[(((long)f * d.N + n) * nz + z) * d.M + m0 + mc] = res[mc * ld + z];
@@ -287,7 +330,8 @@ void launch_zsynth32(const Dims& d, const DevSetup& s, const FftPlan& pz, const 
   dim3 g((d.M + d.mcz - 1) / d.mcz, d.N * 6, d.B);
   const size_t sm = zsynth_smem(d, d.mcz, sizeof(float2));
   with_fft_length(d.nz, [&](auto n) {
-    k_zsynth<float2, decltype(n)::value><<<g, 128, sm, st>>>(d, pz, s.tw_z32, W6, Z6);
+    launch_step_kernel(d, k_zsynth<float2, decltype(n)::value>, g, dim3(128), sm, st, d, pz,
+                       (const float2*)s.tw_z32, W6, Z6);
   });
 }
 
@@ -296,7 +340,8 @@ void launch_zsynth(const Dims& d, const DevSetup& s, const FftPlan& pz, const do
   dim3 g((d.M + d.mcz - 1) / d.mcz, d.N * 6, d.B);
   const size_t sm = zsynth_smem(d, d.mcz, sizeof(double2));
   with_fft_length(d.nz, [&](auto n) {
-    k_zsynth<double2, decltype(n)::value><<<g, 128, sm, st>>>(d, pz, s.tw_z, W6, Z6);
+    launch_step_kernel(d, k_zsynth<double2, decltype(n)::value>, g, dim3(128), sm, st, d, pz,
+                       (const double2*)s.tw_z, W6, Z6);
   });
 }
 
@@ -321,8 +366,10 @@ __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* _
   twth = bofs(twth, d.ps);
   Z6 = bofs(Z6, d.ss);
   ZN = bofs(ZN, d.ss);
+  grid_dep_trigger_at(d, 1);
   for (int e = threadIdx.x; e < nth; e += blockDim.x) tw[e] = twth[e];
   const long fstride = (long)d.N * nz * M;
+  grid_dep_wait();
   // spectra of the pairs (u_r,u_t), (u_z,w_r), (w_t,w_z):  Z = A + i B
   for (int e = threadIdx.x; e < zc * 3 * nth; e += blockDim.x) {
     const int q = e % nth, pr = (e / nth) % 3, zr = e / (3 * nth);
@@ -392,6 +439,7 @@ __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* _
   const V* out;
   if constexpr (NTH > 0) out = block_fft_c<NTH, -1>(C, D, 2 * zc, ld, tw);
   else out = block_fft(C, D, 2 * zc, ld, pth, tw, -1);
+  grid_dep_trigger_at(d, 2);
   for (int e = threadIdx.x; e < zc * M; e += blockDim.x) {
     const int m = e % M, zr = e / M;
     const V y = out[(zr * 2 + 0) * ld + m];
@@ -412,7 +460,8 @@ void launch_product32(const Dims& d, const DevSetup& s, const FftPlan& pth, cons
   dim3 g((d.nz + d.zc - 1) / d.zc, d.N, d.B);
   const size_t sm = product_smem(d, d.zc, sizeof(float2));
   with_fft_length(d.nth, [&](auto n) {
-    k_product<float2, decltype(n)::value><<<g, 128, sm, st>>>(d, pth, s.tw_th32, Z6, ZN);
+    launch_step_kernel(d, k_product<float2, decltype(n)::value>, g, dim3(128), sm, st, d, pth,
+                       (const float2*)s.tw_th32, Z6, ZN);
   });
 }
 
@@ -421,7 +470,8 @@ void launch_product(const Dims& d, const DevSetup& s, const FftPlan& pth, const 
   dim3 g((d.nz + d.zc - 1) / d.zc, d.N, d.B);
   const size_t sm = product_smem(d, d.zc, sizeof(double2));
   with_fft_length(d.nth, [&](auto n) {
-    k_product<double2, decltype(n)::value><<<g, 128, sm, st>>>(d, pth, s.tw_th, Z6, ZN);
+    launch_step_kernel(d, k_product<double2, decltype(n)::value>, g, dim3(128), sm, st, d, pth,
+                       (const double2*)s.tw_th, Z6, ZN);
   });
 }
 
@@ -443,8 +493,10 @@ __global__ void __launch_bounds__(128) k_zanalysis(Dims d, FftPlan pz, const V* 
   Nlin = bofs(Nlin, d.ss);
   Nout = bofs(Nout, d.ss);
   const double Re = bofs(d.prm, d.ps)[kPrmRe];
+  grid_dep_trigger_at(d, 1);
   for (int e = threadIdx.x; e < nz; e += blockDim.x) tw[e] = twz[e];
   const long fs = d.F;
+  grid_dep_wait();
   // FP64 addends of an output point (linear terms, body force); a thread's
   // first point has them loaded before the transform, so that their latency
   // overlaps it
@@ -483,6 +535,7 @@ __global__ void __launch_bounds__(128) k_zanalysis(Dims d, FftPlan pz, const V* 
   // scaling and the +- combination in the transform's precision, then FP64
   using T = typename Scalar<V>::T;
   const T sc = (T)d.inv_grid;
+  grid_dep_trigger_at(d, 2);
   for (int e = threadIdx.x; e < mcn * nk; e += blockDim.x) {
     const int kk = e % nk, mc = e / nk, m = m0 + mc;
     const int k = kk - (K - 1);
@@ -525,7 +578,8 @@ void launch_zanalysis(const Dims& d, const DevSetup& s, const FftPlan& pz, const
   dim3 g((d.M + d.mca - 1) / d.mca, d.N, d.B);
   const size_t sm = zanalysis_smem(d, d.mca, sizeof(double2));
   with_fft_length(d.nz, [&](auto n) {
-    k_zanalysis<double2, decltype(n)::value><<<g, 128, sm, st>>>(d, pz, s.tw_z, ZN, nullptr, Nout);
+    launch_step_kernel(d, k_zanalysis<double2, decltype(n)::value>, g, dim3(128), sm, st, d, pz,
+                       (const double2*)s.tw_z, ZN, (const double2*)nullptr, Nout);
   });
 }
 
@@ -534,7 +588,8 @@ void launch_zanalysis32(const Dims& d, const DevSetup& s, const FftPlan& pz, con
   dim3 g((d.M + d.mca - 1) / d.mca, d.N, d.B);
   const size_t sm = zanalysis_smem(d, d.mca, sizeof(float2));
   with_fft_length(d.nz, [&](auto n) {
-    k_zanalysis<float2, decltype(n)::value><<<g, 128, sm, st>>>(d, pz, s.tw_z32, ZN, Nlin, Nout);
+    launch_step_kernel(d, k_zanalysis<float2, decltype(n)::value>, g, dim3(128), sm, st, d, pz,
+                       (const float2*)s.tw_z32, ZN, Nlin, Nout);
   });
 }
 
@@ -753,6 +808,7 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
     return a.Uj[f * fs + base + (long)i * nk + min(kk0 + mi, nk - 1)];
   };
 
+  grid_dep_trigger_at(d, 1);
   // Pull this block's factor blocks (pressure, u+, u-, u_z per mode) and
   // basis blocks towards L2 with one bulk prefetch each, so they arrive while
   // the right-hand sides are assembled.  Factor blocks start on 16 bytes only
@@ -779,6 +835,7 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
     RIp[e] = 0.5 * (1 + mt) * ri;
     RIm[e] = 0.5 * (1 - mt) * ri;
   }
+  grid_dep_wait();  // everything above read setup data only
 #pragma unroll 4
   for (int e = tid; e < 3 * N * T; e += NB) {
     const int mi = e % T, i = (e / T) % N, f = e / (T * N);
@@ -1008,6 +1065,7 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
   }
   const double bp = has_mean ? misc[0] : 0.0;
 
+  grid_dep_trigger_at(d, 2);
   // ---- write out (coalesced over k)
 #pragma unroll 4
   for (int e = tid; e < N * NT; e += NB) {
@@ -1186,9 +1244,9 @@ void launch_solve(const Dims& d, const DevSetup& s, const SolveArgs& a, int nJ, 
   const bool stage = solve_use_stage(d, T, (long)g.x * g.y * g.z);
   SolveDev sd{s.d1, s.rinv, s.wq, s.hop, s.luH, s.luP, s.basis, s.ainv, s.G, s.prm, nJ, stage ? 1 : 0, s.d1f, s.r};
   const size_t sm = stage ? solve_smem_staged(d.N, T) : solve_smem_base(d.N, T);
-  if (T == 16) k_solve<16><<<g, 24 * 16, sm, st>>>(d, sd, a);
-  else if (T == 8) k_solve<8><<<g, 24 * 8, sm, st>>>(d, sd, a);
-  else k_solve<4><<<g, 24 * 4, sm, st>>>(d, sd, a);
+  if (T == 16) launch_step_kernel(d, k_solve<16>, g, dim3(24 * 16), sm, st, d, sd, a);
+  else if (T == 8) launch_step_kernel(d, k_solve<8>, g, dim3(24 * 8), sm, st, d, sd, a);
+  else launch_step_kernel(d, k_solve<4>, g, dim3(24 * 4), sm, st, d, sd, a);
 }
 
 // ------------------------------------------------------------------ diagnostics
