@@ -590,7 +590,7 @@ def run_large(args):
     print(json.dumps(line), flush=True)
 
 
-LEARNED = dict(N=48, K=24, M=16, m_p=2, alpha=1.25, dt=0.005, precision=1,
+LEARNED = dict(N=48, K=16, M=16, m_p=2, alpha=1.25, dt=0.005, precision=1,
                Re_train=(2000.0, 2500.0), Re_test=2250.0, amp=(0.03, 0.12), B_train=56, B_val=6, B_test=8,
                seed=1705, warmup=20.0, n_snap=320, every=0.5, T_min=10.0, T_max=100.0, thresh=0.3,
                hidden=384, steps=3000, batch=64, lr=1e-3, lam=1.0, net_seed=5, eval_every=200,
@@ -601,7 +601,9 @@ LEARNED = dict(N=48, K=24, M=16, m_p=2, alpha=1.25, dt=0.005, precision=1,
 def run_learned(args):
     """Learned Newton-Krylov proposals: 64 trajectories (56 for training, 6 of
     them for validation, at Re uniform in [2000, 2500]; 8 held out at Re = 2250)
-    of N=48, |k|<24, m<16, m_p=2, 20,480 snapshots every 0.5 time units; the
+    of N=48, |k|<16, m<16, m_p=2 (the named resolution with the radial points
+    raised from 32 to 48: at N=32 these starts go non-finite whatever K and
+    M, at N=48 they stay resolved), 20,480 snapshots every 0.5 time units; the
     BF16 network trained by the library's own kernels; Newton-Krylov-hookstep
     from the 12 best held-out recurrences with recurrence, learned,
     learned-state and snapshot-with-mean-period guesses under the same budget."""
@@ -625,7 +627,7 @@ def run_learned(args):
         "n_gpus": 1,
         "dtype": "bf16 net (f32 accumulate); f32+f64 snapshots; f64 Newton",
         "data": "synthetic (the solver's own trajectories from seeded perturbations)",
-        "config": {"workload": "learned proposals: N=48 |k|<24 m<16 m_p=2 alpha=1.25, Re in [2000,2500], "
+        "config": {"workload": "learned proposals: N=48 |k|<16 m<16 m_p=2 alpha=1.25, Re in [2000,2500], "
                                "64 trajectories x 320 snapshots"},
         "recurrence_median_final": nk.get("recurrence", {}).get("median_final"),
         "snapshot_mean_T_median_final": nk.get("snapshot_mean_T", {}).get("median_final"),

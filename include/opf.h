@@ -310,6 +310,21 @@ int opf_net_gradients(opf_net_t* n, const float* d_x, const float* d_ty, const f
                       float lambda, double* loss);
 int opf_net_train_step(opf_net_t* n, const float* d_x, const float* d_ty, const float* d_tz, int B,
                        float lambda, float lr, double* loss);
+/* Training minibatch with the flow's symmetries applied (data augmentation,
+ * on the net's stream, ordered before the next train step): sample b is row
+ * idx[b] < rows of the DEVICE sets d_x, d_y ([rows][L][ncomp*nkf*mf*2]
+ * float32, channels (component, axial index, azimuthal index, re/im),
+ * axial index kidx for k = kidx - (nkf - 1)/2) and d_z ([rows][nz]); each
+ * complex channel of its x and y is multiplied by e^{i(ang[2b] k +
+ * ang[2b+1] m)} -- an axial shift by a with ang[2b] = alpha a and an
+ * azimuthal rotation by phi with ang[2b+1] = m_p phi, both symmetries of
+ * pipe flow -- and its z is copied unchanged (period and shift are
+ * invariant).  idx and ang are HOST arrays (B and 2B entries, copied);
+ * outputs d_bx, d_by ([B][L][...]) and d_bz ([B][nz]) are DEVICE buffers.
+ * OPF_EINVAL on bad sizes or an index out of range. */
+int opf_net_gather_augment(opf_net_t* n, int B, int L, int ncomp, int nkf, int mf, int nz, const float* d_x,
+                           const float* d_y, const float* d_z, long rows, const int* idx, const float* ang,
+                           float* d_bx, float* d_by, float* d_bz);
 
 /* No counterpart in the paper: an allocation-free variant of opf_nonlinear
  * for callers that must not allocate device memory when they call (their

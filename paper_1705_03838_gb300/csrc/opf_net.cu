@@ -242,6 +242,9 @@ struct opf_net {
   float *pre1 = nullptr, *pre2 = nullptr, *y = nullptr, *dy = nullptr, *dh = nullptr;
   float *pooled = nullptr, *z = nullptr, *dzh = nullptr, *dpooled = nullptr;
   double* sums = nullptr;
+  int* aug_idx = nullptr;    // minibatch rows of opf_net_gather_augment (device)
+  float* aug_ang = nullptr;  // their shift / rotation phases
+  int aug_cap = 0;
   cudaStream_t st = nullptr;
 };
 
@@ -417,6 +420,35 @@ int net_gradients(opf_net* n, const float* x, const float* ty, const float* tz, 
   return OPF_OK;
 }
 
+// Minibatch gather with the pipe-flow symmetries applied (training-data
+// augmentation): sample b is row idx[b] of the device-resident set, its
+// complex channel (component, axial index kidx, azimuthal m) turned by
+// e^{i (ang[2b] k + ang[2b+1] m)}, k = kidx - (nkf - 1)/2 -- an axial shift
+// (ang[2b] = alpha a) and an azimuthal rotation (ang[2b+1] = m_p phi).  The
+// head targets are gathered unchanged (period and shift are invariant).
+__global__ void k_gather_augment(const float2* __restrict__ x, const float2* __restrict__ y,
+                                 const float* __restrict__ z, const int* __restrict__ idx,
+                                 const float* __restrict__ ang, int B, int L, int ncomp, int nkf, int mf, int nz,
+                                 float2* __restrict__ bx, float2* __restrict__ by, float* __restrict__ bz) {
+  const long C = (long)ncomp * nkf * mf;
+  const long total = (long)B * L * C;
+  const long stride = (long)gridDim.x * blockDim.x;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total; t += stride) {
+    const long ch = t % C, bl = t / C;
+    const int l = (int)(bl % L), b = (int)(bl / L);
+    const int m = (int)(ch % mf), kidx = (int)((ch / mf) % nkf);
+    const float ph = ang[2 * b] * (float)(kidx - (nkf - 1) / 2) + ang[2 * b + 1] * (float)m;
+    float sn, cs;
+    sincosf(ph, &sn, &cs);
+    const long src = ((long)idx[b] * L + l) * C + ch, dst = ((long)b * L + l) * C + ch;
+    const float2 xv = x[src], yv = y[src];
+    bx[dst] = make_float2(xv.x * cs - xv.y * sn, xv.x * sn + xv.y * cs);
+    by[dst] = make_float2(yv.x * cs - yv.y * sn, yv.x * sn + yv.y * cs);
+  }
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < (long)B * nz; t += stride)
+    bz[t] = z[(long)idx[t / nz] * nz + t % nz];
+}
+
 void refresh_bf16(opf_net* n) {
   k_to_bf16<<<gs(n->total), 256, 0, n->st>>>(n->P, n->Pb, n->total);
   prepare_weights(n);
@@ -499,7 +531,8 @@ void opf_net_destroy(opf_net_t* n) {
                   (void*)n->y, (void*)n->dy, (void*)n->dh, (void*)n->pooled, (void*)n->z, (void*)n->dzh,
                   (void*)n->dpooled, (void*)n->sums, (void*)n->col[0], (void*)n->col[1], (void*)n->col[2],
                   (void*)n->colT, (void*)n->dzT, (void*)n->dzcol, (void*)n->wp[0], (void*)n->wp[1],
-                  (void*)n->wp[2], (void*)n->ws[0], (void*)n->ws[1], (void*)n->err, (void*)n->gwork})
+                  (void*)n->wp[2], (void*)n->ws[0], (void*)n->ws[1], (void*)n->err, (void*)n->gwork,
+                  (void*)n->aug_idx, (void*)n->aug_ang})
     if (p) cudaFree(p);
   if (n->st) cudaStreamDestroy(n->st);
   delete n;
@@ -585,6 +618,39 @@ int opf_net_train_step(opf_net_t* n, const float* d_x, const float* d_ty, const 
   k_adam<<<gs(n->total), 256, 0, n->st>>>(n->P, n->G, n->M1, n->M2, n->total, lr, b1, b2, c1, c2, 1e-8f, n->Pb);
   prepare_weights(n);
   NCU(cudaStreamSynchronize(n->st));
+  NCU(cudaGetLastError());
+  return OPF_OK;
+}
+
+int opf_net_gather_augment(opf_net_t* n, int B, int L, int ncomp, int nkf, int mf, int nz, const float* d_x,
+                           const float* d_y, const float* d_z, long rows, const int* idx, const float* ang,
+                           float* d_bx, float* d_by, float* d_bz) {
+  if (!n || B < 1 || L < 1 || ncomp < 1 || nkf < 1 || mf < 1 || nz < 1 || rows < 1 || !d_x || !d_y || !d_z ||
+      !idx || !ang || !d_bx || !d_by || !d_bz) {
+    opf::set_last_error("opf_net_gather_augment: bad arguments");
+    return OPF_EINVAL;
+  }
+  for (int b = 0; b < B; ++b)
+    if (idx[b] < 0 || idx[b] >= rows) {
+      opf::set_last_error("opf_net_gather_augment: sample index out of range");
+      return OPF_EINVAL;
+    }
+  if (n->aug_cap < B) {
+    if (n->aug_idx) cudaFree(n->aug_idx);
+    if (n->aug_ang) cudaFree(n->aug_ang);
+    n->aug_idx = nullptr;
+    n->aug_ang = nullptr;
+    n->aug_cap = 0;
+    NCU(cudaMalloc((void**)&n->aug_idx, (size_t)B * sizeof(int)));
+    NCU(cudaMalloc((void**)&n->aug_ang, (size_t)2 * B * sizeof(float)));
+    n->aug_cap = B;
+  }
+  NCU(cudaMemcpyAsync(n->aug_idx, idx, (size_t)B * sizeof(int), cudaMemcpyHostToDevice, n->st));
+  NCU(cudaMemcpyAsync(n->aug_ang, ang, (size_t)2 * B * sizeof(float), cudaMemcpyHostToDevice, n->st));
+  const long total = (long)B * L * ncomp * nkf * mf;
+  k_gather_augment<<<gs(total), 256, 0, n->st>>>((const float2*)d_x, (const float2*)d_y, d_z, n->aug_idx,
+                                                 n->aug_ang, B, L, ncomp, nkf, mf, nz, (float2*)d_bx,
+                                                 (float2*)d_by, d_bz);
   NCU(cudaGetLastError());
   return OPF_OK;
 }

@@ -241,31 +241,40 @@ def rotate_features(f, a, phi, alpha, m_p):
     return np.stack([z.real, z.imag], axis=-1).reshape(f.shape).astype(np.float32)
 
 
-def train(opf, torch, net, data, steps, batch, lr, lam, scale, seed=0, augment=None):
+def device_set(torch, data, scale):
+    """The training set (x, ty, tz) resident on the device, features divided
+    by scale (float32)."""
+    x, ty, tz = data
+    return (torch.from_numpy(np.ascontiguousarray(x / scale, dtype=np.float32)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(ty / scale, dtype=np.float32)).cuda(),
+            torch.from_numpy(np.ascontiguousarray(tz, dtype=np.float32)).cuda())
+
+
+def train(opf, torch, net, data, steps, batch, lr, lam, scale, seed=0, augment=None, dev=None):
     """Adam on minibatches of data = (x, ty, tz), features divided by scale.
-    augment = (alpha, m_p): each sample gets a random axial shift and
+    The set stays on the device (dev: a device_set of it, made here if
+    None); each minibatch is gathered there by the library, and with
+    augment = (alpha, m_p) each sample gets a random axial shift and
     azimuthal rotation (the labels T and s are invariant; the state
     correction turns with the state).  Returns the per-step losses."""
     x, ty, tz = data
     rng = np.random.default_rng(seed)
-    xs = (x / scale).astype(np.float32)
-    ys = (ty / scale).astype(np.float32)
+    dx, dy, dz = dev if dev is not None else device_set(torch, data, scale)
+    rows, L = x.shape[0], x.shape[1]
     bx = torch.empty((batch,) + tuple(x.shape[1:]), dtype=torch.float32, device="cuda")
     by = torch.empty_like(bx)
     bz = torch.empty((batch, tz.shape[1]), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()  # the set and the buffers exist before the net's stream uses them
     losses = []
     for _ in range(steps):
-        idx = rng.integers(0, x.shape[0], batch)
-        fx, fy = xs[idx], ys[idx]
+        idx = rng.integers(0, rows, batch)
+        ang = np.zeros((batch, 2))
         if augment is not None:
             al, mp = augment
-            a = rng.uniform(0.0, 2 * np.pi / al, batch)
-            phi = rng.uniform(0.0, 2 * np.pi / mp, batch)
-            fx = rotate_features(fx, a, phi, al, mp)
-            fy = rotate_features(fy, a, phi, al, mp)
-        bx.copy_(torch.from_numpy(fx))
-        by.copy_(torch.from_numpy(fy))
-        bz.copy_(torch.from_numpy(np.ascontiguousarray(tz[idx], dtype=np.float32)))
+            ang[:, 0] = al * rng.uniform(0.0, 2 * np.pi / al, batch)   # alpha a
+            ang[:, 1] = mp * rng.uniform(0.0, 2 * np.pi / mp, batch)   # m_p phi
+        opf.opf_net_gather_augment(net, dx.data_ptr(), dy.data_ptr(), dz.data_ptr(), rows, idx, ang, L, 3, NKF, MF,
+                                   tz.shape[1], bx.data_ptr(), by.data_ptr(), bz.data_ptr())
         losses.append(opf.opf_net_train_step(net, bx.data_ptr(), by.data_ptr(), bz.data_ptr(), batch, lam, lr))
     return losses
 
@@ -389,9 +398,10 @@ def run_pipeline(opf, torch, cfg, log=None):
     losses = []
     torch.cuda.synchronize()
     t0 = _time.perf_counter()
+    dev = device_set(torch, train_set, scale)
     for r in range(0, c["steps"], every):
         losses += train(opf, torch, net, train_set, min(every, c["steps"] - r), c["batch"], c["lr"], lam, scale,
-                        seed=c["seed"] + r, augment=(alpha, m_p) if c.get("augment", True) else None)
+                        seed=c["seed"] + r, augment=(alpha, m_p) if c.get("augment", True) else None, dev=dev)
         v = evaluate_loss(opf, torch, net, val_set, lam, scale)
         if v < best[0]:
             best = (v, r + every, opf.opf_net_get_params(net))

@@ -151,6 +151,8 @@ def lib():
         L.opf_net_gradients.argtypes = [vp, vp, vp, vp, i, ctypes.c_float, _dp]
         L.opf_net_train_step.restype = i
         L.opf_net_train_step.argtypes = [vp, vp, vp, vp, i, ctypes.c_float, ctypes.c_float, _dp]
+        L.opf_net_gather_augment.restype = i
+        L.opf_net_gather_augment.argtypes = [vp, i, i, i, i, i, i, vp, vp, vp, ctypes.c_long, vp, vp, vp, vp, vp]
         L.opf_nonlinear_noalloc.restype = i
         L.opf_nonlinear_noalloc.argtypes = [i, i, i, i, d, d, vp, vp, vp]
         L.opf_set_forcing.restype = i
@@ -598,6 +600,18 @@ def opf_net_train_step(n, d_x, d_ty, d_tz, B, lam, lr):
     _check(lib().opf_net_train_step(n.ptr, ctypes.c_void_p(d_x), ctypes.c_void_p(d_ty), ctypes.c_void_p(d_tz),
                                     int(B), float(lam), float(lr), ctypes.byref(loss)))
     return loss.value
+
+
+def opf_net_gather_augment(net, d_x, d_y, d_z, rows, idx, ang, L, ncomp, nkf, mf, nz, d_bx, d_by, d_bz):
+    """Device minibatch: rows idx of the device sets, each turned by the
+    phases ang[b] = (alpha a, m_p phi); d_* are device addresses."""
+    ia = np.ascontiguousarray(idx, dtype=np.int32)
+    aa = np.ascontiguousarray(ang, dtype=np.float32).reshape(-1)
+    B = ia.shape[0]
+    if aa.shape[0] != 2 * B:
+        raise OpfError(OPF_EINVAL, "opf_net_gather_augment: ang needs two phases per sample")
+    _check(lib().opf_net_gather_augment(net.ptr, B, L, ncomp, nkf, mf, nz, d_x, d_y, d_z, int(rows),
+                                        ia.ctypes.data, aa.ctypes.data, d_bx, d_by, d_bz))
 
 
 def opf_setup_query(N, K, M, m_p, alpha, Re, dt, what, r=None):

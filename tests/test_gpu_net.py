@@ -69,3 +69,40 @@ def test_training_reduces_loss(env):
     losses = [opf.opf_net_train_step(net, dx.data_ptr(), dty.data_ptr(), dtz.data_ptr(), B, 1.0, 1e-3)
               for _ in range(60)]
     assert losses[-1] < 0.2 * losses[0]
+
+
+def test_device_minibatch_augmentation_matches_the_host_rotation(env):
+    """opf_net_gather_augment (the training minibatch, gathered and turned by
+    the flow's symmetries on the device) against learned.rotate_features
+    (the host form): an axial shift a and azimuthal rotation phi per sample
+    multiply mode (k, m) by e^{i(alpha k a + m_p m phi)}; the head targets are
+    gathered unchanged."""
+    torch, opf = env
+    from paper_1705_03838_gb300 import learned as lp
+
+    rng = np.random.default_rng(3)
+    rows, L, nz, B, alpha, m_p = 40, 12, 3, 16, 1.25, 2
+    x = rng.standard_normal((rows, L, lp.NCH)).astype(np.float32)
+    y = rng.standard_normal((rows, L, lp.NCH)).astype(np.float32)
+    z = rng.standard_normal((rows, nz)).astype(np.float32)
+    idx = rng.integers(0, rows, B)
+    a = rng.uniform(0, 2 * np.pi / alpha, B)
+    phi = rng.uniform(0, 2 * np.pi / m_p, B)
+    net = opf.opf_net_create(lp.NCH, 16, L, nz, seed=1)
+    dx, dy, dz = (torch.from_numpy(v).cuda() for v in (x, y, z))
+    bx = torch.empty((B, L, lp.NCH), device="cuda")
+    by = torch.empty_like(bx)
+    bz = torch.empty((B, nz), device="cuda")
+    torch.cuda.synchronize()
+    ang = np.stack([alpha * a, m_p * phi], axis=1)
+    opf.opf_net_gather_augment(net, dx.data_ptr(), dy.data_ptr(), dz.data_ptr(), rows, idx, ang, L, 3, lp.NKF,
+                               lp.MF, nz, bx.data_ptr(), by.data_ptr(), bz.data_ptr())
+    torch.cuda.synchronize()
+    want_x = lp.rotate_features(x[idx], a, phi, alpha, m_p)
+    want_y = lp.rotate_features(y[idx], a, phi, alpha, m_p)
+    assert np.abs(bx.cpu().numpy() - want_x).max() < 2e-5 * np.abs(want_x).max()
+    assert np.abs(by.cpu().numpy() - want_y).max() < 2e-5 * np.abs(want_y).max()
+    assert np.array_equal(bz.cpu().numpy(), z[idx])
+    with pytest.raises(opf.OpfError):
+        opf.opf_net_gather_augment(net, dx.data_ptr(), dy.data_ptr(), dz.data_ptr(), rows, [rows], [[0.0, 0.0]],
+                                   L, 3, lp.NKF, lp.MF, nz, bx.data_ptr(), by.data_ptr(), bz.data_ptr())
