@@ -120,6 +120,16 @@ int opf_nonlinear(opf_t* h, const double* coeffs, double* out);
  *                the solve) on the current state and keep the fastest; reads
  *                back as 2 once done.  Read-only keys "mcz", "mca", "zc" report
  *                the transforms' shapes in use.
+ *   "fused":     mixed precision only: the z synthesis, theta product and z
+ *                analysis as one launch -- a cluster of blocks per radial
+ *                plane exchanging the half-physical fields through
+ *                distributed shared memory -- where the transform lengths
+ *                are 48, 72 or 96: 0 = three launches (default), 1 = fused
+ *                with the cluster size chosen (4, or 8 for few planes),
+ *                2/4/8 = fused with that cluster size; the autotuner times
+ *                both forms and keeps the faster.  Results are identical.
+ *                Reads back the cluster size in use (0: three launches).
+ *   "timed_kernel" (with "timing" 2): 5 = the fused transforms.
  *   "pdl":       1 = launch the kernels of a step with programmatic dependent
  *                launch, so that each kernel's launch and read-only prologue
  *                overlap the end of its predecessor (default), 0 = plain

@@ -43,8 +43,8 @@ void set_last_error(const std::string& m) { g_err = m; }
 namespace {
 
 constexpr int kMaxSlots = 128;
-const char* kNames[] = {"curl", "zsynth", "product", "zanalysis", "solve"};
-constexpr int kNumNames = 5;
+const char* kNames[] = {"curl", "zsynth", "product", "zanalysis", "solve", "transforms"};
+constexpr int kNumNames = 6;
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -435,6 +435,12 @@ void enqueue_nonlinear(Runner* r, const Group& g, const double2* U, double2* Nou
   cudaStream_t st = r->st();
   if (with_curl) enqueue_curl(r, g, U);
   if (r->precision == 1) {
+    if (opf::fused32_cluster(d)) {  // the three transforms as one cluster launch
+      r->begin(5);
+      opf::launch_nl_fused32(d, g.ds, g.W6f, g.Nlin, Nout, st);
+      r->end();
+      return;
+    }
     r->begin(1);
     opf::launch_zsynth32(d, g.ds, g.pz, g.W6f, g.Z6f, st);
     r->end();
@@ -611,6 +617,22 @@ int tune_group(Runner* r, Group* g) {
     if (t < best) best = t, pick = c;
   }
   d.mca = pick;
+  if (mixed) {  // the three transforms as they stand, against the fused launch per cluster size
+    d.fused = 0;
+    best = time_launch(r, [&] {
+      opf::launch_zsynth32(d, g->ds, g->pz, g->W6f, g->Z6f, st);
+      opf::launch_product32(d, g->ds, g->pth, g->Z6f, g->ZNf, st);
+      opf::launch_zanalysis32(d, g->ds, g->pz, g->ZNf, g->Nlin, g->Nq, st);
+    });
+    pick = 0;
+    for (int C : {2, 4, 8}) {
+      d.fused = C;
+      if (opf::fused32_cluster(d) != C) continue;
+      const float t = time_launch(r, [&] { opf::launch_nl_fused32(d, g->ds, g->W6f, g->Nlin, g->Nq, st); });
+      if (t < best) best = t, pick = C;
+    }
+    d.fused = pick;
+  }
   best = 1e30f;
   pick = 0;
   for (int T : {4, 8, 16}) {
@@ -722,11 +744,15 @@ int runner_option(Runner* r, const char* key, double v) {
     if ((int)v != r->timing) r->drop_graph();  // the event nodes are part of the graph
     r->timing = (int)v;
   } else if (!strcmp(key, "timed_kernel")) {
-    if (!(v >= 0 && v <= 4 && v == std::floor(v))) return fail(OPF_EINVAL, "timed_kernel: 0..4");
+    if (!(v >= 0 && v <= 5 && v == std::floor(v))) return fail(OPF_EINVAL, "timed_kernel: 0..5");
     r->timed_kernel = (int)v;
   } else if (!strcmp(key, "autotune")) {
     if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "autotune: 0 or 1");
     r->autotune = (int)v;
+  } else if (!strcmp(key, "fused")) {
+    if (v != 0.0 && v != 1.0 && v != 2.0 && v != 4.0 && v != 8.0)
+      return fail(OPF_EINVAL, "fused: 0 (off), 1 (cluster size chosen), 2, 4 or 8 (cluster size)");
+    for (Group* g : r->groups) g->d.fused = (int)v;
   } else if (!strcmp(key, "pdl")) {
     if (v != 0.0 && v != 1.0 && v != 2.0) return fail(OPF_EINVAL, "pdl: 0, 1 or 2");
     for (Group* g : r->groups) g->d.pdl = (int)v;
@@ -757,6 +783,7 @@ int runner_get_option(Runner* r, const char* key, double* v) {
   else if (!strcmp(key, "autotune")) *v = r->autotune;
   else if (!strcmp(key, "tile")) *v = r->groups.empty() ? 0 : r->groups[0]->d.tile;
   else if (!strcmp(key, "pdl")) *v = r->groups.empty() ? 0 : r->groups[0]->d.pdl;
+  else if (!strcmp(key, "fused")) *v = r->groups.empty() ? 0 : opf::fused32_cluster(r->groups[0]->d);
   else if (!strcmp(key, "mcz")) *v = r->groups.empty() ? 0 : r->groups[0]->d.mcz;
   else if (!strcmp(key, "mca")) *v = r->groups.empty() ? 0 : r->groups[0]->d.mca;
   else if (!strcmp(key, "zc")) *v = r->groups.empty() ? 0 : r->groups[0]->d.zc;

@@ -81,6 +81,8 @@ struct Dims {
   int mcz, mca;   // m columns per block: z synthesis, z analysis
   int zc;         // z rows per block in the theta/product kernel
   int tile = 0;   // modes per block in the solve (0: heuristic)
+  int fused = 0;  // mixed precision: the three transform kernels as one cluster launch where it
+                  // fits (0 off, 1 cluster size chosen, 2/4/8 that cluster size)
   int pdl = 0;    // programmatic dependent launch of the step kernels: 0 off, 1 trigger at
                   // the top of each block, 2 before its final store phase
   // batching: B trajectories of this shape per launch (grid z); trajectory b's
@@ -134,6 +136,11 @@ void launch_product32(const Dims& d, const DevSetup& s, const FftPlan& pth, cons
                       float2* ZN, cudaStream_t st);
 void launch_zanalysis32(const Dims& d, const DevSetup& s, const FftPlan& pz, const float2* ZN,
                         const double2* Nlin, double2* Nout, cudaStream_t st);
+// The three FP32 transform kernels above as one cluster launch (false, and
+// nothing launched, where the shape takes the three-kernel path).
+bool launch_nl_fused32(const Dims& d, const DevSetup& s, const float2* W6, const double2* Nlin, double2* Nout,
+                       cudaStream_t st);
+int fused32_cluster(const Dims& d);
 struct SolveArgs {
   const double2* Uj;
   const double2* Na;

@@ -9,6 +9,8 @@
 //               (N_r, N_theta) -> N+-, base forcing 4/Re on the (0,0) mode
 // Linear part (section 2.2, banded LU per Fourier mode; section 2 influence
 // matrix): k_solve, one block per tile of T modes at fixed m.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cstdio>
 
@@ -593,6 +595,278 @@ void launch_zanalysis32(const Dims& d, const DevSetup& s, const FftPlan& pz, con
   });
 }
 
+// ------------------------------------------------------------------ fused FP32 transforms (A2-A4)
+// The mixed-precision nonlinear term after the curl, in one launch: a cluster
+// of C blocks per (radial plane n, trajectory b) keeps the plane's
+// half-physical fields in distributed shared memory instead of round trips
+// through L2 between three kernels.
+//   phase 1  block r takes m columns [r MC, (r+1) MC) of all six fields:
+//            inverse z transforms (the z synthesis kernel's arithmetic);
+//   phase 2  block r takes z rows [r ZR, (r+1) ZR): gathers those rows of
+//            every m column from the blocks that own them, inverse theta
+//            transforms, u x w (with the Coriolis term and the CFL maximum),
+//            forward theta transforms (the product kernel's arithmetic);
+//   phase 3  block r takes its m columns again: gathers them over all z rows,
+//            forward z transforms, truncation, scaling, +- form and the FP64
+//            addends (the z analysis kernel's arithmetic).
+// Each transform runs the same block FFT on the same sequences as the
+// three-kernel path, so the results are identical to it.
+namespace cg = cooperative_groups;
+
+__host__ __device__ inline int fused_mc(int M, int C) { return (M + C - 1) / C; }
+__host__ __device__ inline int fused_zr(int nz, int C) { return (nz + C - 1) / C; }
+
+size_t fused32_smem(const Dims& d, int C) {
+  const int MC = fused_mc(d.M, C), ZR = fused_zr(d.nz, C);
+  return (2 * 6 * (size_t)MC * (d.nz + 1) + 3 * (size_t)ZR * d.M + d.nz + d.nth) * sizeof(float2);
+}
+
+template <int NZ, int NTH>
+__global__ void __launch_bounds__(256) k_nl_fused32(Dims d, int C, const float2* __restrict__ twz,
+                                                    const float2* __restrict__ twth,
+                                                    const float2* __restrict__ W6,
+                                                    const double2* __restrict__ Nlin,
+                                                    double2* __restrict__ Nout) {
+  using V = float2;
+  using T = float;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int LDZ = NZ + 1;
+  const int M = d.M, K = d.K, nk = d.nk, N = d.N;
+  const int MC = fused_mc(M, C), ZR = fused_zr(NZ, C);
+  const int rank = (int)cl.block_rank();
+  const int n = blockIdx.x / C;
+  V* A = (V*)smraw;            // [6 MC][LDZ]  phase 1 (then phase 3)
+  V* B = A + 6 * MC * LDZ;     // [6 MC][LDZ]  phase 1 ping-pong (then phase 2)
+  V* ZNl = B + 6 * MC * LDZ;   // [3][ZR][M]   product spectra of this block's z rows
+  V* tz = ZNl + 3 * ZR * M;    // [NZ]
+  V* tth = tz + NZ;            // [NTH]
+  twz = bofs(twz, d.ps);
+  twth = bofs(twth, d.ps);
+  W6 = bofs(W6, d.ss);
+  Nlin = bofs(Nlin, d.ss);
+  Nout = bofs(Nout, d.ss);
+  const double Re = bofs(d.prm, d.ps)[kPrmRe];
+  for (int e = threadIdx.x; e < NZ; e += blockDim.x) tz[e] = twz[e];
+  for (int e = threadIdx.x; e < NTH; e += blockDim.x) tth[e] = twth[e];
+  const long fs = d.F;
+  const int m0 = rank * MC;
+  const int mcn = max(0, min(MC, M - m0));
+
+  // ---- phase 1: inverse z transforms of this block's m columns, six fields
+  for (int e = threadIdx.x; e < 6 * MC * NZ; e += blockDim.x) {
+    const int z = e % NZ, col = e / NZ, f = col / MC, mc = col % MC;
+    const int k = z < K ? z : z - NZ;
+    V v = V{0, 0};
+    if (mc < mcn && (z < K || z > NZ - K)) v = W6[f * fs + ((long)(m0 + mc) * N + n) * nk + k + K - 1];
+    A[col * LDZ + z] = v;
+  }
+  __syncthreads();
+  V* res1 = block_fft_c<NZ, +1>(A, B, 6 * MC, LDZ, tz);
+  V* free1 = (res1 == A) ? B : A;
+  cl.sync();  // every block's half-physical columns are in place
+
+  // ---- phase 2: this block's z rows: theta transforms and the product
+  const int z0 = rank * ZR;
+  const int zrn = max(0, min(ZR, NZ - z0));
+  const int ZC = max(1, min(max(zrn, 1), (6 * MC * LDZ) / (6 * NTH)));
+  V* P0 = free1;               // [3 ZC][NTH]
+  V* P1 = free1 + 3 * ZC * NTH;  // [3 ZC][NTH]
+  double* cfl = bofs(d.cfl, d.ss);
+  T inv_dr = 0, inv_rdt = 0, inv_dz = 0, Ubase = 0;
+  if (cfl) {
+    const double* rinv = bofs(d.rinv_cfl, d.ps);
+    const T one = 1, rn = one / (T)rinv[n];
+    const T rm = n > 0 ? one / (T)rinv[n - 1] : -rn;
+    const T rp = n < N - 1 ? one / (T)rinv[n + 1] : one + (one - rm);
+    const T twopi = (T)6.283185307179586;
+    inv_dr = one / fmin(rn - rm, rp - rn);
+    inv_rdt = (T)(d.m_p * NTH) / (twopi * rn);
+    inv_dz = (T)d.alpha * (T)NZ / twopi;
+    Ubase = one - rn * rn;
+  }
+  T cmax = 0;
+  for (int c0 = 0; c0 < zrn; c0 += ZC) {
+    const int zc = min(ZC, zrn - c0);
+    // spectra of the pairs (u_r,u_t), (u_z,w_r), (w_t,w_z):  Z = A + i B
+    for (int e = threadIdx.x; e < zc * 3 * NTH; e += blockDim.x) {
+      const int q = e % NTH, pr = (e / NTH) % 3, zr = e / (3 * NTH);
+      const int z = z0 + c0 + zr;
+      V v = V{0, 0};
+      const int mq = q < M ? q : (q > NTH - M ? NTH - q : -1);
+      if (mq >= 0) {
+        const V* src = cl.map_shared_rank(res1, mq / MC);
+        V a = src[((2 * pr) * MC + mq % MC) * LDZ + z], b = src[((2 * pr + 1) * MC + mq % MC) * LDZ + z];
+        if (q < M) {
+          if (q == 0) {
+            a.y = 0;
+            b.y = 0;
+          }
+          v = V{a.x - b.y, a.y + b.x};
+        } else {
+          v = V{a.x + b.y, -a.y + b.x};  // conj(a) + i conj(b)
+        }
+      }
+      P0[(zr * 3 + pr) * NTH + q] = v;
+    }
+    __syncthreads();
+    V* res = block_fft_c<NTH, +1>(P0, P1, 3 * zc, NTH, tth);
+    V* Cb = (res == P0) ? P1 : P0;
+    for (int e = threadIdx.x; e < zc * NTH; e += blockDim.x) {
+      const int q = e % NTH, zr = e / NTH;
+      const V x0 = res[(zr * 3 + 0) * NTH + q], x1 = res[(zr * 3 + 1) * NTH + q], x2 = res[(zr * 3 + 2) * NTH + q];
+      const T ur = x0.x, ut = x0.y, uz = x1.x, wr = x1.y, wt = x2.x, wz = x2.y;
+      T nr = ut * wz - uz * wt, nt = uz * wr - ur * wz, nz = ur * wt - ut * wr;
+      if (d.rotate) {  // Coriolis -2 Omega x u, Omega in cylindrical components at theta_q
+        T sn, cs;
+        sincos_pi((T)(2 * q) / (T)(d.m_p * NTH), &sn, &cs);
+        const T rx = (T)d.rot_x, ry = (T)d.rot_y;
+        const T o_r = rx * cs + ry * sn, o_t = -rx * sn + ry * cs;
+        const T o_z = (T)d.rot_z;
+        nr -= (T)2 * (o_t * uz - o_z * ut);
+        nt -= (T)2 * (o_z * ur - o_r * uz);
+        nz -= (T)2 * (o_r * ut - o_t * ur);
+      }
+      Cb[(zr * 2 + 0) * NTH + q] = V{nr, nt};
+      Cb[(zr * 2 + 1) * NTH + q] = V{nz, (T)0};
+      if (cfl) cmax = fmax(cmax, fmax(fabs(ur) * inv_dr, fmax(fabs(ut) * inv_rdt, fabs(uz + Ubase) * inv_dz)));
+    }
+    __syncthreads();
+    V* Db = (Cb == P0) ? P1 : P0;
+    const V* out = block_fft_c<NTH, -1>(Cb, Db, 2 * zc, NTH, tth);
+    for (int e = threadIdx.x; e < zc * M; e += blockDim.x) {
+      const int m = e % M, zr = e / M;
+      const V y = out[(zr * 2 + 0) * NTH + m];
+      const V yc = out[(zr * 2 + 0) * NTH + (m == 0 ? 0 : NTH - m)];
+      const int row = c0 + zr;
+      ZNl[(0 * ZR + row) * M + m] = V{(T)0.5 * (y.x + yc.x), (T)0.5 * (y.y - yc.y)};
+      ZNl[(1 * ZR + row) * M + m] = V{(T)0.5 * (y.y + yc.y), (T)-0.5 * (y.x - yc.x)};
+      ZNl[(2 * ZR + row) * M + m] = out[(zr * 2 + 1) * NTH + m];
+    }
+    __syncthreads();  // P0 / P1 are reused by the next chunk of rows
+  }
+  if (cfl) {  // warp max, then one atomic per warp (non-negative doubles order as integers)
+    for (int o = 16; o > 0; o >>= 1) cmax = fmax(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    const double cm = (double)cmax;
+    if ((threadIdx.x & 31) == 0 && cm > 0.0)
+      atomicMax((unsigned long long*)cfl, (unsigned long long)__double_as_longlong(cm));
+  }
+  cl.sync();  // every block's product spectra are in place; nobody reads res1 any more
+
+  // ---- phase 3: forward z transforms of this block's m columns, three fields
+  V* A3 = A;
+  V* B3 = A + 3 * MC * LDZ;
+  for (int e = threadIdx.x; e < 3 * MC * NZ; e += blockDim.x) {
+    const int z = e % NZ, col = e / NZ, f = col / MC, mc = col % MC;
+    V v = V{0, 0};
+    if (mc < mcn) {
+      const V* src = cl.map_shared_rank(ZNl, z / ZR);
+      v = src[(f * ZR + z % ZR) * M + m0 + mc];
+    }
+    A3[col * LDZ + z] = v;
+  }
+  cl.sync();  // every remote read is done before any block moves on or exits
+  const V* res3 = block_fft_c<NZ, -1>(A3, B3, 3 * MC, LDZ, tz);
+  const T sc = (T)d.inv_grid;
+  for (int e = threadIdx.x; e < mcn * nk; e += blockDim.x) {
+    const int kk = e % nk, mc = e / nk, m = m0 + mc;
+    const int k = kk - (K - 1);
+    const int zp = k < 0 ? k + NZ : k;
+    const V r_ = res3[(0 * MC + mc) * LDZ + zp], t_ = res3[(1 * MC + mc) * LDZ + zp];
+    const V z_ = res3[(2 * MC + mc) * LDZ + zp];
+    double2 np = double2{(double)(sc * (r_.x - t_.y)), (double)(sc * (r_.y + t_.x))};  // N+ = N_r + i N_theta
+    double2 nm = double2{(double)(sc * (r_.x + t_.y)), (double)(sc * (r_.y - t_.x))};  // N- = N_r - i N_theta
+    double2 nz2 = double2{(double)(sc * z_.x), (double)(sc * z_.y)};
+    if (k == 0 && m == 0) nz2.x += 4.0 / Re;  // base driving force (laminar balance)
+    const long o = ((long)m * N + n) * nk + kk;
+    double2 ap = double2{0.0, 0.0}, am = ap, az = ap;
+    if (d.forcing) {  // constant body force (shared by the trajectories of a group)
+      ap = d.forcing[o];
+      am = d.forcing[fs + o];
+      az = d.forcing[2 * fs + o];
+    }
+    if (Nlin) {  // terms linear in the perturbation, evaluated in FP64
+      const double2 a = Nlin[o], b = Nlin[fs + o], c = Nlin[2 * fs + o];
+      ap = double2{ap.x + a.x, ap.y + a.y};
+      am = double2{am.x + b.x, am.y + b.y};
+      az = double2{az.x + c.x, az.y + c.y};
+    }
+    if (Nlin || d.forcing) {
+      np.x += ap.x;
+      np.y += ap.y;
+      nm.x += am.x;
+      nm.y += am.y;
+      nz2.x += az.x;
+      nz2.y += az.y;
+    }
+    Nout[o] = np;
+    Nout[fs + o] = nm;
+    Nout[2 * fs + o] = nz2;
+  }
+}
+
+// Cluster size for a fused launch of this shape (0: the shape takes the
+// three-kernel path): transform lengths with a compiled plan up to 96;
+// d.fused = 2, 4 or 8 forces the cluster size, 1 chooses it (eight blocks
+// per plane when the grid would otherwise leave SMs idle, else four).
+int fused32_cluster(const Dims& d) {
+  auto ok = [](int n) { return n == 48 || n == 72 || n == 96; };
+  if (!d.fused || !ok(d.nz) || !ok(d.nth)) return 0;
+  int dev = 0, sms = 152, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int C = d.fused >= 2 ? d.fused : ((long)4 * d.N * d.B < 2L * sms ? 8 : 4);
+  if (fused32_smem(d, C) > (size_t)optin) return 0;
+  if ((long)fused_mc(d.M, C) * (d.nz + 1) < d.nth) return 0;  // phase 2 needs one row's buffers
+  return C;
+}
+
+template <int NZ, int NTH>
+void launch_fused_len(const Dims& d, const DevSetup& s, int C, const float2* W6, const double2* Nlin,
+                      double2* Nout, cudaStream_t st) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(C * d.N, 1, d.B);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = fused32_smem(d, C);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_nl_fused32<NZ, NTH>, d, C, (const float2*)s.tw_z32, (const float2*)s.tw_th32, W6,
+                     Nlin, Nout);
+}
+
+template <class F>
+void with_fused_lengths(int nz, int nth, F&& f) {
+  auto inner = [&](auto z) {
+    switch (nth) {
+      case 48: f(z, std::integral_constant<int, 48>{}); break;
+      case 72: f(z, std::integral_constant<int, 72>{}); break;
+      default: f(z, std::integral_constant<int, 96>{}); break;
+    }
+  };
+  switch (nz) {
+    case 48: inner(std::integral_constant<int, 48>{}); break;
+    case 72: inner(std::integral_constant<int, 72>{}); break;
+    default: inner(std::integral_constant<int, 96>{}); break;
+  }
+}
+
+bool launch_nl_fused32(const Dims& d, const DevSetup& s, const float2* W6, const double2* Nlin, double2* Nout,
+                       cudaStream_t st) {
+  const int C = fused32_cluster(d);
+  if (!C) return false;
+  with_fused_lengths(d.nz, d.nth, [&](auto z, auto t) {
+    launch_fused_len<decltype(z)::value, decltype(t)::value>(d, s, C, W6, Nlin, Nout, st);
+  });
+  return true;
+}
+
 // ------------------------------------------------------------------ linear solve (A5-A7)
 struct SolveDev {
   const double* d1;
@@ -636,12 +910,17 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // the influence step and the write-out read them from shared memory.
 // The host stages only where that costs no resident blocks (see
 // launch_solve); the launch gives the staged size then, the base size else.
+// Rows of P: the pressure, later the influence step's scratch (12 complex per mode).
+__host__ __device__ constexpr int solve_prows(int N) { return N > 12 ? N : 12; }
 __host__ __device__ constexpr size_t solve_smem_base(int N, int T) {
-  return (size_t)(5 * N * T + 4 * T) * 16 + (size_t)6 * N * T * 8 + (size_t)(2 * N * 9 + 3 * N + 2) * 8;
+  return (size_t)(N * T + solve_prows(N) * T + 4 * T) * 16 + (size_t)6 * N * T * 8 +
+         (size_t)(2 * N * 9 + 3 * N + 2) * 8 + 16;
 }
 __host__ __device__ constexpr size_t solve_smem_staged(int N, int T) {
-  return solve_smem_base(N, T) + 16 + (size_t)96 * N * T;
+  return solve_smem_base(N, T) + (size_t)96 * N * T;
 }
+// The FP32 copy of u_theta for the mixed-precision curl of the solved state.
+__host__ __device__ constexpr size_t solve_smem_curl32(int N, int T) { return (size_t)8 * N * T; }
 __host__ __device__ constexpr bool solve_stage_fits(int N, int T) { return solve_smem_staged(N, T) <= 100 * 1024; }
 
 // Banded substitution on one real right-hand side held in shared memory at
@@ -759,16 +1038,18 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
   constexpr int NT = 6 * T;   // velocity right-hand sides (chains)
   constexpr int NB = 24 * T;  // threads: 4 lanes per velocity chain
   constexpr int NP = 8 * T;   // threads of the pressure substitution (2T chains x 4 lanes)
-  double2* NE = (double2*)smraw;        // [3][N][T]  N_eff
-  double2* S = NE + 3 * N * T;          // [N][T]     N+ + N-, later d_r p
-  double2* P = S + N * T;               // [N][T]     pressure
-  double2* coef = P + N * T;            // [T][4]     influence coefficients
-  double* X = (double*)(coef + 4 * T);  // [N][6T]    velocity chains
-  double* W1 = X + N * NT;              // [2][N][9]  first-derivative stencils
-  double* RI = W1 + 2 * N * 9;          // [N]        1/r
-  double* RIp = RI + N;                 // [N]        (1 + m~) / (2r)
-  double* RIm = RIp + N;                // [N]        (1 - m~) / (2r)
-  double* misc = RIm + N;               // [2]        flux correction
+  // X holds N_eff first (chain layout: field f, mode mi, re/im part), then
+  // the velocity right-hand sides built on it in place, then the chains'
+  // solutions; S and P are reused by the influence step and the curl.
+  double2* S = (double2*)smraw;                // [N][T]     N+ + N- (later u_j near the wall, u_r)
+  double2* P = S + N * T;                      // [N][T]     pressure (later influence scratch, u_theta)
+  double2* coef = P + solve_prows(N) * T;      // [T][4]     influence coefficients
+  double* X = (double*)(coef + 4 * T);         // [N][6T]    N_eff -> right-hand sides -> velocity chains
+  double* W1 = X + N * NT;                     // [2][N][9]  first-derivative stencils
+  double* RI = W1 + 2 * N * 9;                 // [N]        1/r
+  double* RIp = RI + N;                        // [N]        (1 + m~) / (2r)
+  double* RIm = RIp + N;                       // [N]        (1 - m~) / (2r)
+  double* misc = RIm + N;                      // [2]        flux correction
   const bool stage = s.stage;
   // u_j near the wall for the influence step, when not staged: in S (free
   // after the pressure right-hand side) if it holds [T][19], else from global
@@ -776,6 +1057,11 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
   const bool uw_in_s = !stage && N >= 19;
   double2* UJ = (double2*)(((size_t)(misc + 2) + 15) & ~(size_t)15);  // [3][N][T] u_j (stage)
   double* BS = (double*)(UJ + 3 * N * T);                             // [T][6N]   responses (stage)
+  float2* UT32 = stage ? (float2*)(BS + 6 * N * T) : (float2*)UJ;     // [N][T] FP32 u_theta (curl 2)
+  // N_eff of field f, row i, mode mi as a complex pair in X's chain layout
+  auto ne_at = [&](int f, int i, int mi) -> double2& {
+    return *(double2*)(X + (long)i * NT + ((f * T + mi) << 1));
+  };
   const int m = blockIdx.y, kk0 = blockIdx.x * T, tid = threadIdx.x;
   const int mt = d.m_p * m, ps = mt & 1, pv = ps ^ 1;
   s.d1 = bofs(s.d1, d.ps);
@@ -848,12 +1134,13 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
       v.x += a.wb * w.x;
       v.y += a.wb * w.y;
     }
-    NE[(f * N + i) * T + mi] = v;
+    ne_at(f, i, mi) = v;
   }
   cp_async_wait<0>();
   __syncthreads();
   for (int e = tid; e < N * T; e += NB) {
-    const double2 p = NE[e], q = NE[N * T + e];
+    const int mi = e % T, i = e / T;
+    const double2 p = ne_at(0, i, mi), q = ne_at(1, i, mi);
     S[e] = double2{p.x + q.x, p.y + q.y};
   }
   __syncthreads();
@@ -876,7 +1163,7 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
         ax = fma(w, sv.x, ax);
         ay = fma(w, sv.y, ay);
       }
-      const double2 np = NE[i * T + mi_t], nm = NE[(N + i) * T + mi_t], nz = NE[(2 * N + i) * T + mi_t];
+      const double2 np = ne_at(0, i, mi_t), nm = ne_at(1, i, mi_t), nz = ne_at(2, i, mi_t);
       b.x = fma(0.5, ax, fma(RIp[i], np.x, fma(RIm[i], nm.x, -ak_t * nz.y)));
       b.y = fma(0.5, ay, fma(RIp[i], np.y, fma(RIm[i], nm.y, ak_t * nz.x)));
     }
@@ -899,8 +1186,7 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
       if (i < N - 1) {
         const double2 u = uj(f, i, mi);
         if (stage && part == 0) UJ[(f * N + i) * T + mi] = u;
-        const double2 ne = NE[(f * N + i) * T + mi];
-        b = ci * (part ? u.y : u.x) + (part ? ne.y : ne.x);
+        b = fma(ci, part ? u.y : u.x, X[i * NT + c]);  // X held N_eff of this chain's element
       }
       X[i * NT + c] = b;
     }
@@ -973,10 +1259,10 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
   //      its active lanes, so the work is spread: step 1, one thread per
   //      (mode, tap) of the wall divergence stencil and per (mode, field) of
   //      u(1); step 2, one thread per (mode, row of A^{-1}, re/im part), the
-  //      tap sum reduced over the mode's 8 lanes.  (NE is free by now.)
+  //      tap sum reduced over the mode's 8 lanes.  (P is free by now.)
   {
-    double2* Dt = NE;          // [T][9] w_q (u+ + u-)(N-9+q)
-    double2* Gw = NE + 9 * T;  // [T][3] u+-, u_z at the wall
+    double2* Dt = P;          // [T][9] w_q (u+ + u-)(N-9+q)
+    double2* Gw = P + 9 * T;  // [T][3] u+-, u_z at the wall
     auto uv = [&](int ff, int i, int mj) {  // rows N-9.. of u+-, row N-1 of u_z
       const int c = (ff * T + mj) << 1;
       const double2 w = stage     ? UJ[(ff * N + i) * T + mj]
@@ -1080,12 +1366,12 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
   }
 
   // ---- the curl of the new state (A1) for the next nonlinear evaluation, from
-  //      the block's radial columns (NE is free: u_r, u_theta, FP32 u_theta)
+  //      the block's radial columns (S and P are free: u_r, u_theta; the FP32
+  //      u_theta of the mixed-precision curl sits in the tail of shared memory)
   if (a.curl) {
     __syncthreads();
-    double2* UR = NE;
-    double2* UT = NE + N * T;
-    float2* UT32 = (float2*)(NE + 2 * N * T);
+    double2* UR = S;
+    double2* UT = P;
     const int c0 = mi_t << 1, c1 = (T + mi_t) << 1, c2 = (2 * T + mi_t) << 1;
     for (int i = tid / T; i < N; i += NB / T) {
       const double* xr = X + i * NT;
@@ -1093,7 +1379,7 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
       const double2 ut = double2{0.5 * (up.y - um.y), -0.5 * (up.x - um.x)};
       UR[i * T + mi_t] = double2{0.5 * (up.x + um.x), 0.5 * (up.y + um.y)};
       UT[i * T + mi_t] = ut;
-      UT32[i * T + mi_t] = float2{(float)ut.x, (float)ut.y};
+      if (a.curl == 2) UT32[i * T + mi_t] = float2{(float)ut.x, (float)ut.y};  // (allocated for curl 2 only)
     }
     __syncthreads();
     const int kk = kk0 + mi_t;
@@ -1116,13 +1402,15 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
 static size_t solve_smem(int N, int T);
 
 // Tile of T modes: 4 keeps every warp of the sequential phases full (8
-// right-hand sides per warp) with the most blocks; larger tiles only when
-// there are many modes per SM.
+// right-hand sides per warp) with the most blocks; 8 when there are many
+// modes per SM and two blocks of the tile still fit on an SM (so that one
+// block's sequential phases overlap another's).  Measured on the ensemble's
+// groups, 16 was never faster than 8 (N=32: 827 vs 767 us per launch); the
+// autotuner and option "tile" can still choose it.
 static int solve_tile(const Dims& d) {
   if (d.tile == 4 || d.tile == 8 || d.tile == 16) return d.tile;
   const long modes = (long)d.nk * d.M * d.B;
-  if (modes / 16 >= 8 * 152 && solve_smem(d.N, 16) <= 200 * 1024) return 16;
-  if (modes / 8 >= 4 * 152 && solve_smem(d.N, 8) <= 200 * 1024) return 8;
+  if (modes / 8 >= 4 * 152 && solve_smem(d.N, 8) <= 110 * 1024) return 8;
   return 4;
 }
 
@@ -1207,6 +1495,11 @@ bool prepare_kernel_attrs(const Dims& d) {
   ok = ok && cudaFuncSetAttribute(k_solve<16>, a, optin) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(k_solve<8>, a, optin) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(k_solve<4>, a, optin) == cudaSuccess;
+  auto fusable = [](int n) { return n == 48 || n == 72 || n == 96; };
+  if (fusable(d.nz) && fusable(d.nth))  // (the option or the autotuner may switch the fused launch on later)
+    with_fused_lengths(d.nz, d.nth, [&](auto z, auto t) {
+      ok = ok && cudaFuncSetAttribute(k_nl_fused32<decltype(z)::value, decltype(t)::value>, a, optin) == cudaSuccess;
+    });
   return ok;
 }
 
@@ -1243,7 +1536,8 @@ void launch_solve(const Dims& d, const DevSetup& s, const SolveArgs& a, int nJ, 
   dim3 g((d.nk + T - 1) / T, d.M, d.B);
   const bool stage = solve_use_stage(d, T, (long)g.x * g.y * g.z);
   SolveDev sd{s.d1, s.rinv, s.wq, s.hop, s.luH, s.luP, s.basis, s.ainv, s.G, s.prm, nJ, stage ? 1 : 0, s.d1f, s.r};
-  const size_t sm = stage ? solve_smem_staged(d.N, T) : solve_smem_base(d.N, T);
+  const size_t sm = (stage ? solve_smem_staged(d.N, T) : solve_smem_base(d.N, T)) +
+                    (a.curl == 2 ? solve_smem_curl32(d.N, T) : 0);
   if (T == 16) launch_step_kernel(d, k_solve<16>, g, dim3(24 * 16), sm, st, d, sd, a);
   else if (T == 8) launch_step_kernel(d, k_solve<8>, g, dim3(24 * 8), sm, st, d, sd, a);
   else launch_step_kernel(d, k_solve<4>, g, dim3(24 * 4), sm, st, d, sd, a);
