@@ -130,14 +130,25 @@ int opf_nonlinear(opf_t* h, const double* coeffs, double* out);
  *                both forms and keeps the faster.  Results are identical.
  *                Reads back the cluster size in use (0: three launches).
  *   "timed_kernel" (with "timing" 2): 5 = the fused transforms.
- *   "pdl":       1 = launch the kernels of a step with programmatic dependent
+ *   "pdl":       launch the kernels of a step with programmatic dependent
  *                launch, so that each kernel's launch and read-only prologue
- *                overlap the end of its predecessor (default), 0 = plain
- *                launches.  Results do not depend on it.
+ *                overlap the end of its predecessor: 0 = plain launches
+ *                (default; measured faster), 1 = each kernel signals its
+ *                successor at the top of each block, 2 = before each block's
+ *                final store phase.  Results do not depend on it.
  *   "tile":      modes per block of the solve: 0 = chosen from the grid size
  *                (default), 4, 8 or 16 (OPF_EINVAL if that block's shared
  *                memory does not fit); reads back the value set or the one the
  *                autotuner chose.  Results do not depend on it.
+ *   "spike":     1 = the split solve with 4-mode tiles: each banded system
+ *                (section 2.2) is substituted as two halves at once, joined by an
+ *                8 x 8 interface system and rank-4 spike corrections (the
+ *                factors are built at creation when N is even, N >= 26 and the
+ *                grid is at most three 4-mode blocks per SM; elsewhere setting
+ *                it is a no-op and it reads back 0).  Default: on where the
+ *                grid is at most one block per SM.  It agrees with the
+ *                single-chain solve to round-off (not bit for bit); the
+ *                autotuner keeps whichever is set.
  *   "rot_x", "rot_y", "rot_z": frame rotation Omega (Cartesian components, pipe
  *                axis z; default 0): the Coriolis force -2 Omega x u joins the
  *                nonlinear term (section 3.1's rotating pipe; a transverse axis

@@ -82,6 +82,9 @@ struct Group {
   size_t o_prm = 0, o_rinv = 0, o_d1 = 0, o_wq = 0, o_hop = 0, o_luH = 0, o_luP = 0;
   size_t o_basis = 0, o_ainv = 0, o_G = 0, o_twz = 0, o_twt = 0, o_twz32 = 0, o_twt32 = 0;
   size_t o_r = 0, o_d1f = 0;
+  size_t o_luH2 = 0, o_luP2 = 0, o_spkH = 0, o_spkP = 0, o_rH = 0, o_rP = 0;
+  bool spike_built = false;  // split factors built (decided once, at creation)
+  bool spike_default = false;  // the split solve is on unless the option says otherwise
 
   template <typename P>
   P* at(P* p, int b) const {
@@ -108,6 +111,14 @@ struct Group {
     s.tw_th32 = sh(s.tw_th32);
     s.r = sh(s.r);
     s.d1f = sh(s.d1f);
+    if (spike_built) {
+      s.luH2 = sh(s.luH2);
+      s.luP2 = sh(s.luP2);
+      s.spkH = sh(s.spkH);
+      s.spkP = sh(s.spkP);
+      s.rH = sh(s.rH);
+      s.rP = sh(s.rP);
+    }
     return s;
   }
   // launch dimensions of trajectory b alone (pointers offset on the host)
@@ -162,6 +173,7 @@ int group_fill_setups(Group* g, bool first) {
     s.dt = dt[b];
     s.c = 0.5;
     s.r_user = g->mesh;
+    s.spike = g->spike_built;
     ok[b] = opf::build_setup(&s, &errs[b]) ? 1 : 0;
   };
   const int nthreads = std::max(1, std::min<int>(nsetup, (int)std::thread::hardware_concurrency()));
@@ -199,6 +211,12 @@ int group_fill_setups(Group* g, bool first) {
   g->o_twt32 = pl.add(d.nth * sizeof(float2));
   g->o_r = pl.add(s0.r.size() * 8);
   g->o_d1f = pl.add((s0.d1.size() + s0.rinv.size()) * sizeof(float));
+  g->o_luH2 = pl.add(s0.luH2.size() * 8);
+  g->o_luP2 = pl.add(s0.luP2.size() * 8);
+  g->o_spkH = pl.add(s0.spkH.size() * 8);
+  g->o_spkP = pl.add(s0.spkP.size() * 8);
+  g->o_rH = pl.add(s0.rH.size() * 8);
+  g->o_rP = pl.add(s0.rP.size() * 8);
   if (first) {
     g->pstride = pl.off;
     if (cudaMalloc((void**)&g->parena, g->pstride * nsetup) != cudaSuccess)
@@ -242,6 +260,12 @@ int group_fill_setups(Group* g, bool first) {
     std::vector<float> d1f(s.d1.begin(), s.d1.end());  // FP32 stencils, then FP32 1/r
     d1f.insert(d1f.end(), s.rinv.begin(), s.rinv.end());
     put(g->o_d1f, d1f.data(), d1f.size() * sizeof(float));
+    put(g->o_luH2, s.luH2.data(), s.luH2.size() * 8);
+    put(g->o_luP2, s.luP2.data(), s.luP2.size() * 8);
+    put(g->o_spkH, s.spkH.data(), s.spkH.size() * 8);
+    put(g->o_spkP, s.spkP.data(), s.spkP.size() * 8);
+    put(g->o_rH, s.rH.data(), s.rH.size() * 8);
+    put(g->o_rP, s.rP.data(), s.rP.size() * 8);
     CU(cudaMemcpy(g->parena + (size_t)b * g->pstride, host.data(), g->pstride, cudaMemcpyHostToDevice));
   }
   return OPF_OK;
@@ -282,6 +306,15 @@ int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, con
   for (int b = 1; b < B; ++b)
     if (Re[b] != Re[0] || dt[b] != dt[0]) g->shared_setup = false;
   g->nJ = 0;
+  {  // split factors are built for grids of up to three 4-mode blocks per SM;
+     // the split solve is the default where there is at most one (the
+     // substitution chains are then the critical path, not the FP64 pipe)
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long blocks = (long)((d.nk + 3) / 4) * M * B;
+    g->spike_built = N % 2 == 0 && N >= 26 && blocks <= 3L * sms;
+    g->spike_default = g->spike_built && blocks <= sms;
+  }
   int rc = group_fill_setups(g, true);
   if (rc) return rc;
   char* P = g->parena;
@@ -301,6 +334,15 @@ int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, con
   g->ds.tw_th32 = (float2*)(P + g->o_twt32);
   g->ds.r = (double*)(P + g->o_r);
   g->ds.d1f = (float*)(P + g->o_d1f);
+  if (g->spike_built) {
+    g->ds.luH2 = (double*)(P + g->o_luH2);
+    g->ds.luP2 = (double*)(P + g->o_luP2);
+    g->ds.spkH = (double*)(P + g->o_spkH);
+    g->ds.spkP = (double*)(P + g->o_spkP);
+    g->ds.rH = (double*)(P + g->o_rH);
+    g->ds.rP = (double*)(P + g->o_rP);
+  }
+  d.spike = g->spike_default ? 1 : 0;
   d.ps = g->shared_setup ? 0 : (long)g->pstride;
   d.prm = g->ds.prm;
 
@@ -633,9 +675,13 @@ int tune_group(Runner* r, Group* g) {
     }
     d.fused = pick;
   }
+  // the split solve (4-mode tiles only) changes the rounding order of the
+  // substitution, so the tuner keeps it and its tile: launch shapes alone are
+  // tuned, never the arithmetic
   best = 1e30f;
-  pick = 0;
+  pick = d.spike ? 4 : 0;
   for (int T : {4, 8, 16}) {
+    if (d.spike) break;
     if (opf::solve_smem_bytes(d.N, T) > (size_t)optin) continue;
     d.tile = T;
     opf::SolveArgs a{g->U, g->Nj, nullptr, 1.0, 0.0, g->U1, g->beta_p};
@@ -749,6 +795,9 @@ int runner_option(Runner* r, const char* key, double v) {
   } else if (!strcmp(key, "autotune")) {
     if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "autotune: 0 or 1");
     r->autotune = (int)v;
+  } else if (!strcmp(key, "spike")) {
+    if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "spike: 0 or 1");
+    for (Group* g : r->groups) g->d.spike = (v != 0.0 && g->spike_built) ? 1 : 0;
   } else if (!strcmp(key, "fused")) {
     if (v != 0.0 && v != 1.0 && v != 2.0 && v != 4.0 && v != 8.0)
       return fail(OPF_EINVAL, "fused: 0 (off), 1 (cluster size chosen), 2, 4 or 8 (cluster size)");
@@ -784,6 +833,7 @@ int runner_get_option(Runner* r, const char* key, double* v) {
   else if (!strcmp(key, "tile")) *v = r->groups.empty() ? 0 : r->groups[0]->d.tile;
   else if (!strcmp(key, "pdl")) *v = r->groups.empty() ? 0 : r->groups[0]->d.pdl;
   else if (!strcmp(key, "fused")) *v = r->groups.empty() ? 0 : opf::fused32_cluster(r->groups[0]->d);
+  else if (!strcmp(key, "spike")) *v = r->groups.empty() ? 0 : r->groups[0]->d.spike;
   else if (!strcmp(key, "mcz")) *v = r->groups.empty() ? 0 : r->groups[0]->d.mcz;
   else if (!strcmp(key, "mca")) *v = r->groups.empty() ? 0 : r->groups[0]->d.mca;
   else if (!strcmp(key, "zc")) *v = r->groups.empty() ? 0 : r->groups[0]->d.zc;

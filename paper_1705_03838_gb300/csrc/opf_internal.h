@@ -44,6 +44,11 @@ struct Setup {
   std::vector<double> ainv;   // [M][2K-1][16][2] inverse influence matrices
   std::vector<double> G;      // fixed-flux response of the (0,0) axial mode
   double flux_G = 0;          // 2 pi sum wq G
+  // two-partition (split) factors of the same operators, built when spike is
+  // set: per operator N rows of 13 slots (top block, then bottom block), N
+  // rows of 4 spike entries, 64 entries of the interface inverse
+  bool spike = false;
+  std::vector<double> luH2, luP2, spkH, spkP, rH, rP;
 };
 
 bool build_setup(Setup* s, std::string* err);
@@ -69,6 +74,8 @@ struct DevSetup {
   float2* tw_th32 = nullptr;
   double* r = nullptr;    // radial points (null where the split curl is not used)
   float* d1f = nullptr;   // d1 in FP32, then 1/r in FP32 ([2][N][9] + [N])
+  // two-partition (split) solve data (Setup::luH2 ...; null unless built)
+  double *luH2 = nullptr, *luP2 = nullptr, *spkH = nullptr, *spkP = nullptr, *rH = nullptr, *rP = nullptr;
 };
 
 // Spectral fields are stored [field][m][n][kk] (kk = k + K - 1 fastest).
@@ -81,6 +88,7 @@ struct Dims {
   int mcz, mca;   // m columns per block: z synthesis, z analysis
   int zc;         // z rows per block in the theta/product kernel
   int tile = 0;   // modes per block in the solve (0: heuristic)
+  int spike = 0;  // solve the banded systems in two halves at once (split factors built)
   int fused = 0;  // mixed precision: the three transform kernels as one cluster launch where it
                   // fits (0 off, 1 cluster size chosen, 2/4/8 that cluster size)
   int pdl = 0;    // programmatic dependent launch of the step kernels: 0 off, 1 trigger at

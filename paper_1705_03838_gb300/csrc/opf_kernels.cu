@@ -883,6 +883,13 @@ struct SolveDev {
   int stage;  // u_j and the influence responses staged in shared memory
   const float* d1f;
   const double* r;
+  // split solve: both blocks' factors, spikes, interface inverses
+  const double* luH2;
+  const double* luP2;
+  const double* spkH;
+  const double* spkP;
+  const double* rH;
+  const double* rP;
 };
 
 // Bulk L2 prefetch by the TMA unit: p 16-byte aligned, bytes a multiple of 16.
@@ -912,12 +919,13 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // launch_solve); the launch gives the staged size then, the base size else.
 // Rows of P: the pressure, later the influence step's scratch (12 complex per mode).
 __host__ __device__ constexpr int solve_prows(int N) { return N > 12 ? N : 12; }
-__host__ __device__ constexpr size_t solve_smem_base(int N, int T) {
+// sp: the split solve's interface values (6T chains x 8 doubles) after misc.
+__host__ __device__ constexpr size_t solve_smem_base(int N, int T, bool sp = false) {
   return (size_t)(N * T + solve_prows(N) * T + 4 * T) * 16 + (size_t)6 * N * T * 8 +
-         (size_t)(2 * N * 9 + 3 * N + 2) * 8 + 16;
+         (size_t)(2 * N * 9 + 3 * N + 2) * 8 + 16 + (sp ? (size_t)48 * T * 8 : 0);
 }
-__host__ __device__ constexpr size_t solve_smem_staged(int N, int T) {
-  return solve_smem_base(N, T) + (size_t)96 * N * T;
+__host__ __device__ constexpr size_t solve_smem_staged(int N, int T, bool sp = false) {
+  return solve_smem_base(N, T, sp) + (size_t)96 * N * T;
 }
 // The FP32 copy of u_theta for the mixed-precision curl of the solved state.
 __host__ __device__ constexpr size_t solve_smem_curl32(int N, int T) { return (size_t)8 * N * T; }
@@ -1026,18 +1034,55 @@ __device__ __forceinline__ void band_solve4(const double* __restrict__ L, double
 //
 // Resident blocks per SM the register budget must allow (the shared-memory
 // footprints of the tiles allow about as many at moderate N).
-template <int T>
+template <int T, bool SP>
 constexpr int solve_min_blocks() {
-  return T == 4 ? 4 : (T == 8 ? 3 : 2);
+  return SP ? 3 : (T == 4 ? 4 : (T == 8 ? 3 : 2));
 }
 
-template <int T>
-__global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d, SolveDev s, SolveArgs a) {
+// Interface and correction of the split solve for nch chains held in x
+// (chain c's column at x + col(c), rows at stride st) after both halves were
+// substituted: z = R (y_T[k-4:k], y_B[0:4]) per chain, then every row
+// x_i -= S_i . z_B (top half) or S_i . z_T (bottom half), k = N/2.  spk: per
+// operator N rows of 4; R: per operator 8 x 8.  Ends with a block barrier.
+template <int NB, typename OpOf>
+__device__ __forceinline__ void spike_fix(int tid, int N, int nch, int st, double* x, const double* __restrict__ spk,
+                                          const double* __restrict__ R, double* Zs, OpOf op_of) {
+  const int kh = N >> 1;
+  for (int e = tid; e < nch * 8; e += NB) {
+    const int c = e >> 3, q = e & 7;
+    const double* Rc = R + (long)op_of(c) * 64 + q * 8;
+    const double* xc = x + c;
+    double z = 0.0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) z = fma(Rc[b], xc[(kh - 4 + b) * st], z);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) z = fma(Rc[4 + b], xc[(kh + b) * st], z);
+    Zs[e] = z;
+  }
+  __syncthreads();
+  for (int e = tid; e < nch * N; e += NB) {
+    const int c = e % nch, i = e / nch;
+    const double* S = spk + ((long)op_of(c) * N + i) * 4;
+    const double* z = Zs + c * 8 + (i < kh ? 4 : 0);
+    double v = x[i * st + c];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v = fma(-S[q], z[q], v);
+    x[i * st + c] = v;
+  }
+  __syncthreads();
+}
+
+// SP: the split (two-partition) solve for the latency-bound grids -- each
+// chain's substitution runs on 8 lanes, the two halves of its rows at once
+// (twice the threads; the other phases use them too).
+template <int T, bool SP = false>
+__global__ void __launch_bounds__((SP ? 48 : 24) * T, solve_min_blocks<T, SP>())
+    k_solve(Dims d, SolveDev s, SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int N = d.N, nk = d.nk, M = d.M, K = d.K;
-  constexpr int NT = 6 * T;   // velocity right-hand sides (chains)
-  constexpr int NB = 24 * T;  // threads: 4 lanes per velocity chain
-  constexpr int NP = 8 * T;   // threads of the pressure substitution (2T chains x 4 lanes)
+  constexpr int NT = 6 * T;                // velocity right-hand sides (chains)
+  constexpr int NB = (SP ? 48 : 24) * T;   // threads: 4 (SP: 8) lanes per velocity chain
+  constexpr int NP = (SP ? 16 : 8) * T;    // threads of the pressure substitution (2T chains)
   // X holds N_eff first (chain layout: field f, mode mi, re/im part), then
   // the velocity right-hand sides built on it in place, then the chains'
   // solutions; S and P are reused by the influence step and the curl.
@@ -1055,7 +1100,8 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
   // after the pressure right-hand side) if it holds [T][19], else from global
   double2* UW = S;
   const bool uw_in_s = !stage && N >= 19;
-  double2* UJ = (double2*)(((size_t)(misc + 2) + 15) & ~(size_t)15);  // [3][N][T] u_j (stage)
+  double* Zs = misc + 2;                       // [6T][8]    split-solve interface values (SP)
+  double2* UJ = (double2*)(((size_t)(Zs + (SP ? 48 * T : 0)) + 15) & ~(size_t)15);  // [3][N][T] u_j (stage)
   double* BS = (double*)(UJ + 3 * N * T);                             // [T][6N]   responses (stage)
   float2* UT32 = stage ? (float2*)(BS + 6 * N * T) : (float2*)UJ;     // [N][T] FP32 u_theta (curl 2)
   // N_eff of field f, row i, mode mi as a complex pair in X's chain layout
@@ -1076,6 +1122,14 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
   s.prm = bofs(s.prm, d.ps);
   s.d1f = bofs(s.d1f, d.ps);
   s.r = bofs(s.r, d.ps);
+  if constexpr (SP) {
+    s.luH2 = bofs(s.luH2, d.ps);
+    s.luP2 = bofs(s.luP2, d.ps);
+    s.spkH = bofs(s.spkH, d.ps);
+    s.spkP = bofs(s.spkP, d.ps);
+    s.rH = bofs(s.rH, d.ps);
+    s.rP = bofs(s.rP, d.ps);
+  }
   a.W6 = bofs(a.W6, d.ss);
   a.Nlin = bofs(a.Nlin, d.ss);
   a.Uj = bofs(a.Uj, d.ss);
@@ -1106,7 +1160,8 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
       if (!stage) prefetch_l2_bulk(s.basis + (long)(ik * M + m) * 6 * N, 48u * N);
     } else if (!(N & 1)) {
       const long op = which == 0 ? ((ik == 0 && m == 0) ? K * M : ik * M + m) : ik * s.nJ + s.hop[3 * m + which - 1];
-      prefetch_l2_bulk((which == 0 ? s.luP : s.luH) + op * N * kLuSlots, (unsigned)N * kLuSlots * 8u);
+      prefetch_l2_bulk((which == 0 ? (SP ? s.luP2 : s.luP) : (SP ? s.luH2 : s.luH)) + op * N * kLuSlots,
+                       (unsigned)N * kLuSlots * 8u);
     }
   }
 
@@ -1173,10 +1228,16 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
 
   if (tid < NP) {
     // ---- pressure-Poisson solve (provisional dp/dr(1) = 0; (0,0): p(1) = 0)
-    const int j = tid >> 2, part = j & 1, mi = j >> 1;
+    const int j = tid >> (SP ? 3 : 2), part = j & 1, mi = j >> 1;
     const int k = min(kk0 + mi, nk - 1) - (K - 1), ik = abs(k);
     const int op = (ik == 0 && m == 0) ? K * M : ik * M + m;
-    band_solve4(s.luP + (long)op * N * kLuSlots, (double*)P + 2 * mi + part, 2 * T, N);
+    if constexpr (SP) {  // lanes 0-3 of the chain's 8: top half, 4-7: bottom half
+      const int h = (tid >> 2) & 1, kh = N >> 1;
+      band_solve4(s.luP2 + ((long)op * N + h * kh) * kLuSlots, (double*)P + 2 * mi + part + h * kh * 2 * T, 2 * T,
+                  kh);
+    } else {
+      band_solve4(s.luP + (long)op * N * kLuSlots, (double*)P + 2 * mi + part, 2 * T, N);
+    }
   } else {
     // ---- meanwhile: the p-independent part of the velocity right-hand sides
     for (int e = tid - NP; e < N * NT; e += NB - NP) {
@@ -1216,6 +1277,11 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
     }
   }
   __syncthreads();
+  if constexpr (SP)  // the pressure chains' interface and correction
+    spike_fix<NB>(tid, N, 2 * T, 2 * T, (double*)P, s.spkP, s.rP, Zs, [&](int c) {
+      const int ik = abs(min(kk0 + (c >> 1), nk - 1) - (K - 1));
+      return (ik == 0 && m == 0) ? K * M : ik * M + m;
+    });
 
   // ---- d_r p per (mode, row), subtracted at once from the right-hand sides of
   //      the three fields (rows < N-1):
@@ -1244,14 +1310,24 @@ __global__ void __launch_bounds__(24 * T, solve_min_blocks<T>()) k_solve(Dims d,
   __syncthreads();
 
   // ---- implicit viscous solves (1/dt - cL) v = rhs, Dirichlet 0
-  {  // 6T chains x 4 lanes = all threads
-    const int c = tid >> 2;
+  {  // 6T chains x 4 (SP: 8) lanes = all threads
+    const int c = tid >> (SP ? 3 : 2);
     const int mi = (c >> 1) % T, f = (c >> 1) / T;
     const int k = min(kk0 + mi, nk - 1) - (K - 1), ik = abs(k);
     const int op = ik * s.nJ + s.hop[3 * m + f];
-    band_solve4(s.luH + (long)op * N * kLuSlots, X + c, NT, N);
+    if constexpr (SP) {
+      const int h = (tid >> 2) & 1, kh = N >> 1;
+      band_solve4(s.luH2 + ((long)op * N + h * kh) * kLuSlots, X + c + h * kh * NT, NT, kh);
+    } else {
+      band_solve4(s.luH + (long)op * N * kLuSlots, X + c, NT, N);
+    }
   }
   __syncthreads();
+  if constexpr (SP)  // the velocity chains' interface and correction
+    spike_fix<NB>(tid, N, NT, NT, X, s.spkH, s.rH, Zs, [&](int c) {
+      const int ik = abs(min(kk0 + ((c >> 1) % T), nk - 1) - (K - 1));
+      return ik * s.nJ + s.hop[3 * m + (c >> 1) / T];
+    });
 
   // ---- influence matrix on u = v - ((1-c)/c) u_j:
   //      g = (u+(1), u-(1), u_z(1), div u(1)),  a = -A^{-1} g.
@@ -1422,7 +1498,7 @@ static size_t solve_smem(int N, int T) {
 
 // Stage u_j and the responses when the staged block fits and the SM still
 // holds as many blocks as the grid can use (so staging never costs occupancy).
-static bool solve_use_stage(const Dims& d, int T, long blocks) {
+static bool solve_use_stage(const Dims& d, int T, long blocks, bool sp = false) {
   if (!solve_stage_fits(d.N, T)) return false;
   struct SmInfo {
     int sms = 1, smem_sm = 0;
@@ -1438,8 +1514,8 @@ static bool solve_use_stage(const Dims& d, int T, long blocks) {
   }();
   const int sms = info.sms, smem_sm = info.smem_sm;
   const size_t reserve = 1024;  // per-block shared memory the system keeps
-  const long with = (long)(smem_sm / (solve_smem_staged(d.N, T) + reserve));
-  const long without = (long)(smem_sm / (solve_smem_base(d.N, T) + reserve));
+  const long with = (long)(smem_sm / (solve_smem_staged(d.N, T, sp) + reserve));
+  const long without = (long)(smem_sm / (solve_smem_base(d.N, T, sp) + reserve));
   const long need = (blocks + sms - 1) / sms;
   return with >= std::min(need, without);
 }
@@ -1495,6 +1571,7 @@ bool prepare_kernel_attrs(const Dims& d) {
   ok = ok && cudaFuncSetAttribute(k_solve<16>, a, optin) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(k_solve<8>, a, optin) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(k_solve<4>, a, optin) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_solve<4, true>, a, optin) == cudaSuccess;
   auto fusable = [](int n) { return n == 48 || n == 72 || n == 96; };
   if (fusable(d.nz) && fusable(d.nth))  // (the option or the autotuner may switch the fused launch on later)
     with_fused_lengths(d.nz, d.nth, [&](auto z, auto t) {
@@ -1533,13 +1610,16 @@ bool prepare_nonlinear_attrs(const Dims& d) {
 
 void launch_solve(const Dims& d, const DevSetup& s, const SolveArgs& a, int nJ, cudaStream_t st) {
   const int T = solve_tile(d);
+  const bool sp = d.spike && T == 4 && s.luH2;  // the split solve (one-wave grids, factors built)
   dim3 g((d.nk + T - 1) / T, d.M, d.B);
-  const bool stage = solve_use_stage(d, T, (long)g.x * g.y * g.z);
-  SolveDev sd{s.d1, s.rinv, s.wq, s.hop, s.luH, s.luP, s.basis, s.ainv, s.G, s.prm, nJ, stage ? 1 : 0, s.d1f, s.r};
-  const size_t sm = (stage ? solve_smem_staged(d.N, T) : solve_smem_base(d.N, T)) +
+  const bool stage = solve_use_stage(d, T, (long)g.x * g.y * g.z, sp);
+  SolveDev sd{s.d1,  s.rinv, s.wq,   s.hop,  s.luH,  s.luP,  s.basis, s.ainv, s.G,  s.prm,
+              nJ,    stage ? 1 : 0,  s.d1f,  s.r,    s.luH2, s.luP2, s.spkH,  s.spkP, s.rH, s.rP};
+  const size_t sm = (stage ? solve_smem_staged(d.N, T, sp) : solve_smem_base(d.N, T, sp)) +
                     (a.curl == 2 ? solve_smem_curl32(d.N, T) : 0);
   if (T == 16) launch_step_kernel(d, k_solve<16>, g, dim3(24 * 16), sm, st, d, sd, a);
   else if (T == 8) launch_step_kernel(d, k_solve<8>, g, dim3(24 * 8), sm, st, d, sd, a);
+  else if (sp) launch_step_kernel(d, k_solve<4, true>, g, dim3(48 * 4), sm, st, d, sd, a);
   else launch_step_kernel(d, k_solve<4>, g, dim3(24 * 4), sm, st, d, sd, a);
 }
 

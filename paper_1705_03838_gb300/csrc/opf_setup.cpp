@@ -255,6 +255,135 @@ static bool factor(Op* op, double* out, std::string* err, const char* what) {
   return true;
 }
 
+// Two-partition (SPIKE) form of an operator, for the latency-bound solves:
+// rows split at k = N/2 into a top block T and a bottom block B, each
+// factored on its own (13-slot rows, local indices), so the two halves are
+// substituted at the same time.  The blocks couple only through the upper
+// band of T's last four rows (columns k..k+3) and the lower band of B's first
+// four rows (columns k-4..k-1):
+//   x_T = y_T - S_T x_B[0:4],    S_T = T^{-1} H(0:k, k:k+4)      (k x 4)
+//   x_B = y_B - S_B x_T[k-4:k],  S_B = B^{-1} H(k:N, k-4:k)  ((N-k) x 4)
+// with y = the block solves of the right-hand side; the interface values
+// z = (x_T[k-4:k], x_B[0:4]) solve G z = (y_T[k-4:k], y_B[0:4]),
+// G = [I, S_T[k-4:k]; S_B[0:4], I], whose inverse R (8 x 8) is stored.
+// out_lu: N rows of 13 slots (T's rows, then B's); out_spk: N rows of 4
+// (S_T, then S_B); out_r: 64 (R row-major).  Checked against the unfactored
+// matrix on a test right-hand side.
+static bool inv_dense(int n, std::vector<double> a, std::vector<double>* out) {
+  std::vector<double> x((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) x[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int i = c + 1; i < n; ++i)
+      if (std::fabs(a[(size_t)i * n + c]) > std::fabs(a[(size_t)p * n + c])) p = i;
+    if (a[(size_t)p * n + c] == 0.0) return false;
+    for (int j = 0; j < n; ++j) {
+      std::swap(a[(size_t)c * n + j], a[(size_t)p * n + j]);
+      std::swap(x[(size_t)c * n + j], x[(size_t)p * n + j]);
+    }
+    const double inv = 1.0 / a[(size_t)c * n + c];
+    for (int j = 0; j < n; ++j) {
+      a[(size_t)c * n + j] *= inv;
+      x[(size_t)c * n + j] *= inv;
+    }
+    for (int i = 0; i < n; ++i) {
+      if (i == c) continue;
+      const double f = a[(size_t)i * n + c];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) {
+        a[(size_t)i * n + j] -= f * a[(size_t)c * n + j];
+        x[(size_t)i * n + j] -= f * x[(size_t)c * n + j];
+      }
+    }
+  }
+  *out = x;
+  return true;
+}
+
+static bool factor_split(const Op& full, double* out_lu, double* out_spk, double* out_r, std::string* err,
+                         const char* what) {
+  const int N = full.N, k = N / 2, nb = N - k;
+  Op top, bot;
+  top.N = k;
+  top.a.assign((size_t)k * k, 0.0);
+  bot.N = nb;
+  bot.a.assign((size_t)nb * nb, 0.0);
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) top.at(i, j) = full.a[(size_t)i * N + j];
+  for (int i = 0; i < nb; ++i)
+    for (int j = 0; j < nb; ++j) bot.at(i, j) = full.a[(size_t)(k + i) * N + k + j];
+  // the coupling must lie within the four columns / rows the device uses
+  for (int i = 0; i < k; ++i)
+    for (int j = k + 4; j < N; ++j)
+      if (full.a[(size_t)i * N + j] != 0.0) {
+        *err = std::string("split solve: upper coupling wider than 4 in ") + what;
+        return false;
+      }
+  for (int i = k; i < N; ++i)
+    for (int j = 0; j < k - 4; ++j)
+      if (full.a[(size_t)i * N + j] != 0.0) {
+        *err = std::string("split solve: lower coupling wider than 4 in ") + what;
+        return false;
+      }
+  std::string e2;
+  if (!factor(&top, out_lu, err, what) || !factor(&bot, out_lu + (size_t)k * kLuSlots, err, what)) return false;
+  std::vector<double> v(N);
+  for (int c = 0; c < 4; ++c) {
+    for (int i = 0; i < k; ++i) v[i] = full.a[(size_t)i * N + k + c];
+    lu_solve(out_lu, k, v.data());
+    for (int i = 0; i < k; ++i) out_spk[(size_t)i * 4 + c] = v[i];
+    for (int i = 0; i < nb; ++i) v[i] = full.a[(size_t)(k + i) * N + k - 4 + c];
+    lu_solve(out_lu + (size_t)k * kLuSlots, nb, v.data());
+    for (int i = 0; i < nb; ++i) out_spk[(size_t)(k + i) * 4 + c] = v[i];
+  }
+  std::vector<double> G(64, 0.0), R;
+  for (int a = 0; a < 8; ++a) G[(size_t)a * 8 + a] = 1.0;
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 4; ++c) {
+      G[(size_t)a * 8 + 4 + c] = out_spk[(size_t)(k - 4 + a) * 4 + c];  // S_T rows k-4..k-1
+      G[(size_t)(4 + a) * 8 + c] = out_spk[(size_t)(k + a) * 4 + c];    // S_B rows 0..3
+    }
+  if (!inv_dense(8, G, &R)) {
+    *err = std::string("split solve: singular interface in ") + what;
+    return false;
+  }
+  std::copy(R.begin(), R.end(), out_r);
+  // self-check of the whole split solve against the unfactored matrix
+  std::vector<double> b(N), x(N), z(8);
+  for (int i = 0; i < N; ++i) b[i] = std::cos(0.7 * i) + 0.3;
+  x = b;
+  lu_solve(out_lu, k, x.data());
+  lu_solve(out_lu + (size_t)k * kLuSlots, nb, x.data() + k);
+  double y[8];
+  for (int a = 0; a < 4; ++a) y[a] = x[k - 4 + a], y[4 + a] = x[k + a];
+  for (int a = 0; a < 8; ++a) {
+    z[a] = 0.0;
+    for (int c = 0; c < 8; ++c) z[a] += out_r[a * 8 + c] * y[c];
+  }
+  for (int i = 0; i < k; ++i)
+    for (int c = 0; c < 4; ++c) x[i] -= out_spk[(size_t)i * 4 + c] * z[4 + c];
+  for (int i = 0; i < nb; ++i)
+    for (int c = 0; c < 4; ++c) x[k + i] -= out_spk[(size_t)(k + i) * 4 + c] * z[c];
+  double res = 0.0, anorm = 0.0, xnorm = 0.0;
+  for (int i = 0; i < N; ++i) {
+    double acc = 0.0, rs = 0.0;
+    for (int j = 0; j < N; ++j) {
+      acc += full.a[(size_t)i * N + j] * x[j];
+      rs += std::fabs(full.a[(size_t)i * N + j]);
+    }
+    res = std::max(res, std::fabs(acc - b[i]));
+    anorm = std::max(anorm, rs);
+    xnorm = std::max(xnorm, std::fabs(x[i]));
+  }
+  if (!(res <= 1e-12 * anorm * xnorm)) {
+    char buf[200];
+    std::snprintf(buf, sizeof buf, "split solve of %s inaccurate (residual %.3e)", what, res / (anorm * xnorm));
+    *err = buf;
+    return false;
+  }
+  return true;
+}
+
 // Banded LU solve with the 13-slot factor (same arithmetic as the device).
 
 static void d1_apply(const Setup* s, int par, const double* v, double* out) {
@@ -355,6 +484,17 @@ bool build_setup(Setup* s, std::string* err) {
   const size_t opsz = (size_t)N * kLuSlots;
   s->luH.assign((size_t)K * s->nJ * opsz, 0.0);
   s->luP.assign((size_t)(K * M + 1) * opsz, 0.0);
+  if (s->spike && (N % 2 || N < 26)) {
+    *err = "split solve needs an even N >= 26";
+    return false;
+  }
+  const size_t nH = s->spike ? (size_t)K * s->nJ : 0, nP = s->spike ? (size_t)(K * M + 1) : 0;
+  s->luH2.assign(nH * opsz, 0.0);
+  s->luP2.assign(nP * opsz, 0.0);
+  s->spkH.assign(nH * N * 4, 0.0);
+  s->spkP.assign(nP * N * 4, 0.0);
+  s->rH.assign(nH * 64, 0.0);
+  s->rP.assign(nP * 64, 0.0);
   Op op;
   std::vector<double> diag(N);
   char what[96];
@@ -366,7 +506,10 @@ bool build_setup(Setup* s, std::string* err) {
       assemble(s, j & 1, -c * nu, diag, &op);
       wall_dirichlet(&op);
       std::snprintf(what, sizeof what, "Helmholtz |k|=%d |j|=%d", ik, j);
-      if (!factor(&op, &s->luH[((size_t)ik * s->nJ + q) * opsz], err, what)) return false;
+      const size_t o = (size_t)ik * s->nJ + q;
+      if (s->spike && !factor_split(op, &s->luH2[o * opsz], &s->spkH[o * N * 4], &s->rH[o * 64], err, what))
+        return false;
+      if (!factor(&op, &s->luH[o * opsz], err, what)) return false;
     }
     for (int m = 0; m < M; ++m) {  // P = D2 + D1/r - m~^2/r^2 - ak^2, Neumann wall row
       const int mt = mp * m;
@@ -374,12 +517,19 @@ bool build_setup(Setup* s, std::string* err) {
       assemble(s, mt & 1, 1.0, diag, &op);
       if (ik == 0 && m == 0) {  // pure Neumann is singular here: gauge p(1) = 0
         wall_dirichlet(&op);
-        if (!factor(&op, &s->luP[(size_t)K * M * opsz], err, "Poisson (0,0)")) return false;
+        const size_t o = (size_t)K * M;
+        if (s->spike &&
+            !factor_split(op, &s->luP2[o * opsz], &s->spkP[o * N * 4], &s->rP[o * 64], err, "Poisson (0,0)"))
+          return false;
+        if (!factor(&op, &s->luP[o * opsz], err, "Poisson (0,0)")) return false;
         continue;
       }
       wall_neumann(s, mt & 1, &op);
       std::snprintf(what, sizeof what, "Poisson |k|=%d m=%d", ik, m);
-      if (!factor(&op, &s->luP[((size_t)ik * M + m) * opsz], err, what)) return false;
+      const size_t o = (size_t)ik * M + m;
+      if (s->spike && !factor_split(op, &s->luP2[o * opsz], &s->spkP[o * N * 4], &s->rP[o * 64], err, what))
+        return false;
+      if (!factor(&op, &s->luP[o * opsz], err, what)) return false;
     }
   }
 

@@ -48,18 +48,24 @@ def oracle_steps(N, K, M, m_p, alpha, Re, dt, amp, seed, nsteps):
 
 
 # ------------------------------------------------- N = 64 and N = 128 solves
-@pytest.mark.parametrize("N,K,M,tile", [(64, 4, 4, 0), (64, 4, 4, 16), (128, 2, 3, 0), (128, 2, 3, 8)])
-def test_solve_paths_at_n64_and_n128(opf, N, K, M, tile):
-    """5 steps at N = 64 (staged tile 4; unstaged tile 16 as in the ensemble)
-    and N = 128 (unstaged tile 4; tile 8 as in the large workload)."""
+@pytest.mark.parametrize("N,K,M,tile,spike", [(64, 4, 4, 0, 0), (64, 4, 4, 0, 1), (64, 4, 4, 16, 0),
+                                              (128, 2, 3, 0, 0), (128, 2, 3, 0, 1), (128, 2, 3, 8, 0)])
+def test_solve_paths_at_n64_and_n128(opf, N, K, M, tile, spike):
+    """5 steps at N = 64 (staged tile 4, single-chain and split; unstaged tile
+    16 as in the ensemble) and N = 128 (unstaged tile 4, single-chain and
+    split; tile 8 as in the large workload)."""
     alpha, Re, dt = 1.25, 2000.0, 0.005
     U0, ref, beta = oracle_steps(N, K, M, 1, alpha, Re, dt, 0.05, 640 + N, 5)
     h = opf.opf_create(N, K, M, 1, alpha, Re, dt)
     opf.opf_set_option(h, "tile", tile)
+    opf.opf_set_option(h, "spike", spike)
+    assert opf.opf_get_option(h, "spike") == spike
     opf.opf_set_state(h, U0)
     opf.opf_step(h, 5)
     assert rel(opf.opf_get_state(h), ref) < 1e-12
-    assert abs(opf.opf_get_beta(h) - beta) < 1e-14 * Re
+    # beta' divides the flux defect's round-off (~1e-16) by sum(w G) ~ dt / 2,
+    # and beta is Re / 4 times beta' (as in the large-resolution test below)
+    assert abs(opf.opf_get_beta(h) - beta) < 10 * 2.2e-16 / (dt / 2) * Re / 4
     g = opf.opf_wall_residual(h)
     assert g[0] < 1e-14 and g[1] < 1e-9
 
@@ -139,3 +145,49 @@ def test_predictor_solve_at_the_large_resolution_on_sampled_modes(opf):
     # q becomes ~1e-16 / (dt / 2) in beta', i.e. Re / 4 times that in beta
     dt = 2e-5
     assert abs(opf.opf_get_beta(h) - ref[(0, K - 1)][1] * Re / 4.0) < 10 * 2.2e-16 / (dt / 2) * Re / 4
+
+
+# ------------------------------------------------- the split (two-partition) solve
+@pytest.mark.parametrize("N,K,M,m_p,prec", [(48, 32, 24, 2, 1), (32, 16, 16, 1, 0), (26, 4, 5, 1, 0), (40, 6, 6, 3, 1)])
+def test_split_solve_matches_the_plain_solve_and_the_oracle(opf, N, K, M, m_p, prec):
+    """Where one wave of 4-mode blocks covers the grid and N is even, the
+    solve substitutes the two halves of each banded system at once and joins
+    them through an 8 x 8 interface system and rank-4 spikes: the same
+    solution to round-off as the single-chain substitution, and the oracle's
+    (FP64) after 5 steps."""
+    alpha, Re, dt = 1.25, 2000.0, 0.005
+    U0 = inputs.seeded_state(N, K, M, m_p, alpha, 0.05, 330 + N)
+    out = []
+    for spike in (0, 1):
+        h = opf.opf_create(N, K, M, m_p, alpha, Re, dt)
+        opf.opf_set_option(h, "precision", prec)
+        opf.opf_set_option(h, "spike", spike)
+        assert opf.opf_get_option(h, "spike") == spike
+        opf.opf_set_state(h, U0)
+        opf.opf_step(h, 5)
+        out.append(opf.opf_get_state(h))
+        if spike:
+            g = opf.opf_wall_residual(h)
+            assert g[0] < 1e-14 and g[1] < 1e-9
+    assert rel(out[1], out[0]) < 1e-13
+    if prec == 0:
+        ref = Oracle(Params(N, K, M, m_p, alpha, Re, dt)).step(U0, 5)
+        assert rel(out[1], ref) < 1e-12
+
+
+def test_split_solve_defaults(opf):
+    """On by default where the grid is at most one 4-mode block per SM (the
+    small workload); available but off up to three (the medium workload);
+    absent for odd N, N < 26 or larger grids, where setting it is a no-op."""
+    w = inputs.WORKLOADS
+    for name, default, avail in (("small", 1, 1), ("medium", 0, 1)):
+        a = w[name]
+        h = opf.opf_create(a["N"], a["K"], a["M"], a["m_p"], a["alpha"], a["Re"], a["dt"])
+        assert opf.opf_get_option(h, "spike") == default, name
+        opf.opf_set_option(h, "spike", 1)
+        assert opf.opf_get_option(h, "spike") == avail, name
+    for args in ((27, 4, 4, 1), (24, 4, 4, 1), (64, 32, 32, 1)):
+        h = opf.opf_create(*args, 1.25, 2000.0, 0.005)
+        assert opf.opf_get_option(h, "spike") == 0
+        opf.opf_set_option(h, "spike", 1)
+        assert opf.opf_get_option(h, "spike") == 0
