@@ -422,7 +422,6 @@ def run_ensemble(args):
     dom_ms = kt[dom][0] / max(1, kt[dom][1]) * len(set(shapes))  # one launch per shape group per slot
     pk, src = kernel_peak(dom, args.precision)
     ach = flops[dom] / (dom_ms * 1e-3) / 1e12
-    tot = sum(x[0] for x in kt.values())
     line = {
         "metric": "ensemble trajectory-steps/s (256 uneven trajectories, one graph per step)",
         "value": steps_per_s * n,
@@ -443,8 +442,7 @@ def run_ensemble(args):
         "gdof_steps_per_s": steps_per_s * dofs / 1e9,
         "hbm_roofline_frac": algo_bytes * steps_per_s / (peaks["hbm_gbs"] * 1e9),
         "roofline": {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
-                     "frac": ach / pk, "traffic": None, "peak_source": src,
-                     "share": {k: v[0] / tot for k, v in kt.items()}},
+                     "frac": ach / pk, "traffic": None, "peak_source": src},
         "setup_s": setup_s,
         "inputs_s": inputs_s,
         "clocks": clk,
@@ -561,10 +559,8 @@ def run_large(args):
     dom = max(per, key=per.get)
     pk, src = kernel_peak(dom, 1)
     ach = costs[dom]["flops"] / (per[dom] * 1e-3) / 1e12
-    tot = sum(v[0] for v in kt.values())
     roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-            "traffic": None, "peak_source": src, "launch_ms": per[dom],
-            "share": {k: v[0] / tot for k, v in kt.items() if v[1] > 0}}
+            "traffic": None, "peak_source": src, "launch_ms": per[dom]}
     opf.opf_destroy(h)
     oracle_err = large_oracle_check(opf, w)
     dof = 3 * w["N"] * (2 * w["K"] - 1) * (2 * w["M"] - 1)
@@ -915,13 +911,11 @@ def run_gpu(args, w):
         dom_ms = kt[dom][0] / max(1, kt[dom][1])
         pk, src = kernel_peak(dom, precision)
         ach = costs[dom]["flops"] / (dom_ms * 1e-3) / 1e12
-        tot = sum(x[0] for x in kt.values())
         traffic = PROFILED_DRAM_BYTES.get((dom, precision))
         return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
                 "frac": ach / pk, "traffic": traffic,
                 "traffic_source": PROFILE_FILES.get(dom) if traffic is not None else None,
-                "peak_source": src, "launch_ms": dom_ms,
-                "share": {k: v[0] / tot for k, v in kt.items()}}
+                "peak_source": src, "launch_ms": dom_ms}
 
     roof = roofline(ktimes, args.precision)
     fp64_value = job_rate(args.steps, world, res[0][0] / 1000.0)

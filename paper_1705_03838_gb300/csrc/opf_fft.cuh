@@ -145,9 +145,20 @@ __device__ V* block_fft(V* a, V* b, int batch, int ld, const FftPlan& p, const V
 // constants, so the index arithmetic folds into shifts and multiply-highs, the
 // first stage (all twiddles 1) skips its multiplications, and radix 8 cuts the
 // number of shared-memory passes.  Same conventions as block_fft.
-template <int R, int N, int NS, int SIGN, typename V>
+//
+// The buffers between two stages hold element i of a sequence at
+// fft_swz(i) = i ^ ((i >> 3) & 7) (a permutation inside each group of eight;
+// every compiled length is a multiple of 8): the first stage writes element
+// j R + q for consecutive j, a stride of R complex values that would put a
+// warp's stores on two or four of the 16 eight-byte bank pairs, and the
+// permutation spreads them.  The caller's input and the result are in the
+// plain layout; the arithmetic is unchanged.
+__host__ __device__ constexpr int fft_swz(int i) { return i ^ ((i >> 3) & 7); }
+
+template <int R, int N, int NS, int SIGN, bool SWR, bool SWW, typename V>
 __device__ __forceinline__ void fft_stage_c(const V* __restrict__ a, V* __restrict__ b, int ld, int batch,
                                             const V* __restrict__ tw) {
+  static_assert(N % 8 == 0, "the swizzle permutes groups of eight");
   constexpr int nR = N / R, step = N / (NS * R);
   const int work = batch * nR;
   for (int w = threadIdx.x; w < work; w += blockDim.x) {
@@ -157,32 +168,57 @@ __device__ __forceinline__ void fft_stage_c(const V* __restrict__ a, V* __restri
     const V* src = a + bt * ld;
     V* dst = b + bt * ld;
     V v[R];
-    v[0] = src[j];
+    v[0] = src[SWR ? fft_swz(j) : j];
 #pragma unroll
     for (int q = 1; q < R; ++q) {
+      const int ix = j + q * nR;
       if constexpr (NS == 1) {
-        v[q] = src[j + q * nR];
+        v[q] = src[SWR ? fft_swz(ix) : ix];
       } else {
         V t = tw[q * jm * step];
         if constexpr (SIGN < 0) t.y = -t.y;
-        v[q] = cmul(src[j + q * nR], t);
+        v[q] = cmul(src[SWR ? fft_swz(ix) : ix], t);
       }
     }
     butterfly<R>(v, SIGN);
     const int d0 = (j / NS) * NS * R + jm;
 #pragma unroll
-    for (int q = 0; q < R; ++q) dst[d0 + q * NS] = v[q];
+    for (int q = 0; q < R; ++q) {
+      const int ox = d0 + q * NS;
+      dst[SWW ? fft_swz(ox) : ox] = v[q];
+    }
   }
 }
 
 template <int N, int NS, int SIGN, int R, int... Rest, typename V>
 __device__ __forceinline__ V* fft_stages_c(V* a, V* b, int ld, int batch, const V* tw) {
-  fft_stage_c<R, N, NS, SIGN>(a, b, ld, batch, tw);
+  constexpr bool last = sizeof...(Rest) == 0;
+  fft_stage_c<R, N, NS, SIGN, (NS > 1), !last>(a, b, ld, batch, tw);
   __syncthreads();
-  if constexpr (sizeof...(Rest) == 0) {
+  if constexpr (last) {
     return b;
   } else {
     return fft_stages_c<N, NS * R, SIGN, Rest...>(b, a, ld, batch, tw);
+  }
+}
+
+// Element e < count of a block-wide copy: v = load(e), then store(e, v), with
+// U loads in flight per thread (thread t takes e = t, t + blockDim.x, ...,
+// as a plain strided loop would, so coalescing is the same).
+template <int U, typename V, typename Load, typename Store>
+__device__ __forceinline__ void block_copy_batched(int count, Load load, Store store) {
+  for (int b = threadIdx.x; b < count; b += U * blockDim.x) {
+    V v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = b + u * blockDim.x;
+      if (e < count) v[u] = load(e);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = b + u * blockDim.x;
+      if (e < count) store(e, v[u]);
+    }
   }
 }
 

@@ -306,13 +306,16 @@ __global__ void __launch_bounds__(128) k_zsynth(Dims d, FftPlan pz, const V* __r
   for (int e = threadIdx.x; e < nz; e += blockDim.x) tw[e] = twz[e];
   const long fs = d.F;
   grid_dep_wait();
-  for (int e = threadIdx.x; e < MC * nz; e += blockDim.x) {
-    const int z = e % nz, mc = e / nz, m = m0 + mc;
-    int k = z < K ? z : z - nz;
-    V v = V{0, 0};
-    if (m < d.M && (z < K || z > nz - K)) v = W6[f * fs + ((long)m * d.N + n) * d.nk + k + K - 1];
-    A[mc * ld + z] = v;
-  }
+  block_copy_batched<8, V>(
+      MC * nz,
+      [&](int e) {
+        const int z = e % nz, m = m0 + e / nz;
+        const int k = z < K ? z : z - nz;
+        V v = V{0, 0};
+        if (m < d.M && (z < K || z > nz - K)) v = W6[f * fs + ((long)m * d.N + n) * d.nk + k + K - 1];
+        return v;
+      },
+      [&](int e, V v) { A[(e / nz) * ld + e % nz] = v; });
   __syncthreads();
   const V* res;
   if constexpr (NZ > 0) res = block_fft_c<NZ, +1>(A, B, MC, ld, tw);
@@ -373,21 +376,24 @@ __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* _
   const long fstride = (long)d.N * nz * M;
   grid_dep_wait();
   // spectra of the pairs (u_r,u_t), (u_z,w_r), (w_t,w_z):  Z = A + i B
-  for (int e = threadIdx.x; e < zc * 3 * nth; e += blockDim.x) {
-    const int q = e % nth, pr = (e / nth) % 3, zr = e / (3 * nth);
-    const long rowa = ((long)(2 * pr) * d.N + n) * nz + z0 + zr;
-    V v = V{0, 0};
-    if (q < M) {
-      V a = Z6[rowa * M + q], b = Z6[(rowa + (long)d.N * nz) * M + q];
-      if (q == 0) { a.y = 0; b.y = 0; }
-      v = V{a.x - b.y, a.y + b.x};
-    } else if (q > nth - M) {
-      const int m = nth - q;
-      const V a = Z6[rowa * M + m], b = Z6[(rowa + (long)d.N * nz) * M + m];
-      v = V{a.x + b.y, -a.y + b.x};  // conj(a) + i conj(b)
-    }
-    A[(zr * 3 + pr) * ld + q] = v;
-  }
+  block_copy_batched<8, V>(
+      zc * 3 * nth,
+      [&](int e) {
+        const int q = e % nth, pr = (e / nth) % 3, zr = e / (3 * nth);
+        const long rowa = ((long)(2 * pr) * d.N + n) * nz + z0 + zr;
+        V v = V{0, 0};
+        if (q < M) {
+          V a = Z6[rowa * M + q], b = Z6[(rowa + (long)d.N * nz) * M + q];
+          if (q == 0) { a.y = 0; b.y = 0; }
+          v = V{a.x - b.y, a.y + b.x};
+        } else if (q > nth - M) {
+          const int m = nth - q;
+          const V a = Z6[rowa * M + m], b = Z6[(rowa + (long)d.N * nz) * M + m];
+          v = V{a.x + b.y, -a.y + b.x};  // conj(a) + i conj(b)
+        }
+        return v;
+      },
+      [&](int e, V v) { A[(e / nth) * ld + e % nth] = v; });
   __syncthreads();
   V* res;
   if constexpr (NTH > 0) res = block_fft_c<NTH, +1>(A, B, 3 * zc, ld, tw);
@@ -524,12 +530,18 @@ __global__ void __launch_bounds__(128) k_zanalysis(Dims d, FftPlan pz, const V* 
   const bool have0 = threadIdx.x < mcn * nk;
   if (have0 && (Nlin || d.forcing)) addends(out_index(threadIdx.x), &pp, &pm, &pz0);
   const long fstride = (long)d.N * nz * M;
-  for (int e = threadIdx.x; e < 3 * MC * nz; e += blockDim.x) {
-    const int mc = e % MC, z = (e / MC) % nz, f = e / (MC * nz);
-    V v = V{0, 0};
-    if (mc < mcn) v = ZN[f * fstride + ((long)n * nz + z) * M + m0 + mc];
-    A[(f * MC + mc) * ld + z] = v;
-  }
+  block_copy_batched<8, V>(
+      3 * MC * nz,
+      [&](int e) {
+        const int mc = e % MC, z = (e / MC) % nz, f = e / (MC * nz);
+        V v = V{0, 0};
+        if (mc < mcn) v = ZN[f * fstride + ((long)n * nz + z) * M + m0 + mc];
+        return v;
+      },
+      [&](int e, V v) {
+        const int mc = e % MC, z = (e / MC) % nz, f = e / (MC * nz);
+        A[(f * MC + mc) * ld + z] = v;
+      });
   __syncthreads();
   const V* res;
   if constexpr (NZ > 0) res = block_fft_c<NZ, -1>(A, B, 3 * MC, ld, tw);
