@@ -242,6 +242,8 @@ int group_fill_setups(Group* g, bool first) {
     prm[opf::kPrmDt] = s.dt;
     prm[opf::kPrmC] = s.c;
     prm[opf::kPrmSumWG] = s.flux_G;
+    prm[opf::kPrmCi] = 1.0 / (s.c * s.dt);  // the solve's scalings, divided here once
+    prm[opf::kPrmCu] = (1.0 - s.c) / s.c;
     put(g->o_prm, prm, sizeof prm);
     put(g->o_rinv, s.rinv.data(), s.rinv.size() * 8);
     put(g->o_d1, s.d1.data(), s.d1.size() * 8);

@@ -55,7 +55,7 @@ bool build_setup(Setup* s, std::string* err);
 
 // --------------------------------------------------------------- device side
 // Per-trajectory scalars at the head of each trajectory's setup arrays.
-constexpr int kPrmRe = 0, kPrmDt = 1, kPrmC = 2, kPrmSumWG = 3, kPrmCount = 8;
+constexpr int kPrmRe = 0, kPrmDt = 1, kPrmC = 2, kPrmSumWG = 3, kPrmCi = 4, kPrmCu = 5, kPrmCount = 8;
 
 struct DevSetup {
   double* prm = nullptr;  // [kPrmCount] Re, dt, c, sum(wq G)

@@ -1149,8 +1149,7 @@ __global__ void __launch_bounds__((SP ? 48 : 24) * T, solve_min_blocks<T, SP>())
   a.Nb = bofs(a.Nb, d.ss);
   a.Uout = bofs(a.Uout, d.ss);
   a.beta_p = bofs(a.beta_p, d.ss);
-  const double cc = s.prm[kPrmC], dtb = s.prm[kPrmDt];
-  const double ci = 1.0 / (cc * dtb), cu = (1.0 - cc) / cc;
+  const double ci = s.prm[kPrmCi], cu = s.prm[kPrmCu];  // 1 / (c dt), (1 - c) / c
   const long fs = d.F;
   const long base = (long)m * N * nk;
   const double* wv = W1 + pv * N * 9;  // stencils of u_r, u_theta parity
