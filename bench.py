@@ -90,7 +90,7 @@ def kernel_costs(w, precision=1):
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the current
 # kernels on the medium workload (one ncu capture each, summarised in the
 # named profile), keyed by (kernel, precision of the step)
-PROFILED_DRAM_BYTES = {("solve", 0): 22.52e6, ("solve", 1): 22.51e6, ("product", 0): 10.66e6}
+PROFILED_DRAM_BYTES = {("solve", 1): 20.78e6}  # kernels changed since a capture are left out
 PROFILE_FILES = {"solve": "profiles/k_solve_medium.md", "product": "profiles/transforms_medium.md"}
 
 
