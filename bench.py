@@ -594,6 +594,22 @@ LEARNED = dict(N=48, K=16, M=16, m_p=2, alpha=1.25, dt=0.005, precision=1,
                nk=dict(max_newton=2, max_krylov=12, max_hook=4, dt=0.005, tol=1e-10))
 
 
+# The same pipeline on targets the solver certifies: rotating pipe flow
+# (frame rotation Omega = 1 U_cl/R about the axis, alpha = 1, m_p = 2), whose
+# Hagen-Poiseuille flow loses stability near Re = 108 to a helical mode that
+# saturates into a travelling wave; trajectories at Re in [125, 155] from
+# seeded perturbations, snapshots of the saturation and the wave, 720 feature
+# channels (|k| < 8, m < 8) over 24 radial points.  A travelling wave recurs
+# for any T with s = c T, so the Newton problems fix T at the guess's value
+# and solve for s (the axial phase condition).
+LEARNED_ROT = dict(N=24, K=8, M=8, m_p=2, alpha=1.0, dt=0.01, precision=1, rot=(0.0, 0.0, 1.0),
+                   Re_train=(125.0, 155.0), Re_test=140.0, amp=(0.03, 0.12), B_train=56, B_val=6, B_test=8,
+                   seed=1705, warmup=60.0, n_snap=320, every=0.5, T_min=2.0, T_max=12.0, thresh=0.3,
+                   hidden=384, steps=2000, batch=64, lr=1e-3, lam=1.0, net_seed=5, eval_every=200,
+                   nk_guesses=12, nk_T_max=12.0,
+                   nk=dict(max_newton=8, max_krylov=30, max_hook=4, dt=0.01, tol=1e-10, fix_T=1, fix_s=0))
+
+
 def run_learned(args):
     """Learned Newton-Krylov proposals: 64 trajectories (56 for training, 6 of
     them for validation, at Re uniform in [2000, 2500]; 8 held out at Re = 2250)
@@ -610,11 +626,23 @@ def run_learned(args):
     torch.cuda.set_device(0)
     _build.build()
     opf.lib()
+    rotating = args.workload == "learned_rot"
+    cfg = LEARNED_ROT if rotating else LEARNED
     t0 = time.perf_counter()
-    res = learned.run_pipeline(opf, torch, LEARNED,
+    res = learned.run_pipeline(opf, torch, cfg,
                                log=lambda *a: print(*a, f"[{time.perf_counter() - t0:.0f} s]", file=sys.stderr,
                                                     flush=True))
     nk = res.get("nk", {})
+    arms = {name: {"certified_fraction": v.get("certified_fraction"),
+                   "median_newton_iterations_to_certification": v.get("median_newton_iterations_to_certification"),
+                   "median_final": v.get("median_final"), "seconds": v.get("seconds")}
+            for name, v in nk.items()}
+    if rotating:
+        workload = ("learned proposals on certifiable targets: rotating pipe (Omega_z = 1), N=24 |k|<8 m<8 m_p=2 "
+                    "alpha=1, Re in [125,155], 64 trajectories x 320 snapshots")
+    else:
+        workload = ("learned proposals: N=48 |k|<16 m<16 m_p=2 alpha=1.25, Re in [2000,2500], "
+                    "64 trajectories x 320 snapshots")
     line = {
         "metric": "Newton-Krylov-hookstep from learned vs recurrence guesses: median final relative residual",
         "value": nk.get("learned", {}).get("median_final"),
@@ -623,10 +651,10 @@ def run_learned(args):
         "n_gpus": 1,
         "dtype": "bf16 net (f32 accumulate); f32+f64 snapshots; f64 Newton",
         "data": "synthetic (the solver's own trajectories from seeded perturbations)",
-        "config": {"workload": "learned proposals: N=48 |k|<16 m<16 m_p=2 alpha=1.25, Re in [2000,2500], "
-                               "64 trajectories x 320 snapshots"},
+        "config": {"workload": workload},
         "recurrence_median_final": nk.get("recurrence", {}).get("median_final"),
         "snapshot_mean_T_median_final": nk.get("snapshot_mean_T", {}).get("median_final"),
+        "arms": arms,
         "details": res,
     }
     print(json.dumps(line, default=float), flush=True)
@@ -993,9 +1021,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="medium",
-                    choices=["medium", "ensemble", "large", "learned", "net", "floquet", "kernels", "peaks"],
+                    choices=["medium", "ensemble", "large", "learned", "learned_rot", "net", "floquet", "kernels", "peaks"],
                     help="medium: the default single-run line; ensemble: the batched workload; large: the "
-                         "CFL-controlled large run; learned: the learned Newton-Krylov proposal pipeline; "
+                         "CFL-controlled large run; learned: the learned Newton-Krylov proposal pipeline; learned_rot: the "
+                         "same pipeline on the travelling waves of rotating pipe flow (certifiable targets); "
                          "net: the proposal network's training step; floquet: batched Arnoldi "
                          "Floquet multipliers; kernels: per-kernel device times of one workload's step "
                          "(--kernels-workload, --precision, --steps); peaks: measured FP64/FP32 FMA rates")
@@ -1015,7 +1044,7 @@ def main():
         run_ensemble(args)
     elif args.workload == "large":
         run_large(args)
-    elif args.workload == "learned":
+    elif args.workload in ("learned", "learned_rot"):
         run_learned(args)
     elif args.workload == "net":
         run_net(args)

@@ -152,7 +152,8 @@ int opf_nonlinear(opf_t* h, const double* coeffs, double* out);
  *   "rot_x", "rot_y", "rot_z": frame rotation Omega (Cartesian components, pipe
  *                axis z; default 0): the Coriolis force -2 Omega x u joins the
  *                nonlinear term (section 3.1's rotating pipe; a transverse axis
- *                needs m_p = 1).  Single handles only.
+ *                needs m_p = 1).  On an ensemble (opf_ens_set_option) it
+ *                applies to every trajectory.
  *   "cfl":       C > 0 switches on automatic time-step control (section 2):
  *                after every step dt = min(dt_max, C / max(|u_r|/dr,
  *                |u_theta|/(r dtheta), |u_z|/dz)) over the 3K x 3M grid, applied

@@ -797,6 +797,20 @@ int runner_option(Runner* r, const char* key, double v) {
   } else if (!strcmp(key, "autotune")) {
     if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "autotune: 0 or 1");
     r->autotune = (int)v;
+  } else if (!strcmp(key, "rot_x") || !strcmp(key, "rot_y") || !strcmp(key, "rot_z")) {
+    // frame rotation, shared by every trajectory (all groups)
+    if (!std::isfinite(v)) return fail(OPF_EINVAL, "rotation: finite value");
+    for (Group* g : r->groups) {
+      const opf::Dims& d = g->d;
+      const double x = key[4] == 'x' ? v : d.rot_x, y = key[4] == 'y' ? v : d.rot_y;
+      if ((x != 0.0 || y != 0.0) && d.m_p != 1)
+        return fail(OPF_EINVAL, "rotation about a transverse axis needs m_p = 1 (it couples m to m +- 1)");
+    }
+    for (Group* g : r->groups) {
+      opf::Dims& d = g->d;
+      (key[4] == 'x' ? d.rot_x : key[4] == 'y' ? d.rot_y : d.rot_z) = v;
+      d.rotate = (d.rot_x != 0.0 || d.rot_y != 0.0 || d.rot_z != 0.0) ? 1 : 0;
+    }
   } else if (!strcmp(key, "spike")) {
     if (v != 0.0 && v != 1.0) return fail(OPF_EINVAL, "spike: 0 or 1");
     for (Group* g : r->groups) g->d.spike = (v != 0.0 && g->spike_built) ? 1 : 0;
@@ -836,6 +850,9 @@ int runner_get_option(Runner* r, const char* key, double* v) {
   else if (!strcmp(key, "pdl")) *v = r->groups.empty() ? 0 : r->groups[0]->d.pdl;
   else if (!strcmp(key, "fused")) *v = r->groups.empty() ? 0 : opf::fused32_cluster(r->groups[0]->d);
   else if (!strcmp(key, "spike")) *v = r->groups.empty() ? 0 : r->groups[0]->d.spike;
+  else if (!strcmp(key, "rot_x")) *v = r->groups.empty() ? 0 : r->groups[0]->d.rot_x;
+  else if (!strcmp(key, "rot_y")) *v = r->groups.empty() ? 0 : r->groups[0]->d.rot_y;
+  else if (!strcmp(key, "rot_z")) *v = r->groups.empty() ? 0 : r->groups[0]->d.rot_z;
   else if (!strcmp(key, "mcz")) *v = r->groups.empty() ? 0 : r->groups[0]->d.mcz;
   else if (!strcmp(key, "mca")) *v = r->groups.empty() ? 0 : r->groups[0]->d.mca;
   else if (!strcmp(key, "zc")) *v = r->groups.empty() ? 0 : r->groups[0]->d.zc;
@@ -1083,20 +1100,6 @@ int opf_set_option(opf_t* h, const char* key, double v) {
     h->run.dt_max = v;
     return OPF_OK;
   }
-  if (key && (!strcmp(key, "rot_x") || !strcmp(key, "rot_y") || !strcmp(key, "rot_z"))) {
-    if (!std::isfinite(v)) return fail(OPF_EINVAL, "rotation: finite value");
-    opf::Dims& d = h->g.d;
-    double x = d.rot_x, y = d.rot_y, z = d.rot_z;
-    (key[4] == 'x' ? x : key[4] == 'y' ? y : z) = v;
-    if ((x != 0.0 || y != 0.0) && d.m_p != 1)
-      return fail(OPF_EINVAL, "rotation about a transverse axis needs m_p = 1 (it couples m to m +- 1)");
-    d.rot_x = x;
-    d.rot_y = y;
-    d.rot_z = z;
-    d.rotate = (x != 0.0 || y != 0.0 || z != 0.0) ? 1 : 0;
-    h->run.drop_graph();
-    return OPF_OK;
-  }
   if (key && !strcmp(key, "dt")) {  // set the time step; dt-dependent operators are refactored
     if (!(v > 0.0) || !std::isfinite(v)) return fail(OPF_EINVAL, "dt: > 0");
     if (v != h->g.dt[0]) {
@@ -1120,9 +1123,6 @@ int opf_get_option(opf_t* h, const char* key, double* v) {
     *v = h->run.dt_max > 0.0 ? h->run.dt_max : h->g.dt[0];
     return OPF_OK;
   }
-  if (key && v && !strcmp(key, "rot_x")) return (*v = h->g.d.rot_x), OPF_OK;
-  if (key && v && !strcmp(key, "rot_y")) return (*v = h->g.d.rot_y), OPF_OK;
-  if (key && v && !strcmp(key, "rot_z")) return (*v = h->g.d.rot_z), OPF_OK;
   if (key && v && !strcmp(key, "cfl_number")) {  // max |u| dt / spacing of the last step
     double c = 0.0;
     CU(cudaMemcpy(&c, h->g.cfl, sizeof(double), cudaMemcpyDeviceToHost));

@@ -182,14 +182,15 @@ def constant_predictor_loss(ty, tz, lam, mean_tz, scale):
 
 
 def generate(opf, N, K, M, m_p, alpha, Re, amp, seeds, dt, warmup, n_snap, every, keep=None,
-             precision=1):
+             precision=1, rot=None):
     """Integrate one ensemble (trajectory j: Re[j], puff-envelope perturbation
     of amplitude amp[j] and seed seeds[j]) for `warmup` time units, then
     record features every `every` time units, n_snap times (fewer when keep
     is given: up to its largest index).  keep: {j: set of snapshot indices}
-    whose full states are returned.  Returns (feats [B][S][N][720], kept
-    {(j, i): state}, finite [B] (False where a trajectory went non-finite),
-    seconds)."""
+    whose full states are returned.  rot: frame rotation (Omega_x, Omega_y,
+    Omega_z) shared by the trajectories (None: none).  Returns (feats
+    [B][S][N][720], kept {(j, i): state}, finite [B] (False where a
+    trajectory went non-finite), seconds)."""
     import time as _time
 
     B = len(Re)
@@ -197,6 +198,7 @@ def generate(opf, N, K, M, m_p, alpha, Re, amp, seeds, dt, warmup, n_snap, every
         n_snap = min(n_snap, 1 + max(max(v) for v in keep.values() if v))
     e = opf.opf_ens_create([N] * B, [K] * B, [M] * B, [m_p] * B, [alpha] * B, Re, [dt] * B)
     opf.opf_ens_set_option(e, "precision", precision)
+    set_rotation(opf, e, rot)
     for j in range(B):
         opf.opf_ens_set_state(e, j, inputs.seeded_state(N, K, M, m_p, alpha, amp[j], seeds[j],
                                                         envelope=inputs.envelope_puff))
@@ -311,13 +313,21 @@ def packed_norm(U, K):
     return float(np.sqrt((w[None, :, :, None] * np.abs(U) ** 2).sum()))
 
 
-def relative_residual(opf, N, K, M, m_p, alpha, Re, states, T, s, dt):
+def set_rotation(opf, e, rot):
+    """Frame rotation (Omega_x, Omega_y, Omega_z) of every trajectory of ensemble e."""
+    if rot is not None:
+        for key, v in zip(("rot_x", "rot_y", "rot_z"), rot):
+            opf.opf_ens_set_option(e, key, float(v))
+
+
+def relative_residual(opf, N, K, M, m_p, alpha, Re, states, T, s, dt, rot=None):
     """|sigma_s Phi_T(u) - u| / |u| (packed norms) for a list of guesses,
     batched in one ensemble; all take the same number of steps,
     ceil(max T / dt), each of its own length T_j / steps."""
     B = len(states)
     nmax = max(max(1, int(math.ceil(t / dt - 1e-9))) for t in T)
     e = opf.opf_ens_create([N] * B, [K] * B, [M] * B, [m_p] * B, [alpha] * B, Re, [t / nmax for t in T])
+    set_rotation(opf, e, rot)
     for j in range(B):
         opf.opf_ens_set_state(e, j, states[j])
     opf.opf_ens_step(e, nmax)
@@ -336,7 +346,8 @@ def run_pipeline(opf, torch, cfg, log=None):
     precision Re_train Re_test amp B_train B_test seed warmup n_snap every
     T_min T_max thresh hidden steps batch lr lam net_seed nk_guesses nk_T_max
     nk (options of opf_nk_solve); optional B_val eval_every augment
-    interior_minima."""
+    interior_minima rot (frame rotation (Omega_x, Omega_y, Omega_z) of the
+    data and of the Newton problems)."""
     import time as _time
 
     say = log or (lambda *a: None)
@@ -350,8 +361,9 @@ def run_pipeline(opf, torch, cfg, log=None):
     seeds = [int(c["seed"]) * 1000 + j for j in range(Btr + Bte)]
     out = {"config": {k: v for k, v in c.items() if k != "nk"}, "nk_options": dict(c.get("nk", {}))}
 
+    rot = c.get("rot")
     feats, _, finite, t_gen = generate(opf, N, K, M, m_p, alpha, Re, amp, seeds, c["dt"], c["warmup"],
-                                       c["n_snap"], c["every"], precision=c.get("precision", 1))
+                                       c["n_snap"], c["every"], precision=c.get("precision", 1), rot=rot)
     steps_per_traj = int(round(c["warmup"] / c["dt"])) + (c["n_snap"] - 1) * int(round(c["every"] / c["dt"]))
     out["generate"] = {"seconds": t_gen, "trajectories": Btr + Bte, "finite": int(finite.sum()),
                        "snapshots": int(finite.sum()) * c["n_snap"],
@@ -434,7 +446,7 @@ def run_pipeline(opf, torch, cfg, log=None):
         keep.setdefault(j - Btr, set()).add(r[0])
     feats2, kept, _, _ = generate(opf, N, K, M, m_p, alpha, Re[Btr:], amp[Btr:], seeds[Btr:], c["dt"],
                                   c["warmup"], c["n_snap"], c["every"], keep=keep,
-                                  precision=c.get("precision", 1))
+                                  precision=c.get("precision", 1), rot=rot)
     out["replay_max_abs_diff"] = float(max(np.abs(feats2[j - Btr, r[0]] - feats[j, r[0]]).max()
                                            for _, j, r in cands))
     U0 = [kept[(j - Btr, r[0])] for _, j, r in cands]
@@ -453,17 +465,26 @@ def run_pipeline(opf, torch, cfg, log=None):
             # training-mean period and shift
             "snapshot_mean_T": (U0, [T_mean] * len(U0), [float(s_mean[0])] * len(U0))}
     nk = dict(c.get("nk", {}))
+    if rot is not None:
+        nk.setdefault("rot", tuple(float(v) for v in rot))
     Re_te = [float(c["Re_test"])] * len(U0)
     out["nk"] = {}
     for name, (Us, Ts, ss) in arms.items():
-        r0 = relative_residual(opf, N, K, M, m_p, alpha, Re_te, Us, Ts, ss, nk.get("dt", 0.01))
+        r0 = relative_residual(opf, N, K, M, m_p, alpha, Re_te, Us, Ts, ss, nk.get("dt", 0.01), rot=rot)
         t0 = _time.perf_counter()
         st, T, s, res, it = opf.opf_nk_solve(N, K, M, m_p, alpha, float(c["Re_test"]), Us, Ts, ss, **nk)
         sec = _time.perf_counter() - t0
         tol = nk.get("tol", 1e-10)
+        ok = np.asarray(res) < tol
+        its = np.asarray(it)
         out["nk"][name] = {"initial_residual": [float(v) for v in r0], "final_residual": [float(v) for v in res],
                            "newton_iterations": [int(v) for v in it], "T": [float(v) for v in T],
-                           "converged": int((res < tol).sum()), "guesses": len(Us), "seconds": sec,
+                           "s": [float(v) for v in s],
+                           "converged": int(ok.sum()), "guesses": len(Us), "seconds": sec,
+                           "certified_fraction": float(ok.mean()),
+                           # the guesses of an arm are solved together (one batched solve),
+                           # so the time to certification is given in Newton iterations
+                           "median_newton_iterations_to_certification": float(np.median(its[ok])) if ok.any() else None,
                            "median_initial": float(np.median(r0)), "median_final": float(np.median(res))}
         say("nk", name, {k: out["nk"][name][k] for k in ("median_initial", "median_final", "converged", "seconds")})
     opf.opf_net_destroy(net)

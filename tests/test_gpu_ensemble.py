@@ -122,3 +122,30 @@ def test_autotuned_shapes_give_identical_results(opf, precision):
             assert opf.opf_get_option(h, "autotune") == 2
             assert opf.opf_get_option(h, "tile") in (4, 8, 16)
     assert np.array_equal(out[0], out[1])
+
+
+def test_rotating_ensemble_equals_single_runs(opf):
+    """Frame rotation on an ensemble (every trajectory, several shape groups)
+    gives each trajectory exactly what a single handle with the same
+    rotation gives."""
+    specs = [(16, 4, 4, 2, 1.0, 140.0, 0.01), (16, 4, 4, 2, 1.0, 150.0, 0.01), (12, 3, 5, 2, 1.0, 130.0, 0.01)]
+    cols = list(zip(*specs))
+    e = opf.opf_ens_create(*cols)
+    opf.opf_ens_set_option(e, "rot_z", 1.0)
+    U0s = [inputs.seeded_state(N, K, M, m_p, a, 0.05, 300 + i) for i, (N, K, M, m_p, a, Re, dt) in enumerate(specs)]
+    for i, U in enumerate(U0s):
+        opf.opf_ens_set_state(e, i, U)
+    opf.opf_ens_step(e, 20)
+    for i, (N, K, M, m_p, a, Re, dt) in enumerate(specs):
+        h = opf.opf_create(N, K, M, m_p, a, Re, dt)
+        opf.opf_set_option(h, "rot_z", 1.0)
+        opf.opf_set_option(h, "spike", 0)
+        opf.opf_set_state(h, U0s[i])
+        opf.opf_step(h, 20)
+        assert np.array_equal(opf.opf_ens_get_state(e, i), opf.opf_get_state(h))
+    h = opf.opf_create(*specs[0])
+    opf.opf_set_state(h, U0s[0])
+    opf.opf_step(h, 20)
+    assert not np.array_equal(opf.opf_ens_get_state(e, 0), opf.opf_get_state(h))  # the rotation acts
+    with pytest.raises(opf.OpfError):  # a transverse axis needs m_p = 1 in every group
+        opf.opf_ens_set_option(e, "rot_x", 0.5)
