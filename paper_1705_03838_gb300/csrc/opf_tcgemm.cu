@@ -9,12 +9,14 @@
 // (split K: the ranges' partial sums go to separate slices that a second
 // kernel adds up in a fixed order):
 //   warp 0, one thread: TMA producer -- 128 x 64 (A) and BN x 64 (B) tiles,
-//     128-byte swizzle, into a 4-stage shared-memory ring (mbarrier with tx
-//     count);
+//     128-byte swizzle, into a shared-memory ring of 8 (BN = 64) or 6
+//     (BN = 128) stages, ~192 KB (mbarrier with tx count);
 //   warp 1, one thread: issues tcgen05.mma (M=128, N=BN, K=16) per 16-wide
 //     K slice and commits each stage back to the producer;
 //   all 4 warps: read the accumulator with tcgen05.ld (warp w owns TMEM
-//     lanes 32w..32w+31 = tile rows) and apply the epilogue.
+//     lanes 32w..32w+31 = tile rows), 32 x 32 blocks at a time, pass each
+//     block through shared memory (the ring, free by then) so that a warp
+//     writes whole rows, and apply the epilogue on the way out.
 // Every mbarrier wait is bounded (about 2 s of wall time); on a timeout the
 // kernel records an error flag, still frees its TMEM and returns.
 #include <cuda.h>
@@ -31,7 +33,11 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int kBM = 128, kBK = 64, kStages = 4;
+constexpr int kBM = 128, kBK = 64;
+template <int BN>
+__host__ __device__ constexpr int stages() {
+  return BN == 64 ? 8 : 6;
+}
 constexpr int kTileA = kBM * kBK * 2;  // 128 rows x 128 bytes
 constexpr unsigned long long kWaitNs = 2000000000ull;
 // instruction descriptor (kind::f16): D = F32 (bits 4-5), A = B = BF16 (bits
@@ -42,7 +48,7 @@ __host__ __device__ constexpr uint32_t idesc() {
 }
 template <int BN>
 constexpr size_t smem_bytes() {
-  return 1024 + (size_t)kStages * (kTileA + BN * kBK * 2) + 256;
+  return 1024 + (size_t)stages<BN>() * (kTileA + BN * kBK * 2) + 256;
 }
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -130,7 +136,9 @@ __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N, int nk_all,
               int nsplit, TcEpilogue e, float* part, int* err) {
   constexpr int kTileB = BN * kBK * 2;
+  constexpr int kStages = stages<BN>();
   constexpr uint32_t kCols = BN;  // FP32 accumulator: 128 lanes x BN columns
+  static_assert(4 * 32 * 33 * 4 <= kStages * kTileA, "epilogue staging must fit in the A ring");
   extern __shared__ unsigned char sraw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)sraw + 1023) & ~(uintptr_t)1023);  // 128B swizzle: 1 KB aligned
   unsigned char* sA = sm;
@@ -199,37 +207,40 @@ __global__ void __launch_bounds__(128, 1)
   }
   __syncwarp();
 
-  // epilogue: TMEM lane = tile row (warp w: rows 32w..32w+31), 32 columns per load
+  // epilogue: TMEM lane = tile row (warp w: rows 32w..32w+31), 32 columns per
+  // load; each 32 x 32 block goes through this warp's slice of the A ring
+  // (free once every MMA has completed; rows padded to 33 floats, so neither
+  // the row-wise writes nor the column-wise reads meet bank conflicts), then
+  // lane j takes column n0 + c0 + j of each of the 32 rows: coalesced stores.
   if (!mbar_wait(done, 0)) ok = false;
   tc_fence_after();
-  const int row = m0 + warp * 32 + lane;
+  float* stage = (float*)sA + warp * 32 * 33;
 #pragma unroll 1
   for (int c0 = 0; c0 < BN; c0 += 32) {
     uint32_t v[32];
     tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-    if (row < M) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = nk ? __uint_as_float(v[j]) : 0.f;
+    __syncwarp();
+    const int n = n0 + c0 + lane;
+    const float bn = (!part && e.bias && n < N) ? e.bias[n] : 0.f;
+#pragma unroll 4
+    for (int rr = 0; rr < 32; ++rr) {
+      const int row = m0 + warp * 32 + rr;
+      if (row >= M || n >= N) continue;
+      float x = stage[rr * 33 + lane];
       if (part) {  // split K: raw partial sums into this split's slice
-        float* dst = part + ((long)z * M + row) * N;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = n0 + c0 + j;
-          if (n >= N) break;
-          dst[n] = nk ? __uint_as_float(v[j]) : 0.f;
-        }
+        part[((long)z * M + row) * N + n] = x;
       } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = n0 + c0 + j;
-          if (n >= N) break;
-          float x = __uint_as_float(v[j]) + (e.bias ? e.bias[n] : 0.f);
-          const long o = (long)row * e.ldo + n;
-          if (e.pre_f32) e.pre_f32[o] = x;
-          if (e.gelu) x = gelu_f(x);
-          if (e.out_f32) e.out_f32[o] = e.accumulate ? e.out_f32[o] + x : x;
-          if (e.out_bf16) ((bf16*)e.out_bf16)[o] = __float2bfloat16(x);
-        }
+        x += bn;
+        const long o = (long)row * e.ldo + n;
+        if (e.pre_f32) e.pre_f32[o] = x;
+        if (e.gelu) x = gelu_f(x);
+        if (e.out_f32) e.out_f32[o] = e.accumulate ? e.out_f32[o] + x : x;
+        if (e.out_bf16) ((bf16*)e.out_bf16)[o] = __float2bfloat16(x);
       }
     }
+    __syncwarp();
   }
   if (!ok) atomicExch(err, 1);
   tc_fence_before();
