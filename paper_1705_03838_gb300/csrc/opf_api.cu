@@ -880,30 +880,37 @@ int runner_times(Runner* r, int cap, int* count, const char** names, double* tot
 }
 
 // ---- per-trajectory state transfer and diagnostics
+int traj_state_from_abi(Group* g, int b, cudaStream_t st);
+
 int traj_set_state_device(Group* g, int b, const double* d_coeffs, cudaStream_t st) {
+  const size_t bytes = 3 * (size_t)g->d.F * sizeof(double2);
+  CU(cudaMemcpyAsync(g->at(g->abi, b), d_coeffs, bytes, cudaMemcpyDeviceToDevice, st));
+  return traj_state_from_abi(g, b, st);
+}
+
+// The trajectory's staging copy (abi) into its state: a NaN check, then the
+// layout conversion (with the Hermitian projection and beta reset), which
+// the device skips when the check found a non-finite value -- so the state
+// is unchanged on OPF_ENAN -- and one synchronisation for both.
+int traj_state_from_abi(Group* g, int b, cudaStream_t st) {
   const opf::Dims d = g->single(b);
-  const size_t bytes = 3 * (size_t)d.F * sizeof(double2);
   double2* abi = g->at(g->abi, b);
   int* flag = g->at(g->flag, b);
-  CU(cudaMemcpyAsync(abi, d_coeffs, bytes, cudaMemcpyDeviceToDevice, st));
   opf::launch_nan_check((const double*)abi, 6 * d.F, flag, st);
+  opf::launch_abi_to_internal(d, abi, g->at(g->U, b), st, flag, g->at(g->beta_p, b));
   int h_flag = 0;
   CU(cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
-  if (h_flag) return fail(OPF_ENAN, "set_state: non-finite coefficient; state unchanged");
-  opf::launch_abi_to_internal(d, abi, g->at(g->U, b), st);
-  g->w6_valid = false;
-  CU(cudaMemsetAsync(g->at(g->beta_p, b), 0, sizeof(double), st));
-  CU(cudaStreamSynchronize(st));
   CU(cudaGetLastError());
+  if (h_flag) return fail(OPF_ENAN, "set_state: non-finite coefficient; state unchanged");
+  g->w6_valid = false;
   return OPF_OK;
 }
 
 int traj_set_state_host(Group* g, int b, const double* coeffs, cudaStream_t st) {
   const size_t bytes = 3 * (size_t)g->d.F * sizeof(double2);
-  double2* tmp = g->at(g->tmpU, b);
-  CU(cudaMemcpyAsync(tmp, coeffs, bytes, cudaMemcpyHostToDevice, st));
-  return traj_set_state_device(g, b, (const double*)tmp, st);
+  CU(cudaMemcpyAsync(g->at(g->abi, b), coeffs, bytes, cudaMemcpyHostToDevice, st));
+  return traj_state_from_abi(g, b, st);
 }
 
 int traj_get_state(Group* g, int b, double* out, bool host, cudaStream_t st) {

@@ -124,7 +124,9 @@ size_t solve_smem_bytes(int N, int T);
 void set_last_error(const std::string& m);  // text returned by opf_last_error()
 
 // Launch wrappers (kernels live in opf_kernels.cu).
-void launch_abi_to_internal(const Dims& d, const double2* abi, double2* U, cudaStream_t st);
+// (flag: skip the conversion where the NaN check before it set *flag; beta: reset to 0)
+void launch_abi_to_internal(const Dims& d, const double2* abi, double2* U, cudaStream_t st,
+                            const int* flag = nullptr, double* beta = nullptr);
 void launch_internal_to_abi(const Dims& d, const double2* U, double2* abi, int components_rtz,
                             cudaStream_t st);
 void launch_curl(const Dims& d, const DevSetup& s, const double2* U, double2* W6, cudaStream_t st);

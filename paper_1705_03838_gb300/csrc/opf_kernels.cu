@@ -64,8 +64,13 @@ __device__ __forceinline__ P* bofs(P* p, long stride) {
 
 // ------------------------------------------------------------------ ABI <-> internal
 // abi: [3][M][nk][N] (u_r, u_theta, u_z); internal: [3][M][N][nk] (u+, u-, u_z).
-__global__ void k_abi_to_internal(Dims d, const double2* __restrict__ abi, double2* __restrict__ U) {
+// flag (optional): a non-zero value there (set by the NaN check launched
+// before) leaves U as it is; beta (optional) is reset to 0 otherwise.
+__global__ void k_abi_to_internal(Dims d, const double2* __restrict__ abi, double2* __restrict__ U,
+                                  const int* __restrict__ flag, double* __restrict__ beta) {
+  if (flag && *flag) return;
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (beta && idx == 0) *beta = 0.0;
   if (idx >= d.F) return;
   const int n = idx % d.N;
   const long t = idx / d.N;
@@ -103,9 +108,10 @@ __global__ void k_internal_to_abi(Dims d, const double2* __restrict__ U, double2
   abi[2 * fs + o] = U[2 * fs + i];
 }
 
-void launch_abi_to_internal(const Dims& d, const double2* abi, double2* U, cudaStream_t st) {
+void launch_abi_to_internal(const Dims& d, const double2* abi, double2* U, cudaStream_t st, const int* flag,
+                            double* beta) {
   const int nb = (int)((d.F + 255) / 256);
-  k_abi_to_internal<<<nb, 256, 0, st>>>(d, abi, U);
+  k_abi_to_internal<<<nb, 256, 0, st>>>(d, abi, U, flag, beta);
 }
 void launch_internal_to_abi(const Dims& d, const double2* U, double2* abi, int, cudaStream_t st) {
   const int nb = (int)((d.F + 255) / 256);
@@ -1672,29 +1678,30 @@ __global__ void __launch_bounds__(256) k_energy(Dims d, const double* __restrict
 __global__ void k_energy_final(Dims d, const double* __restrict__ partial, int nblk,
                                const double* __restrict__ wq, const double2* __restrict__ U,
                                const double* beta_p, const double* prm, double* out3) {
-  __shared__ double su[256], sw[256];
-  double a = 0.0, b = 0.0;
+  __shared__ double su[256], sw[256], sq[256];
+  double a = 0.0, b = 0.0, q = 0.0;
   for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
     a += partial[2 * i];
     b += partial[2 * i + 1];
   }
+  const double2* uz = U + 2 * d.F + (d.K - 1);  // (k,m) = (0,0), u_z: the flux int u_z r dr
+  for (int n = threadIdx.x; n < d.N; n += blockDim.x) q += wq[n] * uz[(long)n * d.nk].x;
   su[threadIdx.x] = a;
   sw[threadIdx.x] = b;
+  sq[threadIdx.x] = q;
   __syncthreads();
   for (int h = 128; h > 0; h >>= 1) {
     if (threadIdx.x < h) {
       su[threadIdx.x] += su[threadIdx.x + h];
       sw[threadIdx.x] += sw[threadIdx.x + h];
+      sq[threadIdx.x] += sq[threadIdx.x + h];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    double flux = 0.0;
-    const double2* uz = U + 2 * d.F + (d.K - 1);  // (k,m) = (0,0), u_z
-    for (int n = 0; n < d.N; ++n) flux += wq[n] * uz[(long)n * d.nk].x;
     const double beta = *beta_p * prm[kPrmRe] / 4.0;
     out3[0] = 6.0 * su[0];
-    out3[1] = 4.0 * (1.0 + beta) * flux;
+    out3[1] = 4.0 * (1.0 + beta) * sq[0];
     out3[2] = sw[0];
   }
 }
