@@ -69,7 +69,11 @@ const char* opf_last_error(void);
  * OPF_ENAN if the buffer holds a NaN/Inf (the previous state is kept). */
 int opf_set_state(opf_t* h, const double* coeffs);
 
-/* Copy the current state into a host buffer (layout above). */
+/* Copy the current state into a host buffer (layout above).  Pinned host
+ * buffers (cudaHostAlloc / cudaMallocHost / cudaHostRegister memory) are
+ * read (opf_set_state) and written (opf_get_state) by the library's kernels
+ * directly; other host memory goes through a device staging copy.  Either
+ * way the call is synchronous and the result the same. */
 int opf_get_state(opf_t* h, double* coeffs);
 
 /* Same as opf_set_state / opf_get_state with DEVICE pointers (layout above),

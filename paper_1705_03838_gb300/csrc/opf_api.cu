@@ -907,17 +907,47 @@ int traj_state_from_abi(Group* g, int b, cudaStream_t st) {
   return OPF_OK;
 }
 
+// The device address of a host buffer the GPU can read and write directly --
+// pinned memory (cudaHostAlloc, cudaMallocHost, cudaHostRegister) is mapped
+// under unified addressing -- else nullptr (pageable memory: copies instead).
+const void* device_view(const void* host) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
+}
+
 int traj_set_state_host(Group* g, int b, const double* coeffs, cudaStream_t st) {
-  const size_t bytes = 3 * (size_t)g->d.F * sizeof(double2);
-  CU(cudaMemcpyAsync(g->at(g->abi, b), coeffs, bytes, cudaMemcpyHostToDevice, st));
+  const opf::Dims d = g->single(b);
+  if (const void* dv = device_view(coeffs)) {
+    // pinned: the conversion reads the buffer itself (one pass, with the NaN
+    // check) into scratch, which replaces the state only if every value was
+    // finite; one synchronisation
+    int* flag = g->at(g->flag, b);
+    double2* tmp = g->at(g->tmpU, b);
+    CU(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    opf::launch_abi_to_internal(d, (const double2*)dv, tmp, st, nullptr, nullptr, flag);
+    opf::launch_copy_unless(tmp, g->at(g->U, b), 3 * (long)d.F, flag, g->at(g->beta_p, b), st);
+    int h_flag = 0;
+    CU(cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    CU(cudaGetLastError());
+    if (h_flag) return fail(OPF_ENAN, "set_state: non-finite coefficient; state unchanged");
+    g->w6_valid = false;
+    return OPF_OK;
+  }
+  CU(cudaMemcpyAsync(g->at(g->abi, b), coeffs, 3 * (size_t)d.F * sizeof(double2), cudaMemcpyHostToDevice, st));
   return traj_state_from_abi(g, b, st);
 }
 
 int traj_get_state(Group* g, int b, double* out, bool host, cudaStream_t st) {
   const opf::Dims d = g->single(b);
   double2* abi = g->at(g->abi, b);
-  opf::launch_internal_to_abi(d, g->at(g->U, b), host ? abi : (double2*)out, 1, st);
-  if (host)
+  void* dv = host ? const_cast<void*>(device_view(out)) : nullptr;  // pinned: written by the kernel itself
+  opf::launch_internal_to_abi(d, g->at(g->U, b), dv ? (double2*)dv : host ? abi : (double2*)out, 1, st);
+  if (host && !dv)
     CU(cudaMemcpyAsync(out, abi, 3 * (size_t)d.F * sizeof(double2), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   CU(cudaGetLastError());

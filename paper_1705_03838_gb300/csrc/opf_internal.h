@@ -124,9 +124,12 @@ size_t solve_smem_bytes(int N, int T);
 void set_last_error(const std::string& m);  // text returned by opf_last_error()
 
 // Launch wrappers (kernels live in opf_kernels.cu).
-// (flag: skip the conversion where the NaN check before it set *flag; beta: reset to 0)
+// (flag: skip the conversion where the NaN check before it set *flag; beta: reset to 0;
+// nan_out: set where a coefficient read is not finite)
 void launch_abi_to_internal(const Dims& d, const double2* abi, double2* U, cudaStream_t st,
-                            const int* flag = nullptr, double* beta = nullptr);
+                            const int* flag = nullptr, double* beta = nullptr, int* nan_out = nullptr);
+void launch_copy_unless(const double2* src, double2* dst, long n, const int* flag, double* beta,
+                        cudaStream_t st);
 void launch_internal_to_abi(const Dims& d, const double2* U, double2* abi, int components_rtz,
                             cudaStream_t st);
 void launch_curl(const Dims& d, const DevSetup& s, const double2* U, double2* W6, cudaStream_t st);

@@ -66,8 +66,10 @@ __device__ __forceinline__ P* bofs(P* p, long stride) {
 // abi: [3][M][nk][N] (u_r, u_theta, u_z); internal: [3][M][N][nk] (u+, u-, u_z).
 // flag (optional): a non-zero value there (set by the NaN check launched
 // before) leaves U as it is; beta (optional) is reset to 0 otherwise.
+// nan_out (optional): set to 1 if any coefficient read is not finite (every
+// coefficient is read by the thread of its own (m, k, n)).
 __global__ void k_abi_to_internal(Dims d, const double2* __restrict__ abi, double2* __restrict__ U,
-                                  const int* __restrict__ flag, double* __restrict__ beta) {
+                                  const int* __restrict__ flag, double* __restrict__ beta, int* nan_out) {
   if (flag && *flag) return;
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (beta && idx == 0) *beta = 0.0;
@@ -79,6 +81,9 @@ __global__ void k_abi_to_internal(Dims d, const double2* __restrict__ abi, doubl
   const long fs = d.F;
   auto ld = [&](int c, int kq) { return abi[c * fs + ((long)m * d.nk + kq) * d.N + n]; };
   double2 ur = ld(0, kk), ut = ld(1, kk), uz = ld(2, kk);
+  if (nan_out && !(isfinite(ur.x) && isfinite(ur.y) && isfinite(ut.x) && isfinite(ut.y) && isfinite(uz.x) &&
+                   isfinite(uz.y)))
+    atomicOr(nan_out, 1);
   if (m == 0) {  // Hermitian projection A(-k,0) = conj A(k,0)
     const int kq = d.nk - 1 - kk;
     const double2 vr = ld(0, kq), vt = ld(1, kq), vz = ld(2, kq);
@@ -109,9 +114,24 @@ __global__ void k_internal_to_abi(Dims d, const double2* __restrict__ U, double2
 }
 
 void launch_abi_to_internal(const Dims& d, const double2* abi, double2* U, cudaStream_t st, const int* flag,
-                            double* beta) {
+                            double* beta, int* nan_out) {
   const int nb = (int)((d.F + 255) / 256);
-  k_abi_to_internal<<<nb, 256, 0, st>>>(d, abi, U, flag, beta);
+  k_abi_to_internal<<<nb, 256, 0, st>>>(d, abi, U, flag, beta, nan_out);
+}
+
+// dst = src (n double2) unless *flag is set; beta reset to 0 with it
+__global__ void k_copy_unless(const double2* __restrict__ src, double2* __restrict__ dst, long n,
+                              const int* __restrict__ flag, double* __restrict__ beta) {
+  if (*flag) return;
+  const long i0 = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (beta && i0 == 0) *beta = 0.0;
+  for (long i = i0; i < n; i += (long)gridDim.x * blockDim.x) dst[i] = src[i];
+}
+
+void launch_copy_unless(const double2* src, double2* dst, long n, const int* flag, double* beta,
+                        cudaStream_t st) {
+  const int nb = (int)std::min<long>((n + 255) / 256, 4L * 152);
+  k_copy_unless<<<nb, 256, 0, st>>>(src, dst, n, flag, beta);
 }
 void launch_internal_to_abi(const Dims& d, const double2* U, double2* abi, int, cudaStream_t st) {
   const int nb = (int)((d.F + 255) / 256);
