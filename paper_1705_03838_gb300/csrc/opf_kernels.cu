@@ -386,6 +386,10 @@ template <typename V, int NTH>
 __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* __restrict__ twth,
                                                  const V* __restrict__ Z6, V* __restrict__ ZN) {
   using T = typename Scalar<V>::T;
+  // FP64: the real N_z of two z rows go through one complex forward
+  // transform (1.5 instead of 2 transforms per row on the FP64 pipe); the
+  // FP32 path keeps one per row, the arithmetic of the fused launch
+  constexpr bool kPackNz = sizeof(T) == 8;
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nth = NTH > 0 ? NTH : d.nth, ld = nth, M = d.M;
   const int ZC = d.zc;
@@ -458,8 +462,15 @@ __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* _
       nt -= (T)2 * (o_z * ur - o_r * uz);
       nz -= (T)2 * (o_r * ut - o_t * ur);
     }
-    C[(zr * 2 + 0) * ld + q] = V{nr, nt};
-    C[(zr * 2 + 1) * ld + q] = V{nz, (T)0};
+    if constexpr (kPackNz) {  // rows zr, zr^1 share one sequence for N_z: re <- even row, im <- odd row
+      C[zr * ld + q] = V{nr, nt};
+      T* pz = (T*)&C[(zc + (zr >> 1)) * ld + q];
+      pz[zr & 1] = nz;
+      if ((zc & 1) && zr == zc - 1) pz[1] = (T)0;  // the last row of an odd count has no partner
+    } else {
+      C[(zr * 2 + 0) * ld + q] = V{nr, nt};
+      C[(zr * 2 + 1) * ld + q] = V{nz, (T)0};
+    }
     if (cfl) cmax = fmax(cmax, fmax(fabs(ur) * inv_dr, fmax(fabs(ut) * inv_rdt, fabs(uz + Ubase) * inv_dz)));
   }
   if (cfl) {  // warp max, then one atomic per warp (non-negative doubles order as integers)
@@ -471,19 +482,27 @@ __global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* _
   __syncthreads();
   V* D = (C == A) ? B : A;
   const V* out;
-  if constexpr (NTH > 0) out = block_fft_c<NTH, -1>(C, D, 2 * zc, ld, tw);
-  else out = block_fft(C, D, 2 * zc, ld, pth, tw, -1);
+  const int nfwd = kPackNz ? zc + (zc + 1) / 2 : 2 * zc;
+  if constexpr (NTH > 0) out = block_fft_c<NTH, -1>(C, D, nfwd, ld, tw);
+  else out = block_fft(C, D, nfwd, ld, pth, tw, -1);
   grid_dep_trigger_at(d, 2);
   for (int e = threadIdx.x; e < zc * M; e += blockDim.x) {
-    const int m = e % M, zr = e / M;
-    const V y = out[(zr * 2 + 0) * ld + m];
-    const V yc = out[(zr * 2 + 0) * ld + (m == 0 ? 0 : nth - m)];
+    const int m = e % M, zr = e / M, mc = m == 0 ? 0 : nth - m;
+    const int rp = kPackNz ? zr : zr * 2;  // the (N_r + i N_theta) sequence of row zr
+    const V y = out[rp * ld + m];
+    const V yc = out[rp * ld + mc];
     const V nr = V{(T)0.5 * (y.x + yc.x), (T)0.5 * (y.y - yc.y)};
     const V nt = V{(T)0.5 * (y.y + yc.y), (T)-0.5 * (y.x - yc.x)};
     const long row = ((long)n * nz + z0 + zr) * M + m;
     ZN[row] = nr;
     ZN[fstride + row] = nt;
-    ZN[2 * fstride + row] = out[(zr * 2 + 1) * ld + m];
+    if constexpr (kPackNz) {  // Z = F(a) + i F(b): F(a) = (Z + conj Z(-m)) / 2, F(b) = (Z - conj Z(-m)) / 2i
+      const V w = out[(zc + (zr >> 1)) * ld + m], wc = out[(zc + (zr >> 1)) * ld + mc];
+      ZN[2 * fstride + row] = (zr & 1) ? V{(T)0.5 * (w.y + wc.y), (T)-0.5 * (w.x - wc.x)}
+                                       : V{(T)0.5 * (w.x + wc.x), (T)0.5 * (w.y - wc.y)};
+    } else {
+      ZN[2 * fstride + row] = out[(zr * 2 + 1) * ld + m];
+    }
   }
 }
 
