@@ -992,31 +992,33 @@ __host__ __device__ constexpr bool solve_stage_fits(int N, int T) { return solve
 // x[i * st], i < N, by a group of 4 consecutive lanes (column-oriented):
 // lane t keeps the partial sum of row c+1+t (and of row c+5+t for the wall
 // rows, whose lower band reaches 8); once row c is final its value is
-// broadcast and each lane subtracts its row's multiple of it.  Factor rows
-// use 13 slots (8 L entries for columns i-8..i-1, 1/U_ii, 4 U entries for
-// columns i+1..i+4, stored divided by U_ii); slots outside a row's band hold
-// zeros.  Each lane needs one factor entry per row; it is loaded kAhead rows
-// ahead into a register queue (the loop is unrolled by kAhead so the queue is
-// indexed statically), which keeps the L2 latency off the recursion.  All 32
-// lanes of the warp must call this together (8 right-hand sides per warp).
+// broadcast and each lane subtracts its row's multiple of it.  The factor is
+// stored by columns (13 N values, see to_columns on the host): [N][4]
+// L(c+1+t, c), [N][4] L(c+5+t, c), [N] 1/U_ii, [N][4] U(c-1-t, c) / U_ii,
+// zeros outside the band, so the four lanes of a chain read one 32-byte run
+// per column.  Each lane needs one factor entry per row; it is loaded kAhead
+// rows ahead into a register queue (the loop is unrolled by kAhead so the
+// queue is indexed statically), which keeps the L2 latency off the recursion.
+// All 32 lanes of the warp must call this together (8 right-hand sides per
+// warp).
 __device__ __forceinline__ void band_solve4(const double* __restrict__ L, double* x, int st, int N) {
   const int t = threadIdx.x & 3;
   const unsigned full = 0xffffffffu;
   constexpr int kAhead = 16;
+  const double* Lw = L + 4 * N;  // L(c+5+t, c)
+  const double* Dg = L + 8 * N;  // 1/U_ii
+  const double* Uc = L + 9 * N;  // U(c-1-t, c) / U_(c-1-t)
   // forward: y = L^{-1} b.  Row c+1+t's entry in column c, queued kAhead rows
   // ahead; on the wall rows (c >= N-9) also row c+5+t's entry in column c,
   // all nine loaded up front.
-  auto la_of = [&](int c) {
-    const int r = c + 1 + t;
-    return (c < N && r < N) ? __ldg(L + r * kLuSlots + 7 - t) : 0.0;
-  };
+  auto la_of = [&](int c) { return c < N ? __ldg(L + c * 4 + t) : 0.0; };
   double qa[kAhead], qw[9];
 #pragma unroll
   for (int j = 0; j < kAhead; ++j) qa[j] = la_of(j);
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
-    const int c = N - 9 + j, r = c + 5 + t;
-    qw[j] = (c >= 0 && r < N) ? __ldg(L + r * kLuSlots + 3 - t) : 0.0;
+    const int c = N - 9 + j;
+    qw[j] = c >= 0 ? __ldg(Lw + c * 4 + t) : 0.0;
   }
   double sa = t < N ? x[t * st] : 0.0;
   double sb = 4 + t < N ? x[(4 + t) * st] : 0.0;
@@ -1051,13 +1053,10 @@ __device__ __forceinline__ void band_solve4(const double* __restrict__ L, double
   // y_i / U_ii for all rows at once (off the recursion; the U rows are stored
   // scaled by 1/U_ii, so the backward sweep has a single FMA per row)
   __syncwarp();
-  for (int i = t; i < N; i += 4) x[i * st] *= __ldg(L + i * kLuSlots + 8);
+  for (int i = t; i < N; i += 4) x[i * st] *= __ldg(Dg + i);
   __syncwarp();
   // backward: x = U~^{-1} (y / diag U).  Row c-1-t's scaled entry in column c.
-  auto ua_of = [&](int c) {
-    const int r = c - 1 - t;
-    return (c >= 0 && r >= 0) ? __ldg(L + r * kLuSlots + 9 + t) : 0.0;
-  };
+  auto ua_of = [&](int c) { return c >= 0 ? __ldg(Uc + c * 4 + t) : 0.0; };
   double qu[kAhead];
 #pragma unroll
   for (int j = 0; j < kAhead; ++j) qu[j] = ua_of(N - 1 - j);

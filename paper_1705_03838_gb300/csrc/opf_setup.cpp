@@ -255,6 +255,25 @@ static bool factor(Op* op, double* out, std::string* err, const char* what) {
   return true;
 }
 
+// Device order of a factor (13 N values, like the row slots): per column c,
+// [N][4] L(c+1+t, c), [N][4] L(c+5+t, c) (the wall rows' wider band),
+// [N] 1/U_ii, [N][4] U~(c-1-t, c), t = 0..3.  The substitution's four lanes
+// of a chain read the entries of one column at a time, so a warp's loads come
+// in 32-byte runs instead of one 104-byte row per lane.  Applied after every
+// host use of the row form.
+static void to_columns(double* f, int N) {
+  std::vector<double> g((size_t)kLuSlots * N, 0.0);
+  for (int c = 0; c < N; ++c)
+    for (int t = 0; t < 4; ++t) {
+      const int r = c + 1 + t, rw = c + 5 + t, ru = c - 1 - t;
+      g[(size_t)c * 4 + t] = r < N ? f[(size_t)r * kLuSlots + 7 - t] : 0.0;
+      g[(size_t)4 * N + c * 4 + t] = rw < N ? f[(size_t)rw * kLuSlots + 3 - t] : 0.0;
+      g[(size_t)9 * N + c * 4 + t] = ru >= 0 ? f[(size_t)ru * kLuSlots + 9 + t] : 0.0;
+    }
+  for (int i = 0; i < N; ++i) g[(size_t)8 * N + i] = f[(size_t)i * kLuSlots + 8];
+  std::copy(g.begin(), g.end(), f);
+}
+
 // Two-partition (SPIKE) form of an operator, for the latency-bound solves:
 // rows split at k = N/2 into a top block T and a bottom block B, each
 // factored on its own (13-slot rows, local indices), so the two halves are
@@ -628,6 +647,16 @@ bool build_setup(Setup* s, std::string* err) {
   double fg = 0.0;
   for (int n = 0; n < N; ++n) fg += s->wq[n] * s->G[n];
   s->flux_G = fg;
+  // the factors in the order the device reads them (the split forms: each
+  // half as an operator of its own size)
+  for (size_t o = 0; o * opsz < s->luH.size(); ++o) to_columns(&s->luH[o * opsz], N);
+  for (size_t o = 0; o * opsz < s->luP.size(); ++o) to_columns(&s->luP[o * opsz], N);
+  const int kh = N / 2;
+  for (std::vector<double>* v : {&s->luH2, &s->luP2})
+    for (size_t o = 0; o * opsz < v->size(); ++o) {
+      to_columns(&(*v)[o * opsz], kh);
+      to_columns(&(*v)[o * opsz + (size_t)kh * kLuSlots], N - kh);
+    }
   return true;
 }
 
