@@ -312,11 +312,25 @@ void launch_curl_split32(const Dims& d, const DevSetup& s, const double2* U, flo
                      (const float*)s.d1f, (const double*)s.r, (const double*)s.rinv, U, W6, Nlin);
 }
 
+// Threads per block of the transform kernels: 256 for grids of at most eight
+// blocks per SM (one or a few waves: more threads per batch of sequences
+// shorten each block's passes), 128 for larger grids (batched ensemble
+// groups, the N = 128 grid), which measured as fast or faster in the smaller
+// unit.  The arithmetic is the same either way.
+static unsigned transform_threads(const dim3& g) {
+  static const int sms = [] {
+    int dev = 0, n = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 152;
+  }();
+  return (long)g.x * g.y * g.z <= 8L * sms ? 256u : 128u;
+}
+
 // ------------------------------------------------------------------ z synthesis (A2)
 
 // NZ > 0: the z length 3K is the compile-time constant NZ (compiled plan).
 template <typename V, int NZ>
-__global__ void __launch_bounds__(128) k_zsynth(Dims d, FftPlan pz, const V* __restrict__ twz,
+__global__ void __launch_bounds__(256) k_zsynth(Dims d, FftPlan pz, const V* __restrict__ twz,
                                                 const V* __restrict__ W6, V* __restrict__ Z6) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nz = NZ > 0 ? NZ : d.nz, ld = nz + 1, MC = d.mcz;
@@ -361,7 +375,7 @@ void launch_zsynth32(const Dims& d, const DevSetup& s, const FftPlan& pz, const 
   dim3 g((d.M + d.mcz - 1) / d.mcz, d.N * 6, d.B);
   const size_t sm = zsynth_smem(d, d.mcz, sizeof(float2));
   with_fft_length(d.nz, [&](auto n) {
-    launch_step_kernel(d, k_zsynth<float2, decltype(n)::value>, g, dim3(128), sm, st, d, pz,
+    launch_step_kernel(d, k_zsynth<float2, decltype(n)::value>, g, dim3(transform_threads(g)), sm, st, d, pz,
                        (const float2*)s.tw_z32, W6, Z6);
   });
 }
@@ -371,7 +385,7 @@ void launch_zsynth(const Dims& d, const DevSetup& s, const FftPlan& pz, const do
   dim3 g((d.M + d.mcz - 1) / d.mcz, d.N * 6, d.B);
   const size_t sm = zsynth_smem(d, d.mcz, sizeof(double2));
   with_fft_length(d.nz, [&](auto n) {
-    launch_step_kernel(d, k_zsynth<double2, decltype(n)::value>, g, dim3(128), sm, st, d, pz,
+    launch_step_kernel(d, k_zsynth<double2, decltype(n)::value>, g, dim3(transform_threads(g)), sm, st, d, pz,
                        (const double2*)s.tw_z, W6, Z6);
   });
 }
@@ -383,7 +397,7 @@ __device__ __forceinline__ void sincos_pi(float x, float* s, float* c) { sincosp
 
 // NTH > 0: the theta length 3M is the compile-time constant NTH.
 template <typename V, int NTH>
-__global__ void __launch_bounds__(128) k_product(Dims d, FftPlan pth, const V* __restrict__ twth,
+__global__ void __launch_bounds__(256) k_product(Dims d, FftPlan pth, const V* __restrict__ twth,
                                                  const V* __restrict__ Z6, V* __restrict__ ZN) {
   using T = typename Scalar<V>::T;
   // FP64: the real N_z of two z rows go through one complex forward
@@ -513,7 +527,7 @@ void launch_product32(const Dims& d, const DevSetup& s, const FftPlan& pth, cons
   dim3 g((d.nz + d.zc - 1) / d.zc, d.N, d.B);
   const size_t sm = product_smem(d, d.zc, sizeof(float2));
   with_fft_length(d.nth, [&](auto n) {
-    launch_step_kernel(d, k_product<float2, decltype(n)::value>, g, dim3(128), sm, st, d, pth,
+    launch_step_kernel(d, k_product<float2, decltype(n)::value>, g, dim3(transform_threads(g)), sm, st, d, pth,
                        (const float2*)s.tw_th32, Z6, ZN);
   });
 }
@@ -523,14 +537,14 @@ void launch_product(const Dims& d, const DevSetup& s, const FftPlan& pth, const 
   dim3 g((d.nz + d.zc - 1) / d.zc, d.N, d.B);
   const size_t sm = product_smem(d, d.zc, sizeof(double2));
   with_fft_length(d.nth, [&](auto n) {
-    launch_step_kernel(d, k_product<double2, decltype(n)::value>, g, dim3(128), sm, st, d, pth,
+    launch_step_kernel(d, k_product<double2, decltype(n)::value>, g, dim3(transform_threads(g)), sm, st, d, pth,
                        (const double2*)s.tw_th, Z6, ZN);
   });
 }
 
 // ------------------------------------------------------------------ z analysis (A4)
 template <typename V, int NZ>
-__global__ void __launch_bounds__(128) k_zanalysis(Dims d, FftPlan pz, const V* __restrict__ twz,
+__global__ void __launch_bounds__(256) k_zanalysis(Dims d, FftPlan pz, const V* __restrict__ twz,
                                                    const V* __restrict__ ZN, const double2* __restrict__ Nlin,
                                                    double2* __restrict__ Nout) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -637,7 +651,7 @@ void launch_zanalysis(const Dims& d, const DevSetup& s, const FftPlan& pz, const
   dim3 g((d.M + d.mca - 1) / d.mca, d.N, d.B);
   const size_t sm = zanalysis_smem(d, d.mca, sizeof(double2));
   with_fft_length(d.nz, [&](auto n) {
-    launch_step_kernel(d, k_zanalysis<double2, decltype(n)::value>, g, dim3(128), sm, st, d, pz,
+    launch_step_kernel(d, k_zanalysis<double2, decltype(n)::value>, g, dim3(transform_threads(g)), sm, st, d, pz,
                        (const double2*)s.tw_z, ZN, (const double2*)nullptr, Nout);
   });
 }
@@ -647,7 +661,7 @@ void launch_zanalysis32(const Dims& d, const DevSetup& s, const FftPlan& pz, con
   dim3 g((d.M + d.mca - 1) / d.mca, d.N, d.B);
   const size_t sm = zanalysis_smem(d, d.mca, sizeof(float2));
   with_fft_length(d.nz, [&](auto n) {
-    launch_step_kernel(d, k_zanalysis<float2, decltype(n)::value>, g, dim3(128), sm, st, d, pz,
+    launch_step_kernel(d, k_zanalysis<float2, decltype(n)::value>, g, dim3(transform_threads(g)), sm, st, d, pz,
                        (const float2*)s.tw_z32, ZN, Nlin, Nout);
   });
 }
