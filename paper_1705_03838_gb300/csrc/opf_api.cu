@@ -251,7 +251,14 @@ int group_fill_setups(Group* g, bool first) {
     put(g->o_hop, s.hop.data(), s.hop.size() * sizeof(int));
     put(g->o_luH, s.luH.data(), s.luH.size() * 8);
     put(g->o_luP, s.luP.data(), s.luP.size() * 8);
-    put(g->o_basis, s.basis.data(), s.basis.size() * 8);
+    {  // device order [K][M][N][6]: the six responses of one radial row together
+      const size_t nmode = s.basis.size() / (6 * (size_t)d.N);
+      std::vector<double> bt(s.basis.size());
+      for (size_t q = 0; q < nmode; ++q)
+        for (int v = 0; v < 6; ++v)
+          for (int i = 0; i < d.N; ++i) bt[(q * d.N + i) * 6 + v] = s.basis[(q * 6 + v) * d.N + i];
+      put(g->o_basis, bt.data(), bt.size() * 8);
+    }
     put(g->o_ainv, s.ainv.data(), s.ainv.size() * 8);
     put(g->o_G, s.G.data(), s.G.size() * 8);
     put(g->o_twz, twz.data(), d.nz * sizeof(double2));

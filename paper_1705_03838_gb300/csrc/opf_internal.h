@@ -65,7 +65,7 @@ struct DevSetup {
   int* hop = nullptr;
   double* luH = nullptr;
   double* luP = nullptr;
-  double* basis = nullptr;
+  double* basis = nullptr;  // device order [K][M][N][6] (host Setup: [K][M][6][N])
   double2* ainv = nullptr;
   double* G = nullptr;
   double2* tw_z = nullptr;   // e^{+2 pi i t / nz}, t < nz

@@ -1474,7 +1474,7 @@ __global__ void __launch_bounds__((SP ? 48 : 24) * T, solve_min_blocks<T, SP>())
     const double c1 = part ? ax.y : ax.x;
     const double2 w = stage ? UJ[(f * N + i) * T + mi] : a.Uj[f * fs + base + (long)i * nk + kk];
     const double* B = stage ? BS + (long)mi * 6 * N : Bv;
-    return X[i * NT + c] - cu * (part ? w.y : w.x) + c0 * B[f * N + i] + c1 * B[(3 + f) * N + i];
+    return X[i * NT + c] - cu * (part ? w.y : w.x) + c0 * B[i * 6 + f] + c1 * B[i * 6 + 3 + f];
   };
 
   // ---- fixed flux on (0,0): beta' so that 2 pi int u_z r dr = pi/2
