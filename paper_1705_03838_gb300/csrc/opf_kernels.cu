@@ -312,18 +312,18 @@ void launch_curl_split32(const Dims& d, const DevSetup& s, const double2* U, flo
                      (const float*)s.d1f, (const double*)s.r, (const double*)s.rinv, U, W6, Nlin);
 }
 
-// Threads per block of the transform kernels: 256 for grids of at most eight
-// blocks per SM (one or a few waves: more threads per batch of sequences
-// shorten each block's passes), 128 for larger grids (batched ensemble
-// groups, the N = 128 grid), which measured as fast or faster in the smaller
-// unit.  The arithmetic is the same either way.
+// Threads per block of the transform kernels: 256 for grids of at most four
+// blocks per SM (a single wave of few blocks: more threads per batch of
+// sequences shorten each block's passes), 128 for larger grids, which
+// measured as fast or faster in the smaller unit.  The arithmetic is the
+// same either way.
 static unsigned transform_threads(const dim3& g) {
   static const int sms = [] {
     int dev = 0, n = 152;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     return n > 0 ? n : 152;
   }();
-  return (long)g.x * g.y * g.z <= 8L * sms ? 256u : 128u;
+  return (long)g.x * g.y * g.z <= 4L * sms ? 256u : 128u;
 }
 
 // ------------------------------------------------------------------ z synthesis (A2)
