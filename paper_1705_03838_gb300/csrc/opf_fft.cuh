@@ -34,6 +34,34 @@ template <typename V, typename T>
 __device__ __forceinline__ V cscale(V a, T f) { return V{a.x * f, a.y * f}; }
 
 // In-place DFT of size R on v[0..R-1] with kernel e^{sign 2 pi i tq/R}.
+// Radix 8 with v[3] = v[4] = 0 (the first stage of a synthesis whose middle
+// third is the zero padding of the 3/2 rule): the same outputs as
+// butterfly<8> without the additions of the two zero inputs.
+template <typename V>
+__device__ __forceinline__ void butterfly8_zm(V* v, int sign) {
+  using T = typename Scalar<V>::T;
+  // even points (v0, v2, 0, v6)
+  const V ec = cadd(v[2], v[6]), ed = cmul_si(csub(v[2], v[6]), sign);
+  V e[4] = {cadd(v[0], ec), cadd(v[0], ed), csub(v[0], ec), csub(v[0], ed)};
+  // odd points (v1, 0, v5, v7)
+  const V oa = cadd(v[1], v[5]), ob = csub(v[1], v[5]);
+  const V od = cmul_si(V{-v[7].x, -v[7].y}, sign);
+  V o[4] = {cadd(oa, v[7]), cadd(ob, od), csub(oa, v[7]), csub(ob, od)};
+  const T h = (T)0.70710678118654752440;  // 1 / sqrt(2)
+  const T s = (T)sign;
+  const V o1 = V{h * (o[1].x - s * o[1].y), h * (o[1].y + s * o[1].x)};
+  const V o2 = cmul_si(o[2], sign);
+  const V o3 = V{-h * (o[3].x + s * o[3].y), h * (s * o[3].x - o[3].y)};
+  v[0] = cadd(e[0], o[0]);
+  v[4] = csub(e[0], o[0]);
+  v[1] = cadd(e[1], o1);
+  v[5] = csub(e[1], o1);
+  v[2] = cadd(e[2], o2);
+  v[6] = csub(e[2], o2);
+  v[3] = cadd(e[3], o3);
+  v[7] = csub(e[3], o3);
+}
+
 template <int R, typename V>
 __device__ __forceinline__ void butterfly(V* v, int sign) {
   using T = typename Scalar<V>::T;
@@ -155,9 +183,10 @@ __device__ V* block_fft(V* a, V* b, int batch, int ld, const FftPlan& p, const V
 // plain layout; the arithmetic is unchanged.
 __host__ __device__ constexpr int fft_swz(int i) { return i ^ ((i >> 3) & 7); }
 
-template <int R, int N, int NS, int SIGN, bool SWR, bool SWW, typename V>
+template <int R, int N, int NS, int SIGN, bool SWR, bool SWW, bool ZM, typename V>
 __device__ __forceinline__ void fft_stage_c(const V* __restrict__ a, V* __restrict__ b, int ld, int batch,
                                             const V* __restrict__ tw) {
+  constexpr bool zm = ZM && NS == 1 && R == 8;  // inputs 3 and 4 lie in the zero middle third
   static_assert(N % 8 == 0, "the swizzle permutes groups of eight");
   constexpr int nR = N / R, step = N / (NS * R);
   const int work = batch * nR;
@@ -172,6 +201,9 @@ __device__ __forceinline__ void fft_stage_c(const V* __restrict__ a, V* __restri
 #pragma unroll
     for (int q = 1; q < R; ++q) {
       const int ix = j + q * nR;
+      if constexpr (zm) {
+        if (q == 3 || q == 4) continue;
+      }
       if constexpr (NS == 1) {
         v[q] = src[SWR ? fft_swz(ix) : ix];
       } else {
@@ -180,7 +212,11 @@ __device__ __forceinline__ void fft_stage_c(const V* __restrict__ a, V* __restri
         v[q] = cmul(src[SWR ? fft_swz(ix) : ix], t);
       }
     }
-    butterfly<R>(v, SIGN);
+    if constexpr (zm) {
+      butterfly8_zm(v, SIGN);
+    } else {
+      butterfly<R>(v, SIGN);
+    }
     const int d0 = (j / NS) * NS * R + jm;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
@@ -190,15 +226,15 @@ __device__ __forceinline__ void fft_stage_c(const V* __restrict__ a, V* __restri
   }
 }
 
-template <int N, int NS, int SIGN, int R, int... Rest, typename V>
+template <int N, int NS, int SIGN, bool ZM, int R, int... Rest, typename V>
 __device__ __forceinline__ V* fft_stages_c(V* a, V* b, int ld, int batch, const V* tw) {
   constexpr bool last = sizeof...(Rest) == 0;
-  fft_stage_c<R, N, NS, SIGN, (NS > 1), !last>(a, b, ld, batch, tw);
+  fft_stage_c<R, N, NS, SIGN, (NS > 1), !last, ZM>(a, b, ld, batch, tw);
   __syncthreads();
   if constexpr (last) {
     return b;
   } else {
-    return fft_stages_c<N, NS * R, SIGN, Rest...>(b, a, ld, batch, tw);
+    return fft_stages_c<N, NS * R, SIGN, ZM, Rest...>(b, a, ld, batch, tw);
   }
 }
 
@@ -227,14 +263,16 @@ __host__ __device__ constexpr bool fft_length_compiled(int n) {
   return n == 48 || n == 72 || n == 96 || n == 192 || n == 384;
 }
 
-template <int N, int SIGN, typename V>
+// ZERO_MID: the inputs in the middle third, positions (N/3, 2N/3), are zero
+// (a synthesis of the 3/2 rule); the radix-8 first stages then skip them.
+template <int N, int SIGN, bool ZERO_MID = false, typename V>
 __device__ __forceinline__ V* block_fft_c(V* a, V* b, int batch, int ld, const V* tw) {
   static_assert(fft_length_compiled(N), "no compiled plan for this length");
-  if constexpr (N == 48) return fft_stages_c<48, 1, SIGN, 4, 4, 3>(a, b, ld, batch, tw);
-  else if constexpr (N == 72) return fft_stages_c<72, 1, SIGN, 8, 3, 3>(a, b, ld, batch, tw);
-  else if constexpr (N == 96) return fft_stages_c<96, 1, SIGN, 8, 4, 3>(a, b, ld, batch, tw);
-  else if constexpr (N == 192) return fft_stages_c<192, 1, SIGN, 8, 8, 3>(a, b, ld, batch, tw);
-  else return fft_stages_c<384, 1, SIGN, 8, 4, 4, 3>(a, b, ld, batch, tw);
+  if constexpr (N == 48) return fft_stages_c<48, 1, SIGN, ZERO_MID, 4, 4, 3>(a, b, ld, batch, tw);
+  else if constexpr (N == 72) return fft_stages_c<72, 1, SIGN, ZERO_MID, 8, 3, 3>(a, b, ld, batch, tw);
+  else if constexpr (N == 96) return fft_stages_c<96, 1, SIGN, ZERO_MID, 8, 4, 3>(a, b, ld, batch, tw);
+  else if constexpr (N == 192) return fft_stages_c<192, 1, SIGN, ZERO_MID, 8, 8, 3>(a, b, ld, batch, tw);
+  else return fft_stages_c<384, 1, SIGN, ZERO_MID, 8, 4, 4, 3>(a, b, ld, batch, tw);
 }
 
 // Calls f(std::integral_constant<int, n>) for a compiled length n, else

@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(256) k_zsynth(Dims d, FftPlan pz, const V* __r
       [&](int e, V v) { A[(e / nz) * ld + e % nz] = v; });
   __syncthreads();
   const V* res;
-  if constexpr (NZ > 0) res = block_fft_c<NZ, +1>(A, B, MC, ld, tw);
+  if constexpr (NZ > 0) res = block_fft_c<NZ, +1, true>(A, B, MC, ld, tw);
   else res = block_fft(A, B, MC, ld, pz, tw, +1);
   const int mcn = min(MC, d.M - m0);
   grid_dep_trigger_at(d, 2);
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(256) k_product(Dims d, FftPlan pth, const V* _
       [&](int e, V v) { A[(e / nth) * ld + e % nth] = v; });
   __syncthreads();
   V* res;
-  if constexpr (NTH > 0) res = block_fft_c<NTH, +1>(A, B, 3 * zc, ld, tw);
+  if constexpr (NTH > 0) res = block_fft_c<NTH, +1, true>(A, B, 3 * zc, ld, tw);
   else res = block_fft(A, B, 3 * zc, ld, pth, tw, +1);
   V* C = (res == A) ? B : A;
   // CFL number of this radial plane (optional): max over the grid of
@@ -733,7 +733,7 @@ __global__ void __launch_bounds__(256) k_nl_fused32(Dims d, int C, const float2*
     A[col * LDZ + z] = v;
   }
   __syncthreads();
-  V* res1 = block_fft_c<NZ, +1>(A, B, 6 * MC, LDZ, tz);
+  V* res1 = block_fft_c<NZ, +1, true>(A, B, 6 * MC, LDZ, tz);
   V* free1 = (res1 == A) ? B : A;
   cl.sync();  // every block's half-physical columns are in place
 
@@ -781,7 +781,7 @@ __global__ void __launch_bounds__(256) k_nl_fused32(Dims d, int C, const float2*
       P0[(zr * 3 + pr) * NTH + q] = v;
     }
     __syncthreads();
-    V* res = block_fft_c<NTH, +1>(P0, P1, 3 * zc, NTH, tth);
+    V* res = block_fft_c<NTH, +1, true>(P0, P1, 3 * zc, NTH, tth);
     V* Cb = (res == P0) ? P1 : P0;
     for (int e = threadIdx.x; e < zc * NTH; e += blockDim.x) {
       const int q = e % NTH, zr = e / NTH;
