@@ -139,10 +139,17 @@ void launch_internal_to_abi(const Dims& d, const double2* U, double2* abi, int, 
 }
 
 // ------------------------------------------------------------------ curl (A1)
-// A block takes kCurlKC consecutive kk of one m over all N radial points: the
-// block reads and combines each u+-, u_z value once (u_r, u_theta formed in
-// FP64) into shared memory, and the 9-point radial stencils read their
-// neighbours from there.
+// The radial columns of a trajectory -- column (m, kk), all N rows -- are
+// split into contiguous runs of whole columns, one per block (their count
+// differing by at most one between blocks).  A block stages its columns --
+// each u+-, u_z value read once, u_r and u_theta formed in FP64 -- in shared
+// memory, and the 9-point radial stencils read their neighbours from there.
+// Threads take the block's points row by row with the columns innermost, so
+// that a warp's stencil rows are shared by the lanes of one row and its
+// stores run along k.  Columns per block: on a grid of a few waves, the
+// count that puts the fewest warp-passes on the busiest SM (then the most
+// resident warps; the grid of four columns per block of a one-wave medium
+// trajectory left a third of the SMs' time idle), else four.
 //
 // SPLIT (mixed precision): the laminar base flow U = (1 - r^2) z,
 // Omega = 2r theta is removed in FP64 (W6 then holds u', w' in FP32), and the
@@ -151,25 +158,71 @@ void launch_internal_to_abi(const Dims& d, const double2* U, double2* abi, int, 
 // written to Nlin in +- form.  FP64 arithmetic is kept to what Nlin needs (the
 // u_z derivative, w_r, w_theta); the u_theta derivative feeds only w_z, which
 // goes to the FP32 product, and is taken in FP32 from an FP32 copy of the
-// u_theta tile.  Without SPLIT everything is FP64.
-constexpr int kCurlKC = 4;
+// u_theta tile.  The factor 1/2 of u_r = (u+ + u-)/2 and
+// u_theta = (u+ - u-)/(2i) goes into the constants that multiply them (exact
+// scalings by two, so the results are those of the halved values).  Without
+// SPLIT everything is FP64.
+constexpr int kCurlThreads = 128;
+
+static int device_sms() {
+  static const int sms = [] {
+    int dev = 0, n = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 152;
+  }();
+  return sms;
+}
+
+// Blocks per trajectory and the most columns one block takes.
+struct CurlShape {
+  int nbx, kc;
+};
+static CurlShape curl_shape(const Dims& d) {
+  const long sms = device_sms();
+  const long cols = (long)d.M * d.nk, B = d.B > 0 ? d.B : 1, N = d.N;
+  const long warps_max = kCurlThreads / 32;
+  long cpb = 4;
+  if ((cols + 3) / 4 * B <= 8 * sms) {
+    long best_cost = -1, best_conc = 0;
+    for (long c = 1; c <= 16 && c <= cols; ++c) {
+      const long w = (c * N + 31) / 32;  // warp-passes of a block
+      if (c * N < 32 || w > 4 * warps_max) continue;
+      const long per_sm = ((cols + c - 1) / c * B + sms - 1) / sms;
+      const long cost = per_sm * w, conc = per_sm * std::min(w, warps_max);
+      if (best_cost < 0 || cost < best_cost || (cost == best_cost && conc > best_conc)) {
+        best_cost = cost;
+        best_conc = conc;
+        cpb = c;
+      }
+    }
+  }
+  cpb = std::min(cpb, cols);
+  const long nbx = (cols + cpb - 1) / cpb;
+  return CurlShape{(int)nbx, (int)((cols + nbx - 1) / nbx)};
+}
 
 size_t curl_smem(const Dims& d) {
-  return (size_t)d.N * kCurlKC * (3 * sizeof(double2) + sizeof(float2)) + kCurlKC * sizeof(double);
+  const size_t kc = (size_t)curl_shape(d).kc, N = (size_t)d.N;
+  return N * kc * (3 * sizeof(double2) + sizeof(float2)) + kc * sizeof(double) + 2 * N * sizeof(double) +
+         2 * kc * sizeof(int);
 }
 
 // One grid point (m, kk, radial row n) of A1 from the radial column of its
 // mode: uz_at(i), ut_at(i) (FP64) and ut32_at(i) (FP32, SPLIT) give u_z and
 // u_theta at row i; ur, ut, uz are the point's own values; ak = alpha k.
-// d1 = [2][N][9] stencils, d1f = the FP32 stencils then FP32 1/r, rr and rinv
-// the radial points and their inverses (all of this trajectory).  Writes the
-// six W6 components (and, SPLIT, the FP64 linear terms Nlin in +- form).
-template <typename V, bool SPLIT, typename UzAt, typename UtAt, typename Ut32At>
+// SPLIT with SUMS: ur and ut are 2 u_r and 2 u_theta, ak is alpha k / 2, and
+// Ub, Ob are U = 1 - r^2 and Omega = 2r at the point's row (else formed
+// here from r).  d1 = [2][N][9] stencils, d1f =
+// the FP32 stencils then FP32 1/r, rr and rinv the radial points and their
+// inverses (all of this trajectory).  Writes the six W6 components (and,
+// SPLIT, the FP64 linear terms Nlin in +- form).
+template <typename V, bool SPLIT, bool SUMS = false, typename UzAt, typename UtAt, typename Ut32At>
 __device__ __forceinline__ void curl_point(const Dims& d, int m, int kk, int n, double ak,
                                            const double* __restrict__ d1, const float* __restrict__ d1f,
                                            const double* __restrict__ rr, const double* __restrict__ rinv,
                                            UzAt uz_at, UtAt ut_at, Ut32At ut32_at, double2 ur, double2 ut,
-                                           double2 uz, V* __restrict__ W6, double2* __restrict__ Nlin) {
+                                           double2 uz, V* __restrict__ W6, double2* __restrict__ Nlin,
+                                           double Ub = 0.0, double Ob = 0.0) {
   using T = typename Scalar<V>::T;
   const int N = d.N, nk = d.nk;
   const long fs = d.F;
@@ -210,7 +263,11 @@ __device__ __forceinline__ void curl_point(const Dims& d, int m, int kk, int n, 
   const long w = ((long)m * N + n) * nk + kk;
   double uzx = uz.x;
   if constexpr (SPLIT) {
-    const double r = rr[n], Ub = 1.0 - r * r, Ob = 2.0 * r;
+    if constexpr (!SUMS) {
+      const double r = rr[n];
+      Ub = 1.0 - r * r;
+      Ob = 2.0 * r;
+    }
     const bool mean = (m == 0 && kk == d.K - 1);
     if (mean) {
       uzx -= Ub;
@@ -227,11 +284,16 @@ __device__ __forceinline__ void curl_point(const Dims& d, int m, int kk, int n, 
       nminus.y -= 2.0 * Ub * d.rot_x;
     }
     Nlin[fs + w] = nminus;
-    Nlin[2 * fs + w] = double2{Ob * ur.x, Ob * ur.y};
+    if constexpr (SUMS) {
+      const double r = rr[n];  // Omega u_r = r (2 u_r)
+      Nlin[2 * fs + w] = double2{r * ur.x, r * ur.y};
+    } else {
+      Nlin[2 * fs + w] = double2{Ob * ur.x, Ob * ur.y};
+    }
     // w_z = d_r u_theta + u_theta / r - i m~ u_r / r, in FP32
     const float ri32 = d1f[2 * 9 * N + n], mri32 = (float)mt * ri32;
     const float2 ut32 = ut32_at(n);
-    const float urx = (float)ur.x, ury = (float)ur.y;
+    const float urx = SUMS ? 0.5f * (float)ur.x : (float)ur.x, ury = SUMS ? 0.5f * (float)ur.y : (float)ur.y;
     W6[0 * fs + w] = float2{urx, ury};
     W6[1 * fs + w] = ut32;
     W6[2 * fs + w] = float2{(float)uzx, (float)uz.y};
@@ -248,20 +310,24 @@ __device__ __forceinline__ void curl_point(const Dims& d, int m, int kk, int n, 
   }
 }
 
+// kc: the most columns of a block (curl_shape), the shared-memory size.
 template <typename V, bool SPLIT>
-__global__ void __launch_bounds__(128) k_curl(Dims d, const double* __restrict__ d1,
-                                              const float* __restrict__ d1f, const double* __restrict__ rr,
-                                              const double* __restrict__ rinv,
-                                              const double2* __restrict__ U, V* __restrict__ W6,
-                                              double2* __restrict__ Nlin) {
+__global__ void __launch_bounds__(kCurlThreads) k_curl(Dims d, int kc, const double* __restrict__ d1,
+                                                       const float* __restrict__ d1f, const double* __restrict__ rr,
+                                                       const double* __restrict__ rinv,
+                                                       const double2* __restrict__ U, V* __restrict__ W6,
+                                                       double2* __restrict__ Nlin) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int KC = kCurlKC;
   const int N = d.N, nk = d.nk;
-  double2* s_uz = (double2*)smraw;              // [N][KC] u_z
-  double2* s_ur = s_uz + N * KC;                // [N][KC] u_r
-  double2* s_ut = s_ur + N * KC;                // [N][KC] u_theta
-  float2* s_ut32 = (float2*)(s_ut + N * KC);    // [N][KC] u_theta in FP32 (SPLIT)
-  double* s_ak = (double*)(s_ut32 + N * KC);    // [KC] alpha k of the block's columns
+  double2* s_uz = (double2*)smraw;            // [N][ncb] u_z
+  double2* s_ur = s_uz + N * kc;              // [N][ncb] u_r (SPLIT: 2 u_r)
+  double2* s_ut = s_ur + N * kc;              // [N][ncb] u_theta (SPLIT: 2 u_theta)
+  float2* s_ut32 = (float2*)(s_ut + N * kc);  // [N][ncb] u_theta in FP32 (SPLIT)
+  double* s_ak = (double*)(s_ut32 + N * kc);  // [ncb] alpha k of the columns (SPLIT: alpha k / 2)
+  double* s_ub = s_ak + kc;                   // [N] U = 1 - r^2 (SPLIT)
+  double* s_ob = s_ub + N;                    // [N] Omega = 2r (SPLIT)
+  int* s_m = (int*)(s_ob + N);                // [ncb] m of the columns
+  int* s_kk = s_m + kc;                       // [ncb] kk of the columns
   d1 = bofs(d1, d.ps);
   d1f = bofs(d1f, d.ps);
   rr = bofs(rr, d.ps);
@@ -269,47 +335,67 @@ __global__ void __launch_bounds__(128) k_curl(Dims d, const double* __restrict__
   U = bofs(U, d.ss);
   W6 = bofs(W6, d.ss);
   Nlin = bofs(Nlin, d.ss);
-  const int m = blockIdx.y, kk0 = blockIdx.x * KC;
-  const long fs = d.F;
-  const double2* up = U + (long)m * N * nk;
+  const long fs = d.F, cols = (long)d.M * nk;
+  const int col0 = (int)((long)blockIdx.x * cols / gridDim.x);
+  const int ncb = (int)((long)(blockIdx.x + 1) * cols / gridDim.x) - col0;  // this block's columns, <= kc
   grid_dep_trigger_at(d, 1);
-  if (threadIdx.x < KC) s_ak[threadIdx.x] = d.alpha * (kk0 + (int)threadIdx.x - (d.K - 1));
+  if (ncb <= 0) return;
+  for (int c = threadIdx.x; c < ncb; c += blockDim.x) {
+    const int col = col0 + c, m = col / nk, kk = col - m * nk;
+    s_m[c] = m;
+    s_kk[c] = kk;
+    const double ak = d.alpha * (kk - (d.K - 1));
+    s_ak[c] = SPLIT ? 0.5 * ak : ak;
+  }
+  if constexpr (SPLIT)
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+      const double r = rr[n];
+      s_ub[n] = 1.0 - r * r;
+      s_ob[n] = 2.0 * r;
+    }
+  __syncthreads();
   grid_dep_wait();
-  for (int e = threadIdx.x; e < N * KC; e += blockDim.x) {
-    const int c = e % KC, n = e / KC, kk = kk0 + c;
-    if (kk >= nk) continue;  // columns past nk are never read
-    const long o = (long)n * nk + kk;
-    const double2 a = up[o], b = up[fs + o];
-    s_uz[e] = up[2 * fs + o];
-    s_ur[e] = double2{0.5 * (a.x + b.x), 0.5 * (a.y + b.y)};
-    const double2 ut = double2{0.5 * (a.y - b.y), -0.5 * (a.x - b.x)};
-    s_ut[e] = ut;
-    if constexpr (SPLIT) s_ut32[e] = float2{(float)ut.x, (float)ut.y};
+  for (int e = threadIdx.x; e < N * ncb; e += blockDim.x) {
+    const int n = e / ncb, c = e - n * ncb;
+    const long o = ((long)s_m[c] * N + n) * nk + s_kk[c];
+    const double2 a = U[o], b = U[fs + o];
+    s_uz[e] = U[2 * fs + o];
+    if constexpr (SPLIT) {
+      const double2 ut2 = double2{a.y - b.y, b.x - a.x};
+      s_ur[e] = double2{a.x + b.x, a.y + b.y};
+      s_ut[e] = ut2;
+      s_ut32[e] = float2{0.5f * (float)ut2.x, 0.5f * (float)ut2.y};
+    } else {
+      s_ur[e] = double2{0.5 * (a.x + b.x), 0.5 * (a.y + b.y)};
+      s_ut[e] = double2{0.5 * (a.y - b.y), -0.5 * (a.x - b.x)};
+    }
   }
   __syncthreads();
   grid_dep_trigger_at(d, 2);
-  for (int e = threadIdx.x; e < N * KC; e += blockDim.x) {
-    const int c = e % KC, n = e / KC, kk = kk0 + c;
-    if (kk >= nk) continue;
-    curl_point<V, SPLIT>(
-        d, m, kk, n, s_ak[c], d1, d1f, rr, rinv, [&](int i) { return s_uz[i * KC + c]; },
-        [&](int i) { return s_ut[i * KC + c]; }, [&](int i) { return s_ut32[i * KC + c]; }, s_ur[e], s_ut[e],
-        s_uz[e], W6, Nlin);
+  for (int e = threadIdx.x; e < N * ncb; e += blockDim.x) {
+    const int n = e / ncb, c = e - n * ncb;
+    const double2 *cz = s_uz + c, *ct = s_ut + c;
+    const float2* ct32 = s_ut32 + c;
+    curl_point<V, SPLIT, true>(
+        d, s_m[c], s_kk[c], n, s_ak[c], d1, d1f, rr, rinv, [=](int i) { return cz[i * ncb]; },
+        [=](int i) { return ct[i * ncb]; }, [=](int i) { return ct32[i * ncb]; }, s_ur[e], s_ut[e], s_uz[e], W6,
+        Nlin, SPLIT ? s_ub[n] : 0.0, SPLIT ? s_ob[n] : 0.0);
   }
 }
 
 void launch_curl(const Dims& d, const DevSetup& s, const double2* U, double2* W6, cudaStream_t st) {
-  dim3 g((unsigned)((d.nk + kCurlKC - 1) / kCurlKC), d.M, d.B);
-  launch_step_kernel(d, k_curl<double2, false>, g, dim3(128), curl_smem(d), st, d, (const double*)s.d1,
-                     (const float*)nullptr, (const double*)nullptr, (const double*)s.rinv, U, W6,
-                     (double2*)nullptr);
+  const CurlShape c = curl_shape(d);
+  launch_step_kernel(d, k_curl<double2, false>, dim3(c.nbx, 1, d.B), dim3(kCurlThreads), curl_smem(d), st, d,
+                     c.kc, (const double*)s.d1, (const float*)nullptr, (const double*)nullptr,
+                     (const double*)s.rinv, U, W6, (double2*)nullptr);
 }
 
 void launch_curl_split32(const Dims& d, const DevSetup& s, const double2* U, float2* W6,
                          double2* Nlin, cudaStream_t st) {
-  dim3 g((unsigned)((d.nk + kCurlKC - 1) / kCurlKC), d.M, d.B);
-  launch_step_kernel(d, k_curl<float2, true>, g, dim3(128), curl_smem(d), st, d, (const double*)s.d1,
-                     (const float*)s.d1f, (const double*)s.r, (const double*)s.rinv, U, W6, Nlin);
+  const CurlShape c = curl_shape(d);
+  launch_step_kernel(d, k_curl<float2, true>, dim3(c.nbx, 1, d.B), dim3(kCurlThreads), curl_smem(d), st, d,
+                     c.kc, (const double*)s.d1, (const float*)s.d1f, (const double*)s.r,
+                     (const double*)s.rinv, U, W6, Nlin);
 }
 
 // Threads per block of the transform kernels: 256 for grids of at most four
@@ -318,12 +404,7 @@ void launch_curl_split32(const Dims& d, const DevSetup& s, const double2* U, flo
 // measured as fast or faster in the smaller unit.  The arithmetic is the
 // same either way.
 static unsigned transform_threads(const dim3& g) {
-  static const int sms = [] {
-    int dev = 0, n = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    return n > 0 ? n : 152;
-  }();
-  return (long)g.x * g.y * g.z <= 4L * sms ? 256u : 128u;
+  return (long)g.x * g.y * g.z <= 4L * device_sms() ? 256u : 128u;
 }
 
 // ------------------------------------------------------------------ z synthesis (A2)
@@ -1512,7 +1593,11 @@ __global__ void __launch_bounds__((SP ? 48 : 24) * T, solve_min_blocks<T, SP>())
 
   // ---- the curl of the new state (A1) for the next nonlinear evaluation, from
   //      the block's radial columns (S and P are free: u_r, u_theta; the FP32
-  //      u_theta of the mixed-precision curl sits in the tail of shared memory)
+  //      u_theta of the mixed-precision curl sits in the tail of shared memory).
+  //      The mixed-precision form (curl 2) is built into the 4-mode tile only:
+  //      the library's steps take it from k_curl, and in the larger tiles its
+  //      code made the solve spill more registers.
+  constexpr bool kMixedCurl = T == 4;
   if (a.curl) {
     __syncthreads();
     double2* UR = S;
@@ -1524,7 +1609,7 @@ __global__ void __launch_bounds__((SP ? 48 : 24) * T, solve_min_blocks<T, SP>())
       const double2 ut = double2{0.5 * (up.y - um.y), -0.5 * (up.x - um.x)};
       UR[i * T + mi_t] = double2{0.5 * (up.x + um.x), 0.5 * (up.y + um.y)};
       UT[i * T + mi_t] = ut;
-      if (a.curl == 2) UT32[i * T + mi_t] = float2{(float)ut.x, (float)ut.y};  // (allocated for curl 2 only)
+      if (kMixedCurl && a.curl == 2) UT32[i * T + mi_t] = float2{(float)ut.x, (float)ut.y};  // (curl 2 only)
     }
     __syncthreads();
     const int kk = kk0 + mi_t;
@@ -1533,7 +1618,7 @@ __global__ void __launch_bounds__((SP ? 48 : 24) * T, solve_min_blocks<T, SP>())
       auto ut_at = [&](int i) { return UT[i * T + mi_t]; };
       auto ut32_at = [&](int i) { return UT32[i * T + mi_t]; };
       for (int i = tid / T; i < N; i += NB / T) {
-        if (a.curl == 2)
+        if (kMixedCurl && a.curl == 2)
           curl_point<float2, true>(d, m, kk, i, ak_t, W1, s.d1f, s.r, RI, uz_at, ut_at, ut32_at, UR[i * T + mi_t],
                                    UT[i * T + mi_t], uz_at(i), (float2*)a.W6, a.Nlin);
         else
