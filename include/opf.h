@@ -18,7 +18,8 @@
  *
  * ERRORS: every int-returning call returns OPF_OK (0) or a negative code; the
  * reason is available from opf_last_error() (thread-local, library-owned
- * string, valid until the next failing call on the same thread).
+ * string, valid until the next failing call or state load on the same
+ * thread).
  * Buffers passed in are owned by the caller and only read/written during the
  * call.  Calls on one handle must not overlap; different handles are
  * independent.  All compute runs on the CUDA device current at opf_create.
@@ -61,11 +62,16 @@ opf_t* opf_create_mesh(int N, int K, int M, int m_p, double alpha, double Re, do
 /* Release the handle and its device memory.  NULL is ignored. */
 void opf_destroy(opf_t* h);
 
-/* Reason for the last failing call on this thread ("" if none). */
+/* Reason for the last failing call on this thread ("" if none); after a
+ * successful opf_set_state family call, "" or that call's note. */
 const char* opf_last_error(void);
 
 /* Load a state from a host buffer (layout above).  The m = 0 coefficients are
- * projected onto Hermitian symmetry A(-k,0) = conj A(k,0) (real fields).
+ * projected onto Hermitian symmetry A(-k,0) = conj A(k,0) (real fields,
+ * section 2).  On success opf_last_error() is "" unless the buffer's m = 0
+ * coefficients were not Hermitian to 1e-12 of the largest of them (parts
+ * compared separately): then it holds a note with that relative asymmetry,
+ * and the call still returns OPF_OK with the projected state loaded.
  * OPF_ENAN if the buffer holds a NaN/Inf (the previous state is kept). */
 int opf_set_state(opf_t* h, const double* coeffs);
 

@@ -887,7 +887,36 @@ int runner_times(Runner* r, int cap, int* count, const char** names, double* tot
 }
 
 // ---- per-trajectory state transfer and diagnostics
-int traj_state_from_abi(Group* g, int b, cudaStream_t st);
+int traj_state_from_abi(Group* g, int b, cudaStream_t st, bool note = true);
+
+// The words a set_state reads back from the trajectory's flag slot: a
+// non-finite coefficient was seen; the m = 0 asymmetry and magnitude maxima of
+// the layout conversion (upper 32 bits of non-negative doubles).
+struct SetFlags {
+  int nan;
+  unsigned asym_hi, amp_hi;
+};
+
+// Leaves a note for opf_last_error() when the m = 0 coefficients were not
+// Hermitian to 1e-12 of the largest of them (the state is projected all the
+// same, section 2: the fields are real).
+void note_asymmetry(const SetFlags& f) {
+  auto value = [](unsigned hi) {
+    const unsigned long long bits = (unsigned long long)hi << 32;
+    double v;
+    std::memcpy(&v, &bits, sizeof v);
+    return v;
+  };
+  const double asym = value(f.asym_hi), amp = value(f.amp_hi);
+  if (asym > 1e-12 * amp) {
+    char msg[160];
+    std::snprintf(msg, sizeof msg,
+                  "set_state: m = 0 coefficients not Hermitian (max |A(k,0) - conj A(-k,0)| = %.3g of the "
+                  "largest); projected",
+                  asym / amp);
+    opf::set_last_error(msg);
+  }
+}
 
 int traj_set_state_device(Group* g, int b, const double* d_coeffs, cudaStream_t st) {
   const size_t bytes = 3 * (size_t)g->d.F * sizeof(double2);
@@ -898,18 +927,21 @@ int traj_set_state_device(Group* g, int b, const double* d_coeffs, cudaStream_t 
 // The trajectory's staging copy (abi) into its state: a NaN check, then the
 // layout conversion (with the Hermitian projection and beta reset), which
 // the device skips when the check found a non-finite value -- so the state
-// is unchanged on OPF_ENAN -- and one synchronisation for both.
-int traj_state_from_abi(Group* g, int b, cudaStream_t st) {
+// is unchanged on OPF_ENAN -- and one synchronisation for both.  note: leave
+// the m = 0 asymmetry note (note_asymmetry) where there is one.
+int traj_state_from_abi(Group* g, int b, cudaStream_t st, bool note) {
   const opf::Dims d = g->single(b);
   double2* abi = g->at(g->abi, b);
   int* flag = g->at(g->flag, b);
   opf::launch_nan_check((const double*)abi, 6 * d.F, flag, st);
-  opf::launch_abi_to_internal(d, abi, g->at(g->U, b), st, flag, g->at(g->beta_p, b));
-  int h_flag = 0;
-  CU(cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemsetAsync(flag + 1, 0, 2 * sizeof(unsigned), st));
+  opf::launch_abi_to_internal(d, abi, g->at(g->U, b), st, flag, g->at(g->beta_p, b), nullptr, (unsigned*)(flag + 1));
+  SetFlags hf{};
+  CU(cudaMemcpyAsync(&hf, flag, sizeof hf, cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   CU(cudaGetLastError());
-  if (h_flag) return fail(OPF_ENAN, "set_state: non-finite coefficient; state unchanged");
+  if (hf.nan) return fail(OPF_ENAN, "set_state: non-finite coefficient; state unchanged");
+  if (note) note_asymmetry(hf);
   g->w6_valid = false;
   return OPF_OK;
 }
@@ -926,7 +958,7 @@ const void* device_view(const void* host) {
   return (a.type == cudaMemoryTypeHost && a.devicePointer) ? a.devicePointer : nullptr;
 }
 
-int traj_set_state_host(Group* g, int b, const double* coeffs, cudaStream_t st) {
+int traj_set_state_host(Group* g, int b, const double* coeffs, cudaStream_t st, bool note = true) {
   const opf::Dims d = g->single(b);
   if (const void* dv = device_view(coeffs)) {
     // pinned: the conversion reads the buffer itself (one pass, with the NaN
@@ -934,19 +966,20 @@ int traj_set_state_host(Group* g, int b, const double* coeffs, cudaStream_t st) 
     // finite; one synchronisation
     int* flag = g->at(g->flag, b);
     double2* tmp = g->at(g->tmpU, b);
-    CU(cudaMemsetAsync(flag, 0, sizeof(int), st));
-    opf::launch_abi_to_internal(d, (const double2*)dv, tmp, st, nullptr, nullptr, flag);
+    CU(cudaMemsetAsync(flag, 0, sizeof(SetFlags), st));
+    opf::launch_abi_to_internal(d, (const double2*)dv, tmp, st, nullptr, nullptr, flag, (unsigned*)(flag + 1));
     opf::launch_copy_unless(tmp, g->at(g->U, b), 3 * (long)d.F, flag, g->at(g->beta_p, b), st);
-    int h_flag = 0;
-    CU(cudaMemcpyAsync(&h_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SetFlags hf{};
+    CU(cudaMemcpyAsync(&hf, flag, sizeof hf, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     CU(cudaGetLastError());
-    if (h_flag) return fail(OPF_ENAN, "set_state: non-finite coefficient; state unchanged");
+    if (hf.nan) return fail(OPF_ENAN, "set_state: non-finite coefficient; state unchanged");
+    if (note) note_asymmetry(hf);
     g->w6_valid = false;
     return OPF_OK;
   }
   CU(cudaMemcpyAsync(g->at(g->abi, b), coeffs, 3 * (size_t)d.F * sizeof(double2), cudaMemcpyHostToDevice, st));
-  return traj_state_from_abi(g, b, st);
+  return traj_state_from_abi(g, b, st, note);
 }
 
 int traj_get_state(Group* g, int b, double* out, bool host, cudaStream_t st) {
@@ -1066,12 +1099,14 @@ int opf_set_forcing(opf_t* h, const double* coeffs) {
 int opf_set_state_device(opf_t* h, const double* d_coeffs) {
   if (check_handle(h)) return OPF_EINVAL;
   if (!d_coeffs) return fail(OPF_EINVAL, "opf_set_state: NULL buffer");
+  g_err.clear();
   return traj_set_state_device(&h->g, 0, d_coeffs, h->run.stream);
 }
 
 int opf_set_state(opf_t* h, const double* coeffs) {
   if (check_handle(h)) return OPF_EINVAL;
   if (!coeffs) return fail(OPF_EINVAL, "opf_set_state: NULL buffer");
+  g_err.clear();
   return traj_set_state_host(&h->g, 0, coeffs, h->run.stream);
 }
 
@@ -1282,6 +1317,7 @@ int opf_ens_set_state(opf_ens_t* e, int i, const double* coeffs) {
   int b;
   if (ens_traj(e, i, &g, &b)) return OPF_EINVAL;
   if (!coeffs) return fail(OPF_EINVAL, "opf_ens_set_state: NULL buffer");
+  g_err.clear();
   return traj_set_state_host(g, b, coeffs, e->run.stream);
 }
 
@@ -1298,6 +1334,7 @@ int opf_ens_set_state_device(opf_ens_t* e, int i, const double* d_coeffs) {
   int b;
   if (ens_traj(e, i, &g, &b)) return OPF_EINVAL;
   if (!d_coeffs) return fail(OPF_EINVAL, "opf_ens_set_state_device: NULL buffer");
+  g_err.clear();
   return traj_set_state_device(g, b, d_coeffs, e->run.stream);
 }
 
@@ -1521,7 +1558,7 @@ int nk_set_periods(NkCtx* c, const int* idx, int cnt, const double* Ts) {
 // steps; states in/out as interleaved complex host arrays
 int nk_integrate(NkCtx* c, int cnt, const int* idx, std::vector<std::vector<double>>& states, int steps) {
   for (int j = 0; j < cnt; ++j) {
-    int rc = traj_set_state_host(&c->g, idx[j], states[j].data(), c->run.stream);
+    int rc = traj_set_state_host(&c->g, idx[j], states[j].data(), c->run.stream, false);
     if (rc) return rc;
   }
   int rc = runner_step(&c->run, steps);

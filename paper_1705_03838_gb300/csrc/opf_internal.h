@@ -125,9 +125,11 @@ void set_last_error(const std::string& m);  // text returned by opf_last_error()
 
 // Launch wrappers (kernels live in opf_kernels.cu).
 // (flag: skip the conversion where the NaN check before it set *flag; beta: reset to 0;
-// nan_out: set where a coefficient read is not finite)
+// nan_out: set where a coefficient read is not finite; herm: two words, zeroed by the
+// caller, that receive the m = 0 asymmetry and magnitude maxima)
 void launch_abi_to_internal(const Dims& d, const double2* abi, double2* U, cudaStream_t st,
-                            const int* flag = nullptr, double* beta = nullptr, int* nan_out = nullptr);
+                            const int* flag = nullptr, double* beta = nullptr, int* nan_out = nullptr,
+                            unsigned* herm = nullptr);
 void launch_copy_unless(const double2* src, double2* dst, long n, const int* flag, double* beta,
                         cudaStream_t st);
 void launch_internal_to_abi(const Dims& d, const double2* U, double2* abi, int components_rtz,

@@ -68,8 +68,14 @@ __device__ __forceinline__ P* bofs(P* p, long stride) {
 // before) leaves U as it is; beta (optional) is reset to 0 otherwise.
 // nan_out (optional): set to 1 if any coefficient read is not finite (every
 // coefficient is read by the thread of its own (m, k, n)).
+// herm (optional, zeroed by the caller): herm[0], herm[1] become the upper 32
+// bits of max |A(k,0) - conj A(-k,0)| and of max |A(k,0)| over the m = 0
+// coefficients (real and imaginary parts separately, all three components):
+// the upper word of a non-negative double orders like the double, and keeps
+// it to 2^-20 relative.
 __global__ void k_abi_to_internal(Dims d, const double2* __restrict__ abi, double2* __restrict__ U,
-                                  const int* __restrict__ flag, double* __restrict__ beta, int* nan_out) {
+                                  const int* __restrict__ flag, double* __restrict__ beta, int* nan_out,
+                                  unsigned* herm) {
   if (flag && *flag) return;
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (beta && idx == 0) *beta = 0.0;
@@ -87,6 +93,20 @@ __global__ void k_abi_to_internal(Dims d, const double2* __restrict__ abi, doubl
   if (m == 0) {  // Hermitian projection A(-k,0) = conj A(k,0)
     const int kq = d.nk - 1 - kk;
     const double2 vr = ld(0, kq), vt = ld(1, kq), vz = ld(2, kq);
+    if (herm) {
+      const double asym = fmax(fmax(fmax(fabs(ur.x - vr.x), fabs(ur.y + vr.y)),
+                                    fmax(fabs(ut.x - vt.x), fabs(ut.y + vt.y))),
+                               fmax(fabs(uz.x - vz.x), fabs(uz.y + vz.y)));
+      const double amp = fmax(fmax(fmax(fabs(ur.x), fabs(ur.y)), fmax(fabs(ut.x), fabs(ut.y))),
+                              fmax(fabs(uz.x), fabs(uz.y)));
+      const unsigned lanes = __activemask();
+      const unsigned ha = __reduce_max_sync(lanes, (unsigned)(__double_as_longlong(asym) >> 32));
+      const unsigned hm = __reduce_max_sync(lanes, (unsigned)(__double_as_longlong(amp) >> 32));
+      if ((int)(threadIdx.x & 31) == __ffs(lanes) - 1) {
+        atomicMax(herm, ha);
+        atomicMax(herm + 1, hm);
+      }
+    }
     ur = double2{0.5 * (ur.x + vr.x), 0.5 * (ur.y - vr.y)};
     ut = double2{0.5 * (ut.x + vt.x), 0.5 * (ut.y - vt.y)};
     uz = double2{0.5 * (uz.x + vz.x), 0.5 * (uz.y - vz.y)};
@@ -114,9 +134,9 @@ __global__ void k_internal_to_abi(Dims d, const double2* __restrict__ U, double2
 }
 
 void launch_abi_to_internal(const Dims& d, const double2* abi, double2* U, cudaStream_t st, const int* flag,
-                            double* beta, int* nan_out) {
+                            double* beta, int* nan_out, unsigned* herm) {
   const int nb = (int)((d.F + 255) / 256);
-  k_abi_to_internal<<<nb, 256, 0, st>>>(d, abi, U, flag, beta, nan_out);
+  k_abi_to_internal<<<nb, 256, 0, st>>>(d, abi, U, flag, beta, nan_out, herm);
 }
 
 // dst = src (n double2) unless *flag is set; beta reset to 0 with it

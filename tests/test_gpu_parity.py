@@ -6,6 +6,7 @@ held to ~1e-12 (differences are round-off only: banded pivot-free LU with
 influence matrices vs dense pivoted LU of the coupled system, FFT ordering).
 """
 import functools
+import re
 
 import numpy as np
 import pytest
@@ -116,13 +117,25 @@ def test_state_round_trip_and_hermitian_projection(opf):
     h = opf.opf_create(N, K, M, 1, 1.25, 100.0, 0.01)
     U0 = inputs.seeded_state(N, K, M, 1, 1.25, 0.1, 3)
     opf.opf_set_state(h, U0)
+    assert opf.lib().opf_last_error() == b""  # the seeded m = 0 part is Hermitian
     # u+- = u_r +- i u_theta and back: exact up to one rounding
     assert np.abs(opf.opf_get_state(h) - U0).max() <= 4e-16 * np.abs(U0).max()
     V = U0.copy()
     V[:, 0, K] += 1e-3 * (1 + 1j)  # break symmetry
     opf.opf_set_state(h, V)
+    note = opf.lib().opf_last_error().decode()
+    assert "not Hermitian" in note
+    # the reported asymmetry: max |A(k,0) - conj A(-k,0)| over parts, relative
+    # to the largest m = 0 part, to the 2^-20 of its reduction
+    d = V[:, 0] - np.conj(V[:, 0, ::-1])
+    want = max(np.abs(d.real).max(), np.abs(d.imag).max()) / max(
+        np.abs(V[:, 0].real).max(), np.abs(V[:, 0].imag).max())
+    got = float(re.search(r"\| = ([0-9.eE+-]+) of the largest", note).group(1))
+    assert abs(got - want) <= 1e-2 * want
     W = opf.opf_get_state(h)
     assert np.abs(W[:, 0] - Oracle.hermitian_project(V)[:, 0]).max() <= 4e-16 * np.abs(V).max()
+    opf.opf_set_state(h, W)  # the projected state is Hermitian: no note
+    assert opf.lib().opf_last_error() == b""
 
 
 def test_nan_state_is_rejected_and_previous_kept(opf):

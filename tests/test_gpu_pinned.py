@@ -36,8 +36,11 @@ def test_pinned_set_and_get_equal_the_copy_path(opf):
     a = opf.opf_create(N, K, M, m_p, 1.25, 1000.0, 0.01)
     b = opf.opf_create(N, K, M, m_p, 1.25, 1000.0, 0.01)
     opf.opf_set_state(a, U)  # pageable: copy path
+    note = opf.lib().opf_last_error()
+    assert b"not Hermitian" in note
     pin = pinned_copy(U)
     assert opf.lib().opf_set_state(b.ptr, ctypes.c_void_p(pin.data_ptr())) == 0  # pinned: read in place
+    assert opf.lib().opf_last_error() == note  # the same asymmetry note
     ref = opf.opf_get_state(a)
     out = torch.empty_like(pin).pin_memory()
     assert opf.lib().opf_get_state(b.ptr, ctypes.c_void_p(out.data_ptr())) == 0  # pinned: written in place
