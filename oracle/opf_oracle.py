@@ -38,7 +38,6 @@ Readings of points the paper leaves open (each is a choice, stated here):
   R7 quadrature: int_0^1 f r dr by integrating the 9-point interpolant of
      r f over each interval [r_(n-1), r_n] (r_0 = 0) with row n's stencil.
 """
-import math
 
 import numpy as np
 import scipy.linalg as sla
