@@ -1861,7 +1861,8 @@ int ms_residual(void* vctx, int cnt, const int* idx, double* const* x, double* c
   return OPF_OK;
 }
 
-int ms_jv(void* vctx, int cnt, const int* idx, double* const* x, double* const* v, double* const* jv) {
+int ms_jv(void* vctx, int cnt, const int* idx, double* const* /*x: the base points, held in the context*/,
+          double* const* v, double* const* jv) {
   MsCtx* m = (MsCtx*)vctx;
   NkCtx* c = m->c;
   const int S = m->S;

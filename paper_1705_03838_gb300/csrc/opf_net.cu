@@ -29,10 +29,8 @@ namespace {
 using bf16 = __nv_bfloat16;
 
 // ------------------------------------------------------------------ operand layouts
-__device__ __forceinline__ float gelu_f(float x) {
-  return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
-}
-
+// d/dx of gelu(x) = x Phi(x): Phi(x) + x phi(x) (the forward GELU is applied
+// in the GEMM epilogue)
 __device__ __forceinline__ float gelu_grad(float x) {
   const float cdf = 0.5f * (1.0f + erff(x * 0.70710678118654752f));
   const float pdf = 0.39894228040143268f * expf(-0.5f * x * x);
