@@ -406,8 +406,15 @@ int opf_change_resolution(int N1, int K1, int M1, const double* in, int N2, int 
  * sum wq f ~ int_0^1 f r dr for even f), "d1" / "d2" ([2][N][9] first/second
  * derivative stencils, [0] = even axis parity, [1] = odd, row n against
  * columns clamp(n-4, 0, N-9) + t), "G" (N, fixed-flux response),
- * "basis" ([K][M][6][N] influence-matrix responses).  *len receives the
- * full length; OPF_EINVAL if cap is too small or what is unknown. */
+ * "basis" ([K][M][6][N] influence-matrix responses), "luH" / "luP" (the
+ * banded LU factors as the device reads them, 13 N values per operator:
+ * [N][4] L(c+1+t, c), [N][4] L(c+5+t, c), [N] 1/U(c,c),
+ * [N][4] U(c-1-t, c) / U(c-1-t, c-1-t), unit-lower L, zeros outside the
+ * band; luH is [K][nJ] Helmholtz operators 1/dt - c L_j with the Dirichlet
+ * wall row, luP is [K][M] pressure operators with the Neumann wall row plus
+ * (0,0) with p(1) = 0 last), "hop" ([M][3] the index j' < nJ of the
+ * Helmholtz operator of u+, u-, u_z at each m; section 2.2).  *len receives
+ * the full length; OPF_EINVAL if cap is too small or what is unknown. */
 int opf_setup_query(int N, int K, int M, int m_p, double alpha, double Re, double dt,
                     const char* what, double* out, long cap, long* len);
 /* Same, on a user radial mesh r (N points as for opf_create_mesh; NULL = the

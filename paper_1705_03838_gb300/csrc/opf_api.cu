@@ -1410,12 +1410,16 @@ int opf_setup_query_mesh(int N, int K, int M, int m_p, double alpha, double Re, 
   std::string err;
   if (!opf::build_setup(&s, &err)) return fail(OPF_EINVAL, "opf_setup_query: " + err);
   const std::vector<double>* v = nullptr;
+  std::vector<double> hop(s.hop.begin(), s.hop.end());
   if (!strcmp(what, "r")) v = &s.r;
   else if (!strcmp(what, "wq")) v = &s.wq;
   else if (!strcmp(what, "d1")) v = &s.d1;
   else if (!strcmp(what, "d2")) v = &s.d2;
   else if (!strcmp(what, "G")) v = &s.G;
   else if (!strcmp(what, "basis")) v = &s.basis;
+  else if (!strcmp(what, "luH")) v = &s.luH;
+  else if (!strcmp(what, "luP")) v = &s.luP;
+  else if (!strcmp(what, "hop")) v = &hop;
   else return fail(OPF_EINVAL, std::string("opf_setup_query: unknown array ") + what);
   *len = (long)v->size();
   if (!out) return OPF_OK;

@@ -97,3 +97,81 @@ def test_flux_response_is_positive_and_vanishes_at_wall(opf):
 def test_setup_rejects_unfactorable_sizes(opf):
     with pytest.raises(opf.OpfError):
         opf.opf_setup_query(4, 4, 4, 1, 1.25, 100.0, 0.01, "r")
+
+
+def column_substitution(F, b):
+    """The banded substitution in the order the solve kernel takes it: column
+    by column, on one operator's factors in the device layout (13 N values:
+    L(c+1+t, c), L(c+5+t, c) read in the last nine columns only, 1/U(c,c),
+    U(c-1-t, c) / U(c-1-t, c-1-t))."""
+    N = len(b)
+    L, Lw = F[:4 * N].reshape(N, 4), F[4 * N:8 * N].reshape(N, 4)
+    dg, Uc = F[8 * N:9 * N], F[9 * N:].reshape(N, 4)
+    x = np.array(b, dtype=np.float64)
+    for c in range(N):
+        for t in range(4):
+            if c + 1 + t < N:
+                x[c + 1 + t] -= L[c, t] * x[c]
+            if c >= N - 9 and c + 5 + t < N:
+                x[c + 5 + t] -= Lw[c, t] * x[c]
+    x *= dg
+    for c in range(N - 1, -1, -1):
+        for t in range(4):
+            if c - 1 - t >= 0:
+                x[c - 1 - t] -= Uc[c, t] * x[c]
+    return x
+
+
+@pytest.mark.parametrize("N,K,M,m_p", [(16, 3, 3, 1), (33, 2, 4, 2), (48, 2, 3, 2)])
+def test_device_factors_solve_the_oracle_operators(opf, N, K, M, m_p):
+    """The factors the solve kernel reads (host LU, stored by columns) solve
+    the radial operators of section 2.2 as the oracle builds them from its
+    own stencils: H_j = 1/dt - c (1/Re)(D2 + D1/r - j^2/r^2 - (alpha k)^2)
+    with the Dirichlet wall row, j = m~+1, |m~-1|, m~ for u+, u-, u_z; the
+    pressure operator D2 + D1/r - m~^2/r^2 - (alpha k)^2 with the Neumann
+    wall row (the (0,0) one with p(1) = 0).  Right-hand sides end in 0 (the
+    wall condition), so the check does not depend on how a wall row is
+    scaled; normwise backward error against the oracle's matrices."""
+    alpha, Re, dt, c = 1.25, 400.0, 0.01, 0.5
+    q = lambda what: opf.opf_setup_query(N, K, M, m_p, alpha, Re, dt, what)  # noqa: E731
+    luH, luP = q("luH"), q("luP").reshape(K * M + 1, 13 * N)
+    hop = q("hop").astype(int).reshape(M, 3)
+    nJ = luH.size // (K * 13 * N)
+    luH = luH.reshape(K, nJ, 13 * N)
+    r = mesh(N)
+    mats = {1: fd_matrices(r, 1), -1: fd_matrices(r, -1)}
+    rng = np.random.default_rng(11)
+
+    def lap(j, ak, par):
+        D1, D2 = mats[par]
+        return D2 + D1 / r[:, None] - np.diag(j * j / r ** 2 + ak * ak)
+
+    def check(A, F):
+        b = rng.standard_normal(N)
+        b[-1] = 0.0
+        x = column_substitution(F, b)
+        res = np.abs(A @ x - b).max()
+        assert res <= 1e-13 * (np.abs(A).sum(axis=1).max() * np.abs(x).max() + np.abs(b).max())
+
+    for ik in range(K):
+        ak = alpha * ik
+        for m in range(M):
+            mt = m_p * m
+            for f, j in enumerate((mt + 1, abs(mt - 1), mt)):
+                H = np.eye(N) / dt - c / Re * lap(j, ak, 1 if j % 2 == 0 else -1)
+                H[-1] = 0.0
+                H[-1, -1] = 1.0
+                check(H, luH[ik, hop[m, f]])
+            par = 1 if mt % 2 == 0 else -1
+            P = lap(mt, ak, par)
+            if ik == 0 and m == 0:
+                P[-1] = 0.0
+                P[-1, -1] = 1.0
+                check(P, luP[K * M])
+            else:
+                P[-1] = mats[par][0][-1]
+                check(P, luP[ik * M + m])
+    # the eight-wide lower band lies in the last nine columns only, where the
+    # kernel reads it
+    for F in list(luH.reshape(-1, 13 * N)) + list(luP):
+        assert not np.any(F[4 * N:4 * N + 4 * max(N - 9, 0)])
