@@ -175,3 +175,58 @@ def test_device_factors_solve_the_oracle_operators(opf, N, K, M, m_p):
     # kernel reads it
     for F in list(luH.reshape(-1, 13 * N)) + list(luP):
         assert not np.any(F[4 * N:4 * N + 4 * max(N - 9, 0)])
+
+
+@pytest.mark.parametrize("N,K,M,m_p", [(16, 3, 3, 1), (33, 2, 4, 2)])
+def test_influence_responses_match_the_oracle_operators(opf, N, K, M, m_p):
+    """The influence-matrix data of section 2 built by the host, against the
+    oracle's operators: per (|k|, m) != (0,0) the pressure p1 with unit wall
+    derivative (laplacian 0 inside), the velocity responses to -grad p1
+    ((grad p)+- = p' -+ m~ p / r, (grad p)_z = i alpha k p; stored without
+    the i), and the responses to unit wall values of u+, u-, u_z; and the
+    fixed-flux response G = H_0^{-1} of a uniform forcing (section 1)."""
+    alpha, Re, dt, c = 1.25, 400.0, 0.01, 0.5
+    q = lambda what: opf.opf_setup_query(N, K, M, m_p, alpha, Re, dt, what)  # noqa: E731
+    basis = q("basis").reshape(K, M, 6, N)
+    r = mesh(N)
+    mats = {1: fd_matrices(r, 1), -1: fd_matrices(r, -1)}
+    e = np.zeros(N)
+    e[-1] = 1.0
+
+    def lap(j, ak, par):
+        D1, D2 = mats[par]
+        return D2 + D1 / r[:, None] - np.diag(j * j / r ** 2 + ak * ak)
+
+    def helm_solve(j, ak, rhs):
+        H = np.eye(N) / dt - c / Re * lap(j, ak, 1 if j % 2 == 0 else -1)
+        H[-1] = 0.0
+        H[-1, -1] = 1.0
+        return np.linalg.solve(H, rhs)
+
+    for ik in range(K):
+        ak = alpha * ik
+        for m in range(M):
+            if ik == 0 and m == 0:
+                assert not np.any(basis[0, 0])
+                continue
+            mt = m_p * m
+            par = 1 if mt % 2 == 0 else -1
+            P = lap(mt, ak, par)
+            P[-1] = mats[par][0][-1]
+            p1 = np.linalg.solve(P, e)
+            dp = mats[par][0] @ p1
+            rhs = [-(dp - mt * p1 / r), -(dp + mt * p1 / r), -ak * p1]
+            for v in rhs:
+                v[-1] = 0.0
+            js = (mt + 1, abs(mt - 1), mt)
+            want = [helm_solve(j, ak, v) for j, v in zip(js, rhs)] + [helm_solve(j, ak, e) for j in js]
+            # (the pressure-driven responses against the largest of the three:
+            # one of them vanishes where the gradient does, e.g. m~ = 1, k = 0)
+            scale_p = max(np.abs(w).max() for w in want[:3])
+            for f in range(6):
+                scale = scale_p if f < 3 else np.abs(want[f]).max()
+                assert np.abs(basis[ik, m, f] - want[f]).max() <= 1e-11 * scale, (ik, m, f)
+    g = np.ones(N)
+    g[-1] = 0.0
+    G = helm_solve(0, 0.0, g)
+    assert np.abs(q("G") - G).max() <= 1e-12 * np.abs(G).max()
