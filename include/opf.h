@@ -413,8 +413,12 @@ int opf_change_resolution(int N1, int K1, int M1, const double* in, int N2, int 
  * band; luH is [K][nJ] Helmholtz operators 1/dt - c L_j with the Dirichlet
  * wall row, luP is [K][M] pressure operators with the Neumann wall row plus
  * (0,0) with p(1) = 0 last), "hop" ([M][3] the index j' < nJ of the
- * Helmholtz operator of u+, u-, u_z at each m; section 2.2).  *len receives
- * the full length; OPF_EINVAL if cap is too small or what is unknown. */
+ * Helmholtz operator of u+, u-, u_z at each m; section 2.2), "ainv"
+ * ([M][2K-1][4][4] complex as (re, im) pairs: the inverse of the influence
+ * matrix A, A[i][j] = g_i of basis response j, g = (u+(1), u-(1), u_z(1),
+ * div u(1)), responses (pressure, unit u+, u-, u_z wall values); section 2;
+ * zero at (0,0)).  *len receives the full length; OPF_EINVAL if cap is too
+ * small or what is unknown. */
 int opf_setup_query(int N, int K, int M, int m_p, double alpha, double Re, double dt,
                     const char* what, double* out, long cap, long* len);
 /* Same, on a user radial mesh r (N points as for opf_create_mesh; NULL = the

@@ -1420,6 +1420,7 @@ int opf_setup_query_mesh(int N, int K, int M, int m_p, double alpha, double Re, 
   else if (!strcmp(what, "luH")) v = &s.luH;
   else if (!strcmp(what, "luP")) v = &s.luP;
   else if (!strcmp(what, "hop")) v = &hop;
+  else if (!strcmp(what, "ainv")) v = &s.ainv;
   else return fail(OPF_EINVAL, std::string("opf_setup_query: unknown array ") + what);
   *len = (long)v->size();
   if (!out) return OPF_OK;

@@ -230,3 +230,37 @@ def test_influence_responses_match_the_oracle_operators(opf, N, K, M, m_p):
     g[-1] = 0.0
     G = helm_solve(0, 0.0, g)
     assert np.abs(q("G") - G).max() <= 1e-12 * np.abs(G).max()
+
+
+@pytest.mark.parametrize("N,K,M,m_p", [(16, 3, 3, 1), (33, 2, 4, 2)])
+def test_inverse_influence_matrices_match_the_oracle(opf, N, K, M, m_p):
+    """The 4 x 4 influence matrices of section 2 per (k, m) != (0,0): column j
+    is the boundary vector g = (u+(1), u-(1), u_z(1), div u(1)) of response j
+    (the pressure-driven velocity, then unit wall values of u+, u-, u_z), the
+    divergence in +- form, 1/2 (u+' + u-') + 1/2 ((1 + m~) u+ + (1 - m~) u-)/r
+    + i alpha k u_z, with the oracle's wall stencil of the u+- parity.  The
+    host's inverses times the oracle's matrices give the identity."""
+    alpha, Re, dt = 1.25, 400.0, 0.01
+    q = lambda what: opf.opf_setup_query(N, K, M, m_p, alpha, Re, dt, what)  # noqa: E731
+    basis = q("basis").reshape(K, M, 6, N)
+    ainv = q("ainv").reshape(M, 2 * K - 1, 4, 4, 2)
+    ainv = ainv[..., 0] + 1j * ainv[..., 1]
+    r = mesh(N)
+    for m in range(M):
+        mt = m_p * m
+        wall_d1 = fd_matrices(r, -1 if mt % 2 == 0 else 1)[0][-1]  # u+- have parity (-1)^(m~+1)
+        for kk in range(2 * K - 1):
+            k = kk - (K - 1)
+            if k == 0 and m == 0:
+                assert not np.any(ainv[m, kk])
+                continue
+            B = basis[abs(k), m]
+            sgn = 1.0 if k >= 0 else -1.0
+            resp = [(B[0], B[1], 1j * sgn * B[2]), (B[3], 0 * r, 0 * r), (0 * r, B[4], 0 * r),
+                    (0 * r, 0 * r, B[5])]
+            A = np.zeros((4, 4), dtype=complex)
+            for j, (up, um, uz) in enumerate(resp):
+                div = 0.5 * wall_d1 @ (up + um) + 0.5 * ((1 + mt) * up[-1] + (1 - mt) * um[-1]) / r[-1] \
+                    + 1j * alpha * k * uz[-1]
+                A[:, j] = (up[-1], um[-1], uz[-1], div)
+            assert np.abs(ainv[m, kk] @ A - np.eye(4)).max() <= 1e-10, (m, k)
