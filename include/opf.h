@@ -417,8 +417,13 @@ int opf_change_resolution(int N1, int K1, int M1, const double* in, int N2, int 
  * ([M][2K-1][4][4] complex as (re, im) pairs: the inverse of the influence
  * matrix A, A[i][j] = g_i of basis response j, g = (u+(1), u-(1), u_z(1),
  * div u(1)), responses (pressure, unit u+, u-, u_z wall values); section 2;
- * zero at (0,0)).  *len receives the full length; OPF_EINVAL if cap is too
- * small or what is unknown. */
+ * zero at (0,0)); the two-partition forms of the same operators (even
+ * N >= 26 only): "luH2" / "luP2" (per operator the top block's factors,
+ * N/2 rows, then the bottom block's, each stored as luH), "spkH" / "spkP"
+ * (per operator N rows of 4: T^{-1} H(0:k, k:k+4), then
+ * B^{-1} H(k:N, k-4:k), k = N/2), "rH" / "rP" (per operator the 8 x 8
+ * inverse of the interface system, row-major).  *len receives the full
+ * length; OPF_EINVAL if cap is too small or what is unknown. */
 int opf_setup_query(int N, int K, int M, int m_p, double alpha, double Re, double dt,
                     const char* what, double* out, long cap, long* len);
 /* Same, on a user radial mesh r (N points as for opf_create_mesh; NULL = the

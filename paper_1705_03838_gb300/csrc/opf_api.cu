@@ -1407,6 +1407,9 @@ int opf_setup_query_mesh(int N, int K, int M, int m_p, double alpha, double Re, 
   s.Re = Re;
   s.dt = dt;
   s.c = 0.5;
+  const char* split_arrays[] = {"luH2", "luP2", "spkH", "spkP", "rH", "rP"};
+  for (const char* a : split_arrays)
+    if (!strcmp(what, a)) s.spike = true;  // the split forms are built on request
   std::string err;
   if (!opf::build_setup(&s, &err)) return fail(OPF_EINVAL, "opf_setup_query: " + err);
   const std::vector<double>* v = nullptr;
@@ -1421,6 +1424,12 @@ int opf_setup_query_mesh(int N, int K, int M, int m_p, double alpha, double Re, 
   else if (!strcmp(what, "luP")) v = &s.luP;
   else if (!strcmp(what, "hop")) v = &hop;
   else if (!strcmp(what, "ainv")) v = &s.ainv;
+  else if (!strcmp(what, "luH2")) v = &s.luH2;
+  else if (!strcmp(what, "luP2")) v = &s.luP2;
+  else if (!strcmp(what, "spkH")) v = &s.spkH;
+  else if (!strcmp(what, "spkP")) v = &s.spkP;
+  else if (!strcmp(what, "rH")) v = &s.rH;
+  else if (!strcmp(what, "rP")) v = &s.rP;
   else return fail(OPF_EINVAL, std::string("opf_setup_query: unknown array ") + what);
   *len = (long)v->size();
   if (!out) return OPF_OK;

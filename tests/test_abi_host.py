@@ -264,3 +264,66 @@ def test_inverse_influence_matrices_match_the_oracle(opf, N, K, M, m_p):
                     + 1j * alpha * k * uz[-1]
                 A[:, j] = (up[-1], um[-1], uz[-1], div)
             assert np.abs(ainv[m, kk] @ A - np.eye(4)).max() <= 1e-10, (m, k)
+
+
+@pytest.mark.parametrize("N,K,M,m_p", [(32, 2, 3, 1), (48, 2, 3, 2)])
+def test_split_factors_solve_the_oracle_operators(opf, N, K, M, m_p):
+    """The two-partition (split) data of every radial operator: the system
+    cut at k = N/2 into diagonal blocks T and B, each substituted on its own
+    (device layout), then the interface values z = R (y_T[k-4:k], y_B[0:4])
+    and the rank-4 spike corrections x_T = y_T - S_T z_B, x_B = y_B - S_B z_T.
+    The result solves the oracle's operators (as in the unsplit check)."""
+    alpha, Re, dt, c = 1.25, 400.0, 0.01, 0.5
+    q = lambda what: opf.opf_setup_query(N, K, M, m_p, alpha, Re, dt, what)  # noqa: E731
+    k = N // 2
+    hop = q("hop").astype(int).reshape(M, 3)
+    data = {}
+    for f in ("H", "P"):
+        lu, spk, rr = q("lu" + f + "2"), q("spk" + f), q("r" + f)
+        nop = lu.size // (13 * N)
+        data[f] = (lu.reshape(nop, 13 * N), spk.reshape(nop, N, 4), rr.reshape(nop, 8, 8))
+    nJ = data["H"][0].shape[0] // K
+    r = mesh(N)
+    mats = {1: fd_matrices(r, 1), -1: fd_matrices(r, -1)}
+    rng = np.random.default_rng(5)
+
+    def lap(j, ak, par):
+        D1, D2 = mats[par]
+        return D2 + D1 / r[:, None] - np.diag(j * j / r ** 2 + ak * ak)
+
+    def check(A, f, o):
+        lu, spk, R = (a[o] for a in data[f])
+        b = rng.standard_normal(N)
+        b[-1] = 0.0
+        x = np.empty(N)
+        x[:k] = column_substitution(lu[:13 * k], b[:k])
+        x[k:] = column_substitution(lu[13 * k:], b[k:])
+        z = R @ np.concatenate([x[k - 4:k], x[k:k + 4]])
+        x[:k] -= spk[:k] @ z[4:]
+        x[k:] -= spk[k:] @ z[:4]
+        res = np.abs(A @ x - b).max()
+        assert res <= 1e-12 * (np.abs(A).sum(axis=1).max() * np.abs(x).max() + np.abs(b).max()), (f, o)
+
+    for ik in range(K):
+        ak = alpha * ik
+        for m in range(M):
+            mt = m_p * m
+            for fi, j in enumerate((mt + 1, abs(mt - 1), mt)):
+                H = np.eye(N) / dt - c / Re * lap(j, ak, 1 if j % 2 == 0 else -1)
+                H[-1] = 0.0
+                H[-1, -1] = 1.0
+                check(H, "H", ik * nJ + hop[m, fi])
+            par = 1 if mt % 2 == 0 else -1
+            P = lap(mt, ak, par)
+            if ik == 0 and m == 0:
+                P[-1] = 0.0
+                P[-1, -1] = 1.0
+                check(P, "P", K * M)
+            else:
+                P[-1] = mats[par][0][-1]
+                check(P, "P", ik * M + m)
+
+
+def test_split_arrays_need_an_even_n_of_26_or_more(opf):
+    with pytest.raises(opf.OpfError):
+        opf.opf_setup_query(25, 2, 2, 1, 1.25, 100.0, 0.01, "luH2")
