@@ -290,6 +290,13 @@ int group_build(Group* g, int N, int K, int M, int m_p, double alpha, int B, con
     if (!(Re[b] > 0) || !(dt[b] > 0)) return fail(OPF_EINVAL, "need Re>0, dt>0");
   if (!smooth235(3 * K) || !smooth235(3 * M))
     return fail(OPF_EINVAL, "3K and 3M must have no prime factor other than 2, 3, 5");
+  int ndev = 0;
+  const cudaError_t de = cudaGetDeviceCount(&ndev);
+  if (de != cudaSuccess || ndev < 1) {
+    cudaGetLastError();
+    return fail(OPF_ECUDA, std::string("no CUDA device available (") +
+                               (de != cudaSuccess ? cudaGetErrorString(de) : "0 devices") + ")");
+  }
   opf::Dims& d = g->d;
   d.N = N;
   d.K = K;

@@ -327,3 +327,15 @@ def test_split_factors_solve_the_oracle_operators(opf, N, K, M, m_p):
 def test_split_arrays_need_an_even_n_of_26_or_more(opf):
     with pytest.raises(opf.OpfError):
         opf.opf_setup_query(25, 2, 2, 1, 1.25, 100.0, 0.01, "luH2")
+
+
+def test_create_without_a_gpu_fails_with_the_reason(opf):
+    """On a machine without a CUDA device the library refuses to create a
+    handle and says why (there is no CPU fallback)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(opf.OpfError, match="no CUDA device"):
+        opf.opf_create(16, 3, 3, 1, 1.25, 100.0, 0.01)
+    with pytest.raises(opf.OpfError, match="need N>=9"):  # arguments are checked first
+        opf.opf_create(8, 3, 3, 1, 1.25, 100.0, 0.01)
